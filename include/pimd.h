@@ -1,0 +1,216 @@
+/*
+ * pimd.h -- C ABI of libpimd: ring-polymer path-integral molecular dynamics
+ * (the "fix pimd/langevin" method of arXiv 2602.13553) on one NVIDIA GB300.
+ *
+ * The library advances N atoms x P beads with the PILE_L-thermostatted
+ * normal-mode integrator of Sec. IV.A (BAOAB or OBABO splitting, Sec. III.C
+ * keyword "integrator"), evaluates bead-batched forces (a harmonic external
+ * well or a flexible water-like model with O-O Lennard-Jones), and reduces
+ * the estimators of App. A.  Every step of that path runs in this library's
+ * CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions for every entry point
+ *   Units       LAMMPS "metal": Angstrom, ps, eV, amu, K (Sec. III.A example).
+ *   Layouts     host arrays are C order [P][N][3] (bead or mode k, atom i,
+ *               component a).  Positions are Cartesian and unwrapped
+ *               (Sec. IV.B: every bead of an atom carries the same image);
+ *               velocities are normal-mode velocities (Sec. III.A: the
+ *               per-bead velocities the method reports are in the normal-mode
+ *               representation).
+ *   Ownership   caller buffers are read or written only during the call;
+ *               device state belongs to the handle and is freed by
+ *               pimd_destroy.
+ *   Errors      every call returns a pimd_status and never aborts the
+ *               process.  Asynchronous failures of pimd_step (a CUDA error, a
+ *               neighbour-list overflow, a non-finite sum) are latched in the
+ *               handle and returned by the next synchronising call
+ *               (pimd_estimators, pimd_get_state, pimd_sync).
+ *               pimd_last_error() gives a human-readable message for the
+ *               calling thread's most recent failure.
+ *   Threads     one host thread per handle at a time.  The serving entry
+ *               points are internally synchronised.
+ */
+#ifndef PIMD_H
+#define PIMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIMD_MAX_BEADS 128
+
+typedef enum {
+  PIMD_OK = 0,
+  PIMD_EINVAL = 1,      /* an argument is out of range (message in pimd_last_error) */
+  PIMD_ENOMEM = 2,      /* a device or host allocation failed */
+  PIMD_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  PIMD_ENONFINITE = 4,  /* an estimator sum became NaN or Inf */
+  PIMD_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+  PIMD_EPENDING = 6,    /* serving: the job has not finished yet */
+  PIMD_ENOTFOUND = 7,   /* serving: unknown job id */
+  PIMD_EBUDGET = 8,     /* serving: the job can never fit the HBM budget */
+  PIMD_EOVERFLOW = 9    /* a fixed-capacity device table (neighbour list) overflowed */
+} pimd_status;
+
+/* potential energy surface U(r^(k)) of one bead (Eq. 1) */
+enum { PIMD_POT_HARMONIC = 0, PIMD_POT_WATERLIKE = 1 };
+/* Sec. III.C keyword "thermostat": none (NVE) or PILE_L (App. D) */
+enum { PIMD_THERMO_NONE = 0, PIMD_THERMO_PILE_L = 1 };
+/* Sec. III.C keyword "integrator" */
+enum { PIMD_BAOAB = 0, PIMD_OBABO = 1 };
+/* Sec. III.C keyword "method": only nmpimd (normal modes) is implemented */
+enum { PIMD_METHOD_NMPIMD = 0 };
+/* arithmetic of the step and force kernels */
+enum { PIMD_PREC_FP64 = 0 };
+
+typedef struct pimd_handle pimd_handle;
+
+/* The physical system.  Copied at pimd_create; the pointers are host memory.
+ *   mass      [n_atoms] physical masses (amu); fmmode physical (Sec. III.C).
+ *   pos       [P][n_atoms][3] bead positions (A), unwrapped.
+ *   vel       [P][n_atoms][3] normal-mode velocities (A/ps) at integer time,
+ *             or NULL: every mode is then drawn from N(0, P kB T/(m mvv2e))
+ *             (the ring polymer is thermostatted at P T, Sec. IV.A) with
+ *             noise stream 2 of the Philox keying described at pimd_create.
+ *   potential PIMD_POT_HARMONIC: U = 1/2 m omega^2 |r|^2 per atom,
+ *               ff[0] = omega (1/ps); box ignored (no pressure estimators).
+ *             PIMD_POT_WATERLIKE: atoms 3m, 3m+1, 3m+2 are the O, H, H of
+ *               molecule m (n_atoms a multiple of 3); ff = {kb (eV/A^2),
+ *               r0 (A), kth (eV/rad^2), th0 (rad), eps (eV), sigma (A),
+ *               rc (A)}; U = sum 1/2 kb (r - r0)^2 over the two O-H bonds +
+ *               1/2 kth (theta - th0)^2 over H-O-H + 4 eps[(s/r)^12-(s/r)^6]
+ *               over O-O pairs closer than rc (no shift), minimum image in a
+ *               periodic orthorhombic box with every edge > 2 rc. */
+typedef struct {
+  int32_t n_atoms;
+  int32_t potential;
+  const double *mass;
+  const double *pos;
+  const double *vel;
+  double box[3];
+  double ff[8];
+} pimd_system;
+
+/* Method keywords (Sec. III.C).  Defaults from pimd_params_default:
+ * thermostat PILE_L, integrator BAOAB, method nmpimd, seed 1, tau 1 ps,
+ * scale 1, sp 1, fixcom 0 (the paper's default is "yes"; it couples
+ * otherwise independent systems, so this library defaults to "no", as the
+ * paper's own example input does), precision FP64.
+ *   tau     damping time of the centroid mode (ps), App. D.
+ *   scale   tau_k = scale / (2 omega_k) for k >= 1, App. D.
+ *   sp      hbar -> sp * hbar; only omega_n changes (Eq. 2).  Must be > 0.
+ *   fixcom  must be 0 (removal of the centroid centre-of-mass velocity is not
+ *           implemented). */
+typedef struct {
+  int32_t thermostat;
+  int32_t integrator;
+  int32_t method;
+  int32_t precision;
+  uint64_t seed;
+  double tau;
+  double scale;
+  double sp;
+  int32_t fixcom;
+  int32_t reserved;
+} pimd_params;
+
+/* App. A outputs 1-10 at integer time, plus bookkeeping.
+ *   K_mode[k]  output 1: 1/2 sum_i m_i |v~_i^(k)|^2 (eV), k < P
+ *   S_mode[k]  output 2: 1/2 sum_i m_i omega_n^2 lambda_k |q~_i^(k)|^2 (eV),
+ *              reading the printed "m omega_n" as m omega_n^2
+ *   U_bead[k]  output 3: potential energy of bead k (eV)
+ *   H          output 4: sum_k (K + S + U)
+ *   K_PR       output 5: 3 P N kB T / 2 - (1/P) sum 1/2 m omega_n^2 |r^k - r^(k+1)|^2
+ *   K_VR       output 6: -(1/2P) sum r.F
+ *   K_CV       output 7: 3 N kB T / 2 - (1/2P) sum (r - r_c).F
+ *   P_PR       output 8: [3 P N kB T - (1/P) sum m omega_n^2 |dr|^2 + (1/P) sum_k Tr Xi^(k)] / 3V
+ *   P_MD       output 9: sum_k [sum_i m |v~^(k)|^2 + Tr Xi^(k)] / 3V
+ *   P_CV       output 10: [sum_i m |v~^(0)|^2 - sum (r - r_c).F + sum_k Tr Xi^(k)] / 3PV
+ *   T_ring     2 sum_k K^(k) / (3 N P kB): equals P T in equilibrium (Sec. IV.A)
+ * Pressures are eV/A^3 (NaN without a periodic box); volume in A^3;
+ * vir_sum = sum_k Tr Xi^(k) (eV). */
+typedef struct {
+  int64_t step;
+  int32_t P;
+  int32_t N;
+  double K_mode[PIMD_MAX_BEADS];
+  double S_mode[PIMD_MAX_BEADS];
+  double U_bead[PIMD_MAX_BEADS];
+  double H, K_PR, K_VR, K_CV, P_PR, P_MD, P_CV, T_ring;
+  double volume, vir_sum;
+} pimd_estimates;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes usable on `stream`,
+ * or NULL on failure; free releases it.  With no allocator set the library
+ * uses cudaMalloc / cudaFree.  Affects handles created afterwards. */
+typedef void *(*pimd_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*pimd_free_fn)(void *ptr, void *stream, void *ctx);
+void pimd_set_allocator(pimd_alloc_fn alloc, pimd_free_fn release, void *ctx);
+
+void pimd_params_default(pimd_params *out);
+const char *pimd_status_string(pimd_status s);
+const char *pimd_last_error(void);
+
+/* Create a handle for one ring-polymer system (Sec. III.C: "fix ... pimd/langevin").
+ *   P       number of beads, 1..PIMD_MAX_BEADS.
+ *   T       temperature (K) > 0; omega_n = P kB T / (sp hbar) (Eq. 2).
+ *   dt      time step (ps) > 0.
+ *   gamma0  centroid friction (1/ps); if > 0 it sets tau = 1/gamma0, and a
+ *           params->tau that disagrees by more than 1e-12 relative is EINVAL.
+ *           Pass 0 to use params->tau.
+ *   params  NULL for pimd_params_default().
+ *   stream  a cudaStream_t on which every kernel of this handle runs (NULL
+ *           for the legacy default stream).
+ * The PILE_L noise is Philox-4x32-10 (Salmon et al., SC'11) with key =
+ * (seed low 32, seed high 32) and counter = (atom, (mode & 0xffff) |
+ * (stream << 16), step low 32, step high 32); its four words w become
+ * u = (w + 1/2) 2^-32 and Box-Muller gives (eta_x, eta_y) from (u0, u1) and
+ * eta_z from (u2, u3).  Streams: 0 = O step of BAOAB and first O of OBABO,
+ * 1 = second O of OBABO, 2 = initial velocities.
+ * Validation (EINVAL): P outside 1..128, T <= 0, dt <= 0, n_atoms <= 0, NULL
+ * mass/pos, non-positive mass, unknown potential/thermostat/integrator/
+ * method/precision, tau <= 0 or scale <= 0 with PILE_L, sp <= 0,
+ * fixcom != 0, water-like n_atoms not a multiple of 3 or a box edge <= 2 rc.
+ * Computes the forces of the initial positions before returning. */
+pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, double dt, double gamma0,
+                        const pimd_params *params, void *stream, pimd_handle **out);
+
+/* Advance n >= 0 time steps (asynchronous on the handle's stream).  Each
+ * step is the splitting chosen at create: BAOAB = B(h/2) A(h/2) O(h) A(h/2)
+ * [forces] B(h/2); OBABO = O(h/2) B(h/2) A(h) [forces] B(h/2) O(h/2), where
+ * B kicks v~ with the normal-mode forces M F (Sec. IV.A), A is the exact
+ * harmonic flow of each free-ring-polymer mode (i-PI's equations of motion)
+ * and O is PILE_L (App. D).  On return of the queued work the state is at
+ * integer time. */
+pimd_status pimd_step(pimd_handle *h, int64_t n);
+
+/* Wait for the handle's queued work; returns any latched error. */
+pimd_status pimd_sync(pimd_handle *h);
+
+/* Reduce the App. A estimators of the current state on the device (one
+ * fixed-order, compensated pass) and copy them to *out (host).  Synchronises
+ * the handle's stream. */
+pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out);
+
+/* Copy the state to host arrays: x [P][N][3] Cartesian positions (A), v_nm
+ * [P][N][3] normal-mode velocities (A/ps), *step the step counter.  Any of
+ * the three pointers may be NULL.  Synchronises the handle's stream. */
+pimd_status pimd_get_state(pimd_handle *h, double *x, double *v_nm, int64_t *step);
+
+/* Replace the state from host arrays (layouts as pimd_get_state; both x and
+ * v_nm are required) and recompute the forces.  Together with
+ * pimd_get_state this is checkpoint / resume: the noise is keyed on the step
+ * counter, so a resumed run continues bit for bit. */
+pimd_status pimd_set_state(pimd_handle *h, const double *x, const double *v_nm, int64_t step);
+
+/* Release the handle and its device memory (waits for its queued work). */
+void pimd_destroy(pimd_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIMD_H */

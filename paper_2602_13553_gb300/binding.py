@@ -1,0 +1,251 @@
+"""ctypes binding of libpimd (include/pimd.h): argument marshalling only.
+
+Every step of the PIMD path runs in the library's CUDA kernels.  If the
+library has not been built, or cannot be loaded, the calls raise: there is no
+CPU fallback.  PyTorch, when present, only provides device memory (through
+the library's allocator hook, see ``use_torch_allocator``) and CUDA streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpimd.so")
+
+POT_HARMONIC = 0
+POT_WATERLIKE = 1
+THERMO_NONE = 0
+THERMO_PILE_L = 1
+BAOAB = 0
+OBABO = 1
+METHOD_NMPIMD = 0
+PREC_FP64 = 0
+MAX_BEADS = 128
+
+STATUS = {0: "PIMD_OK", 1: "PIMD_EINVAL", 2: "PIMD_ENOMEM", 3: "PIMD_ECUDA", 4: "PIMD_ENONFINITE",
+          5: "PIMD_ETIMEOUT", 6: "PIMD_EPENDING", 7: "PIMD_ENOTFOUND", 8: "PIMD_EBUDGET",
+          9: "PIMD_EOVERFLOW"}
+
+
+class PimdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class System(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int32), ("potential", ctypes.c_int32),
+        ("mass", ctypes.POINTER(ctypes.c_double)),
+        ("pos", ctypes.POINTER(ctypes.c_double)),
+        ("vel", ctypes.POINTER(ctypes.c_double)),
+        ("box", ctypes.c_double * 3),
+        ("ff", ctypes.c_double * 8),
+    ]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("thermostat", ctypes.c_int32), ("integrator", ctypes.c_int32),
+        ("method", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("tau", ctypes.c_double), ("scale", ctypes.c_double), ("sp", ctypes.c_double),
+        ("fixcom", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class Estimates(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("P", ctypes.c_int32), ("N", ctypes.c_int32),
+        ("K_mode", ctypes.c_double * MAX_BEADS), ("S_mode", ctypes.c_double * MAX_BEADS),
+        ("U_bead", ctypes.c_double * MAX_BEADS),
+        ("H", ctypes.c_double), ("K_PR", ctypes.c_double), ("K_VR", ctypes.c_double),
+        ("K_CV", ctypes.c_double), ("P_PR", ctypes.c_double), ("P_MD", ctypes.c_double),
+        ("P_CV", ctypes.c_double), ("T_ring", ctypes.c_double),
+        ("volume", ctypes.c_double), ("vir_sum", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        P = self.P
+        out = {k: getattr(self, k) for k in ("H", "K_PR", "K_VR", "K_CV", "P_PR", "P_MD", "P_CV",
+                                             "T_ring", "volume", "vir_sum")}
+        out["step"] = int(self.step)
+        out["K_mode"] = np.array(self.K_mode[:P])
+        out["S_mode"] = np.array(self.S_mode[:P])
+        out["U_bead"] = np.array(self.U_bead[:P])
+        return out
+
+
+# every symbol include/pimd.h declares (checked by the CPU tests)
+EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "pimd_last_error",
+           "pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
+           "pimd_set_state", "pimd_destroy")
+
+_lock = threading.Lock()
+_lib = None
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def lib():
+    """Load libpimd.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpimd.so is not built (%s); run paper_2602_13553_gb300.build.build()"
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.pimd_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+        L.pimd_set_allocator.restype = None
+        L.pimd_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.pimd_params_default.restype = None
+        L.pimd_status_string.argtypes = [ctypes.c_int]
+        L.pimd_status_string.restype = ctypes.c_char_p
+        L.pimd_last_error.argtypes = []
+        L.pimd_last_error.restype = ctypes.c_char_p
+        L.pimd_create.argtypes = [ctypes.POINTER(System), ctypes.c_int32, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.POINTER(Params), vp,
+                                  ctypes.POINTER(vp)]
+        L.pimd_step.argtypes = [vp, ctypes.c_int64]
+        L.pimd_sync.argtypes = [vp]
+        L.pimd_estimators.argtypes = [vp, ctypes.POINTER(Estimates)]
+        L.pimd_get_state.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.pimd_set_state.argtypes = [vp, dp, dp, ctypes.c_int64]
+        L.pimd_destroy.argtypes = [vp]
+        L.pimd_destroy.restype = None
+        for f in ("pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
+                  "pimd_set_state"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def check(status: int) -> None:
+    if status != 0:
+        msg = lib().pimd_last_error().decode(errors="replace")
+        raise PimdError(status, msg)
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().pimd_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+_torch_alloc_refs = None
+
+
+def use_torch_allocator() -> None:
+    """Route libpimd's device allocations through PyTorch's caching allocator."""
+    global _torch_alloc_refs
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or None))
+        except Exception:  # reported to the library as NULL -> PIMD_ENOMEM
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _torch_alloc_refs = (a, f)
+    lib().pimd_set_allocator(a, f, None)
+
+
+def reset_allocator() -> None:
+    global _torch_alloc_refs
+    lib().pimd_set_allocator(ALLOC_FN(), FREE_FN(), None)
+    _torch_alloc_refs = None
+
+
+class Simulation:
+    """One ring-polymer system on the GPU (a pimd_handle).
+
+    x0: [P][N][3] positions (A); v0: [P][N][3] normal-mode velocities or None
+    (thermal draw).  Keyword arguments map onto pimd_params fields.
+    """
+
+    def __init__(self, x0, mass, *, T, dt, potential=POT_HARMONIC, ff=(0.0,), box=(0.0, 0.0, 0.0),
+                 v0=None, gamma0=0.0, stream=None, **params):
+        self.x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        P, N, three = self.x0.shape
+        assert three == 3
+        self.P, self.N = P, N
+        self.mass = np.ascontiguousarray(mass, dtype=np.float64)
+        self.v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
+        s = System()
+        s.n_atoms = N
+        s.potential = potential
+        s.mass = _dp(self.mass)
+        s.pos = _dp(self.x0)
+        s.vel = _dp(self.v0)
+        for a in range(3):
+            s.box[a] = float(box[a])
+        ffl = list(ff) + [0.0] * (8 - len(ff))
+        for a in range(8):
+            s.ff[a] = float(ffl[a])
+        prm = default_params(**params)
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        check(lib().pimd_create(ctypes.byref(s), P, T, dt, gamma0, ctypes.byref(prm), st,
+                                ctypes.byref(h)))
+        self._h = h
+
+    def step(self, n: int) -> None:
+        check(lib().pimd_step(self._h, int(n)))
+
+    def sync(self) -> None:
+        check(lib().pimd_sync(self._h))
+
+    def estimators(self) -> dict:
+        e = Estimates()
+        check(lib().pimd_estimators(self._h, ctypes.byref(e)))
+        return e.as_dict()
+
+    def get_state(self, x=None, v=None):
+        x = np.empty((self.P, self.N, 3)) if x is None else x
+        v = np.empty((self.P, self.N, 3)) if v is None else v
+        st = ctypes.c_int64()
+        check(lib().pimd_get_state(self._h, _dp(x), _dp(v), ctypes.byref(st)))
+        return x, v, int(st.value)
+
+    def set_state(self, x, v, step: int) -> None:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        check(lib().pimd_set_state(self._h, _dp(x), _dp(v), int(step)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().pimd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

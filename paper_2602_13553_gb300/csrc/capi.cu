@@ -1,0 +1,706 @@
+// capi.cu -- host runtime behind the C ABI of include/pimd.h: validation,
+// the precomputed mode tables (App. B, App. D), device memory, the launch
+// sequence of a step, CUDA-graph replay of steady-state steps, and the
+// estimator / state transfers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "pimd.h"
+
+namespace pimd {
+size_t step_smem_bytes(int A, int P);
+size_t close_smem_bytes(int A, int P);
+size_t est_smem_bytes(int A, int P);
+cudaError_t launch_step(const StepArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_close(const StepArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_advance(int64_t *step, int n, cudaStream_t s);
+cudaError_t launch_thermal_v(double *v, const double *sigv, uint64_t seed, int N, int P,
+                             cudaStream_t s);
+cudaError_t launch_pna_to_nap(const double *src, double *dst, int N, int P, cudaStream_t s);
+cudaError_t launch_nap_to_pna(const double *src, double *dst, int N, int P, cudaStream_t s);
+cudaError_t launch_force_harmonic(const ForceArgs &a, cudaStream_t s);
+cudaError_t launch_force_water(const ForceArgs &a, cudaStream_t s);
+cudaError_t launch_nbr(const NbrArgs &a, double *ccur, cudaStream_t s);
+cudaError_t launch_est(const EstArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_est_final(const EstFinalArgs &a, cudaStream_t s);
+int force_blocks(int n_groups, int P);
+int nbr_check_blocks(int nmol);
+}  // namespace pimd
+
+using namespace pimd;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static pimd_status fail(pimd_status s, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(PIMD_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                               \
+  } while (0)
+
+extern "C" const char *pimd_last_error(void) { return g_err; }
+
+extern "C" const char *pimd_status_string(pimd_status s) {
+  switch (s) {
+    case PIMD_OK: return "ok";
+    case PIMD_EINVAL: return "invalid argument";
+    case PIMD_ENOMEM: return "out of memory";
+    case PIMD_ECUDA: return "CUDA error";
+    case PIMD_ENONFINITE: return "non-finite estimator";
+    case PIMD_ETIMEOUT: return "device wait timed out";
+    case PIMD_EPENDING: return "pending";
+    case PIMD_ENOTFOUND: return "not found";
+    case PIMD_EBUDGET: return "exceeds memory budget";
+    case PIMD_EOVERFLOW: return "device table overflow";
+  }
+  return "unknown status";
+}
+
+// ---------------------------------------------------------------------------
+// device allocator (optional external callbacks, e.g. a caching allocator)
+// ---------------------------------------------------------------------------
+struct Allocator {
+  pimd_alloc_fn alloc = nullptr;
+  pimd_free_fn release = nullptr;
+  void *ctx = nullptr;
+};
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
+
+extern "C" void pimd_set_allocator(pimd_alloc_fn alloc, pimd_free_fn release, void *ctx) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.release = release;
+  g_alloc.ctx = ctx;
+}
+
+extern "C" void pimd_params_default(pimd_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->thermostat = PIMD_THERMO_PILE_L;
+  p->integrator = PIMD_BAOAB;
+  p->method = PIMD_METHOD_NMPIMD;
+  p->precision = PIMD_PREC_FP64;
+  p->seed = 1;
+  p->tau = 1.0;
+  p->scale = 1.0;
+  p->sp = 1.0;
+  p->fixcom = 0;
+}
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+struct pimd_handle {
+  int N = 0, P = 0, potential = 0, nmol = 0, integrator = 0, thermostat = 0;
+  double T = 0, dt = 0, tau = 0, scale = 0, sp = 0;
+  uint64_t seed = 0;
+  double box[3] = {0, 0, 0};
+  double ff[8] = {0};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Allocator alloc;
+  void *arena = nullptr;
+  size_t arena_bytes = 0;
+  // device state, layout [N][3][P]
+  double *x = nullptr, *v = nullptr, *F = nullptr, *tmp = nullptr;
+  double *inv_mm = nullptr, *sigv = nullptr, *mass_mm = nullptr, *kspring = nullptr;
+  double *M = nullptr, *Mt = nullptr, *cA = nullptr, *sA = nullptr, *wsA = nullptr;
+  double *c1 = nullptr, *c2 = nullptr, *lam = nullptr;
+  double *Upart = nullptr, *Wpart = nullptr;
+  int nblk_force = 0;
+  double *cref = nullptr, *ccur = nullptr, *blkmax = nullptr;
+  int *nbr = nullptr, *nnbr = nullptr;
+  double *est_part = nullptr, *est_out = nullptr;
+  int nblk_est = 0;
+  int64_t *d_step = nullptr;
+  unsigned *d_err = nullptr;
+  // pinned host mirrors
+  double *h_est = nullptr;
+  unsigned *h_err = nullptr;
+  // launch shapes
+  int A_step = 1, threads_step = 32, A_est = 1, threads_est = 32;
+  double wn = 0;
+  double skin = 1.5, rlist = 0;
+  int64_t step = 0;
+  pimd_status latched = PIMD_OK;
+  char latched_msg[256] = "";
+  // steady-state step graph (kick = h, no pending first step)
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  bool use_graph = true;
+};
+
+static void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s) {
+  if (a.alloc) return a.alloc(bytes, (void *)s, a.ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void dev_free(const Allocator &a, void *p, cudaStream_t s) {
+  if (!p) return;
+  if (a.release)
+    a.release(p, (void *)s, a.ctx);
+  else
+    cudaFree(p);
+}
+
+// Eq. (A1), with cos rows 1 <= i <= floor((P-1)/2), the alternating row at
+// i = P/2 for even P, and sin rows i > P/2.
+static void build_nm_matrix(int P, std::vector<double> &M) {
+  M.assign((size_t)P * P, 0.0);
+  const double rp = 1.0 / std::sqrt((double)P), r2p = std::sqrt(2.0 / P);
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) {
+      double val;
+      if (i == 0)
+        val = rp;
+      else if (P % 2 == 0 && 2 * i == P)
+        val = (j & 1) ? -rp : rp;
+      else if (2 * i < P)
+        val = r2p * std::cos(2.0 * kPi * (double)i * j / P);
+      else
+        val = r2p * std::sin(2.0 * kPi * (double)i * j / P);
+      M[(size_t)i * P + j] = val;
+    }
+}
+
+static int tile_atoms(int N, int P) {
+  const int amax = std::max(1, 256 / P);
+  const int want = (N + 303) / 304;   // >= 2 tiles per SM on 152 SMs while possible
+  return std::min(amax, std::max(1, want));
+}
+
+static int tile_threads(int A, int P) {
+  int t = ((A * P + 31) / 32) * 32;
+  return std::min(256, std::max(32, t));
+}
+
+static StepArgs step_args(pimd_handle *h) {
+  StepArgs a;
+  a.N = h->N;
+  a.P = h->P;
+  a.A = h->A_step;
+  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam};
+  a.inv_mm = h->inv_mm;
+  a.sigv = h->sigv;
+  a.x = h->x;
+  a.v = h->v;
+  a.F = h->F;
+  a.step = h->d_step;
+  a.step_off = 0;
+  a.kick = h->dt;
+  a.half = 0.5 * h->dt;
+  a.integrator = h->integrator;
+  a.first = 0;
+  a.thermo = h->thermostat == PIMD_THERMO_PILE_L;
+  a.seed = h->seed;
+  return a;
+}
+
+static ForceArgs force_args(pimd_handle *h) {
+  ForceArgs a;
+  a.N = h->N;
+  a.P = h->P;
+  a.nmol = h->nmol;
+  a.x = h->x;
+  a.F = h->F;
+  a.Upart = h->Upart;
+  a.Wpart = h->Wpart;
+  a.kspring = h->kspring;
+  for (int d = 0; d < 3; ++d) {
+    a.box[d] = h->box[d];
+    a.invbox[d] = h->box[d] > 0 ? 1.0 / h->box[d] : 0.0;
+  }
+  a.kb = h->ff[0];
+  a.r0 = h->ff[1];
+  a.kth = h->ff[2];
+  a.th0 = h->ff[3];
+  a.eps = h->ff[4];
+  a.sig = h->ff[5];
+  a.rc = h->ff[6];
+  a.nbr = h->nbr;
+  a.nnbr = h->nnbr;
+  return a;
+}
+
+static NbrArgs nbr_args(pimd_handle *h, bool force) {
+  NbrArgs a;
+  a.nmol = h->nmol;
+  a.P = h->P;
+  a.x = h->x;
+  a.cref = h->cref;
+  a.blkmax = h->blkmax;
+  a.nblk_check = nbr_check_blocks(h->nmol);
+  a.nbr = h->nbr;
+  a.nnbr = h->nnbr;
+  a.err = h->d_err;
+  for (int d = 0; d < 3; ++d) {
+    a.box[d] = h->box[d];
+    a.invbox[d] = 1.0 / h->box[d];
+  }
+  a.rlist = h->rlist;
+  a.skin = h->skin;
+  a.force = force ? 1 : 0;
+  return a;
+}
+
+// Forces of the current positions (and the neighbour list they need).
+static pimd_status enqueue_forces(pimd_handle *h, bool force_rebuild) {
+  if (h->potential == PIMD_POT_WATERLIKE) {
+    CK(launch_nbr(nbr_args(h, force_rebuild), h->ccur, h->stream));
+    CK(launch_force_water(force_args(h), h->stream));
+  } else {
+    CK(launch_force_harmonic(force_args(h), h->stream));
+  }
+  return PIMD_OK;
+}
+
+// One full step: the fused integrator kernel, the forces of the new
+// positions, and the step counter.
+static pimd_status enqueue_step(pimd_handle *h, bool first) {
+  StepArgs a = step_args(h);
+  a.first = first ? 1 : 0;
+  a.kick = first ? 0.5 * h->dt : h->dt;
+  CK(launch_step(a, h->threads_step, h->stream));
+  pimd_status st = enqueue_forces(h, false);
+  if (st != PIMD_OK) return st;
+  CK(launch_advance(h->d_step, 1, h->stream));
+  return PIMD_OK;
+}
+
+static pimd_status enqueue_close(pimd_handle *h) {
+  StepArgs a = step_args(h);
+  a.step_off = -1;
+  CK(launch_close(a, h->threads_step, h->stream));
+  return PIMD_OK;
+}
+
+static pimd_status build_graph(pimd_handle *h, int nsteps) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  pimd_status st = PIMD_OK;
+  for (int s = 0; s < nsteps && st == PIMD_OK; ++s) st = enqueue_step(h, false);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (st != PIMD_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(PIMD_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return fail(PIMD_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  h->graph_steps = nsteps;
+  return PIMD_OK;
+}
+
+static pimd_status check_device_errors(pimd_handle *h) {
+  CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (*h->h_err & kErrNbrOverflow) {
+    h->latched = PIMD_EOVERFLOW;
+    snprintf(h->latched_msg, sizeof(h->latched_msg),
+             "neighbour list overflow (more than %d O-O neighbours within rc + skin)",
+             kMaxNeighbours);
+  } else if (*h->h_err & kErrNonFinite) {
+    h->latched = PIMD_ENONFINITE;
+    snprintf(h->latched_msg, sizeof(h->latched_msg), "non-finite estimator sum");
+  }
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  return PIMD_OK;
+}
+
+static void release(pimd_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  dev_free(h->alloc, h->arena, h->stream);
+  if (h->h_est) cudaFreeHost(h->h_est);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+extern "C" void pimd_destroy(pimd_handle *h) { release(h); }
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+static void carve(pimd_handle *h, Carver &c) {
+  const size_t len = (size_t)h->N * 3 * h->P;
+  const int P = h->P, N = h->N;
+  h->x = c.take<double>(len);
+  h->v = c.take<double>(len);
+  h->F = c.take<double>(len);
+  h->tmp = c.take<double>(len);
+  h->inv_mm = c.take<double>(N);
+  h->sigv = c.take<double>(N);
+  h->mass_mm = c.take<double>(N);
+  h->kspring = c.take<double>(N);
+  h->M = c.take<double>((size_t)P * P);
+  h->Mt = c.take<double>((size_t)P * P);
+  h->cA = c.take<double>(P);
+  h->sA = c.take<double>(P);
+  h->wsA = c.take<double>(P);
+  h->c1 = c.take<double>(P);
+  h->c2 = c.take<double>(P);
+  h->lam = c.take<double>(P);
+  const int groups = h->potential == PIMD_POT_WATERLIKE ? h->nmol : h->N;
+  h->nblk_force = force_blocks(groups, P);
+  h->Upart = c.take<double>((size_t)h->nblk_force * P);
+  h->Wpart = c.take<double>((size_t)h->nblk_force * P);
+  if (h->potential == PIMD_POT_WATERLIKE) {
+    h->cref = c.take<double>((size_t)h->nmol * 3);
+    h->ccur = c.take<double>((size_t)h->nmol * 3);
+    h->blkmax = c.take<double>(nbr_check_blocks(h->nmol));
+    h->nbr = c.take<int>((size_t)h->nmol * kMaxNeighbours);
+    h->nnbr = c.take<int>(h->nmol);
+  }
+  h->nblk_est = (N + h->A_est - 1) / h->A_est;
+  h->est_part = c.take<double>((size_t)h->nblk_est * (2 * P + 4));
+  h->est_out = c.take<double>(3 * P + 12);
+  h->d_step = c.take<int64_t>(1);
+  h->d_err = c.take<unsigned>(4);
+}
+
+static pimd_status upload_state(pimd_handle *h, const double *x, const double *v) {
+  const size_t bytes = (size_t)h->N * 3 * h->P * sizeof(double);
+  CK(cudaMemcpyAsync(h->tmp, x, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(launch_pna_to_nap(h->tmp, h->x, h->N, h->P, h->stream));
+  if (v) {
+    CK(cudaMemcpyAsync(h->tmp, v, bytes, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_pna_to_nap(h->tmp, h->v, h->N, h->P, h->stream));
+  } else {
+    CK(launch_thermal_v(h->v, h->sigv, h->seed, h->N, h->P, h->stream));
+  }
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, double dt,
+                                   double gamma0, const pimd_params *params, void *stream,
+                                   pimd_handle **out) {
+  if (!out) return fail(PIMD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!sys) return fail(PIMD_EINVAL, "sys is NULL");
+  pimd_params prm;
+  if (params)
+    prm = *params;
+  else
+    pimd_params_default(&prm);
+  if (P < 1 || P > PIMD_MAX_BEADS) return fail(PIMD_EINVAL, "P = %d outside 1..%d", P, PIMD_MAX_BEADS);
+  if (!(T > 0.0)) return fail(PIMD_EINVAL, "T must be > 0");
+  if (!(dt > 0.0)) return fail(PIMD_EINVAL, "dt must be > 0");
+  if (sys->n_atoms <= 0) return fail(PIMD_EINVAL, "n_atoms must be > 0");
+  if (!sys->mass || !sys->pos) return fail(PIMD_EINVAL, "mass and pos are required");
+  if (sys->potential != PIMD_POT_HARMONIC && sys->potential != PIMD_POT_WATERLIKE)
+    return fail(PIMD_EINVAL, "unknown potential %d", sys->potential);
+  if (prm.thermostat != PIMD_THERMO_NONE && prm.thermostat != PIMD_THERMO_PILE_L)
+    return fail(PIMD_EINVAL, "unknown thermostat %d", prm.thermostat);
+  if (prm.integrator != PIMD_BAOAB && prm.integrator != PIMD_OBABO)
+    return fail(PIMD_EINVAL, "unknown integrator %d", prm.integrator);
+  if (prm.method != PIMD_METHOD_NMPIMD) return fail(PIMD_EINVAL, "only method nmpimd is implemented");
+  if (prm.precision != PIMD_PREC_FP64) return fail(PIMD_EINVAL, "unknown precision %d", prm.precision);
+  if (prm.fixcom != 0) return fail(PIMD_EINVAL, "fixcom is not implemented");
+  if (!(prm.sp > 0.0)) return fail(PIMD_EINVAL, "sp must be > 0");
+  if (gamma0 > 0.0) {
+    const double tau = 1.0 / gamma0;
+    if (params && std::fabs(params->tau - tau) > 1e-12 * tau)
+      return fail(PIMD_EINVAL, "gamma0 and params->tau disagree");
+    prm.tau = tau;
+  } else if (gamma0 < 0.0) {
+    return fail(PIMD_EINVAL, "gamma0 must be >= 0");
+  }
+  if (prm.thermostat == PIMD_THERMO_PILE_L && (!(prm.tau > 0.0) || !(prm.scale > 0.0)))
+    return fail(PIMD_EINVAL, "PILE_L needs tau > 0 and scale > 0");
+  const int N = sys->n_atoms;
+  for (int i = 0; i < N; ++i)
+    if (!(sys->mass[i] > 0.0)) return fail(PIMD_EINVAL, "mass[%d] must be > 0", i);
+  if (sys->potential == PIMD_POT_WATERLIKE) {
+    if (N % 3) return fail(PIMD_EINVAL, "water-like systems need 3 atoms per molecule");
+    const double rc = sys->ff[6];
+    if (!(rc > 0.0)) return fail(PIMD_EINVAL, "cutoff must be > 0");
+    for (int d = 0; d < 3; ++d)
+      if (!(sys->box[d] > 2.0 * rc))
+        return fail(PIMD_EINVAL, "box edge %d (%g) must exceed 2 rc (%g)", d, sys->box[d], 2 * rc);
+    if (!(sys->ff[0] >= 0 && sys->ff[1] > 0 && sys->ff[2] >= 0 && sys->ff[4] >= 0 && sys->ff[5] > 0))
+      return fail(PIMD_EINVAL, "invalid water-like force-field parameters");
+  }
+
+  pimd_handle *h = new pimd_handle();
+  h->N = N;
+  h->P = P;
+  h->potential = sys->potential;
+  h->nmol = sys->potential == PIMD_POT_WATERLIKE ? N / 3 : 0;
+  h->integrator = prm.integrator;
+  h->thermostat = prm.thermostat;
+  h->T = T;
+  h->dt = dt;
+  h->tau = prm.tau;
+  h->scale = prm.scale;
+  h->sp = prm.sp;
+  h->seed = prm.seed;
+  for (int d = 0; d < 3; ++d) h->box[d] = sys->box[d];
+  for (int q = 0; q < 8; ++q) h->ff[q] = sys->ff[q];
+  h->rlist = h->ff[6] + h->skin;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->alloc = g_alloc;
+  }
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return fail(PIMD_ECUDA, "cudaStreamCreate failed");
+    }
+    h->own_stream = true;
+  }
+  h->A_step = tile_atoms(N, P);
+  h->threads_step = tile_threads(h->A_step, P);
+  h->A_est = std::max(1, 256 / P);
+  h->threads_est = tile_threads(h->A_est, P);
+  const char *ng = getenv("PIMD_NO_GRAPH");
+  h->use_graph = !(ng && ng[0] == '1');
+
+  Carver c0{nullptr};
+  carve(h, c0);
+  h->arena_bytes = c0.off + 256;
+  h->arena = dev_alloc(h->alloc, h->arena_bytes, h->stream);
+  if (!h->arena) {
+    release(h);
+    return fail(PIMD_ENOMEM, "device allocation of %zu bytes failed", h->arena_bytes);
+  }
+  Carver c1{(char *)h->arena};
+  carve(h, c1);
+  if (cudaMallocHost(&h->h_est, sizeof(double) * (3 * P + 12)) != cudaSuccess ||
+      cudaMallocHost(&h->h_err, sizeof(unsigned) * 4) != cudaSuccess) {
+    release(h);
+    return fail(PIMD_ENOMEM, "pinned host allocation failed");
+  }
+
+  // ---- host tables (App. B, App. D), FP64 ----
+  std::vector<double> M, Mt((size_t)P * P), cA(P), sA(P), wsA(P), c1v(P), c2v(P), lam(P);
+  build_nm_matrix(P, M);
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) Mt[(size_t)j * P + i] = M[(size_t)i * P + j];
+  const double hbar = prm.sp * kPlanck / (2.0 * kPi);
+  h->wn = P * kBoltzmann * T / hbar;                     // Eq. (2)
+  const double tA = prm.integrator == PIMD_BAOAB ? 0.5 * dt : dt;
+  const double tO = prm.integrator == PIMD_BAOAB ? dt : 0.5 * dt;
+  for (int k = 0; k < P; ++k) {
+    const double s = std::sin(kPi * k / P);
+    lam[k] = 4.0 * s * s;                                 // Eq. (A2)
+    const double wk = 2.0 * h->wn * std::fabs(s);         // w_k = sqrt(lam_k) w_n
+    if (k == 0 || wk == 0.0) {
+      cA[k] = 1.0;
+      sA[k] = tA;
+      wsA[k] = 0.0;
+    } else {
+      cA[k] = std::cos(wk * tA);
+      sA[k] = std::sin(wk * tA) / wk;
+      wsA[k] = wk * std::sin(wk * tA);
+    }
+    const double tauk = (k == 0) ? prm.tau : prm.scale / (2.0 * wk);
+    c1v[k] = std::exp(-tO / tauk);
+    c2v[k] = std::sqrt(1.0 - c1v[k] * c1v[k]);
+  }
+  std::vector<double> inv_mm(N), sigv(N), mass_mm(N), ksp(N);
+  for (int i = 0; i < N; ++i) {
+    const double mm = sys->mass[i] * kMvv2e;
+    mass_mm[i] = mm;
+    inv_mm[i] = 1.0 / mm;
+    sigv[i] = std::sqrt(P * kBoltzmann * T / mm);
+    ksp[i] = mm * sys->ff[0] * sys->ff[0];
+  }
+  pimd_status st = PIMD_OK;
+  auto up = [&](double *dst, const std::vector<double> &src) -> pimd_status {
+    CK(cudaMemcpy(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return PIMD_OK;
+  };
+  if ((st = up(h->M, M)) || (st = up(h->Mt, Mt)) || (st = up(h->cA, cA)) || (st = up(h->sA, sA)) ||
+      (st = up(h->wsA, wsA)) || (st = up(h->c1, c1v)) || (st = up(h->c2, c2v)) ||
+      (st = up(h->lam, lam)) || (st = up(h->inv_mm, inv_mm)) || (st = up(h->sigv, sigv)) ||
+      (st = up(h->mass_mm, mass_mm)) || (st = up(h->kspring, ksp))) {
+    release(h);
+    return st;
+  }
+  auto init = [&]() -> pimd_status {
+    CK(cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
+    CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned), h->stream));
+    if (h->potential == PIMD_POT_WATERLIKE) {
+      CK(cudaMemsetAsync(h->cref, 0, sizeof(double) * 3 * h->nmol, h->stream));
+      CK(cudaMemsetAsync(h->nnbr, 0, sizeof(int) * h->nmol, h->stream));
+    }
+    pimd_status s2 = upload_state(h, sys->pos, sys->vel);
+    if (s2 != PIMD_OK) return s2;
+    s2 = enqueue_forces(h, true);
+    if (s2 != PIMD_OK) return s2;
+    return check_device_errors(h);
+  };
+  if ((st = init()) != PIMD_OK) {
+    release(h);
+    return st;
+  }
+  *out = h;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_step(pimd_handle *h, int64_t n) {
+  if (!h) return fail(PIMD_EINVAL, "handle is NULL");
+  if (n < 0) return fail(PIMD_EINVAL, "n must be >= 0");
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  if (n == 0) return PIMD_OK;
+  pimd_status st = enqueue_step(h, true);
+  if (st != PIMD_OK) return st;
+  int64_t left = n - 1;
+  if (h->use_graph && left >= 4) {
+    const int G = 8;
+    if (!h->graph) {
+      st = build_graph(h, G);
+      if (st != PIMD_OK) return st;
+    }
+    while (left >= h->graph_steps) {
+      CK(cudaGraphLaunch(h->graph, h->stream));
+      left -= h->graph_steps;
+    }
+  }
+  for (; left > 0; --left) {
+    st = enqueue_step(h, false);
+    if (st != PIMD_OK) return st;
+  }
+  st = enqueue_close(h);
+  if (st != PIMD_OK) return st;
+  h->step += n;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_sync(pimd_handle *h) {
+  if (!h) return fail(PIMD_EINVAL, "handle is NULL");
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  return check_device_errors(h);
+}
+
+extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
+  if (!h || !out) return fail(PIMD_EINVAL, "NULL argument");
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  const int P = h->P;
+  EstArgs a;
+  a.N = h->N;
+  a.P = P;
+  a.A = h->A_est;
+  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam};
+  a.mass_mm = h->mass_mm;
+  a.x = h->x;
+  a.v = h->v;
+  a.F = h->F;
+  a.wn2 = h->wn * h->wn;
+  a.part = h->est_part;
+  CK(launch_est(a, h->threads_est, h->stream));
+  EstFinalArgs f;
+  f.N = h->N;
+  f.P = P;
+  f.nblk_est = h->nblk_est;
+  f.nblk_force = h->nblk_force;
+  f.part = h->est_part;
+  f.Upart = h->Upart;
+  f.Wpart = h->Wpart;
+  f.kT = kBoltzmann * h->T;
+  f.kB = kBoltzmann;
+  f.volume = (h->potential == PIMD_POT_WATERLIKE) ? h->box[0] * h->box[1] * h->box[2] : 0.0;
+  f.out = h->est_out;
+  f.err = h->d_err;
+  CK(launch_est_final(f, h->stream));
+  CK(cudaMemcpyAsync(h->h_est, h->est_out, sizeof(double) * (3 * P + 12), cudaMemcpyDeviceToHost,
+                     h->stream));
+  pimd_status st = check_device_errors(h);
+  if (st != PIMD_OK) return st;
+  std::memset(out, 0, sizeof(*out));
+  out->step = h->step;
+  out->P = P;
+  out->N = h->N;
+  const double *e = h->h_est;
+  for (int k = 0; k < P; ++k) {
+    out->K_mode[k] = e[k];
+    out->S_mode[k] = e[P + k];
+    out->U_bead[k] = e[2 * P + k];
+  }
+  const double *g = e + 3 * P;
+  out->H = g[0];
+  out->K_PR = g[1];
+  out->K_VR = g[2];
+  out->K_CV = g[3];
+  out->P_PR = g[4];
+  out->P_MD = g[5];
+  out->P_CV = g[6];
+  out->T_ring = g[7];
+  out->volume = g[8];
+  out->vir_sum = g[9];
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_get_state(pimd_handle *h, double *x, double *v_nm, int64_t *step) {
+  if (!h) return fail(PIMD_EINVAL, "handle is NULL");
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  const size_t bytes = (size_t)h->N * 3 * h->P * sizeof(double);
+  if (x) {
+    CK(launch_nap_to_pna(h->x, h->tmp, h->N, h->P, h->stream));
+    CK(cudaMemcpyAsync(x, h->tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (v_nm) {
+    CK(launch_nap_to_pna(h->v, h->tmp, h->N, h->P, h->stream));
+    CK(cudaMemcpyAsync(v_nm, h->tmp, bytes, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (step) *step = h->step;
+  return check_device_errors(h);
+}
+
+extern "C" pimd_status pimd_set_state(pimd_handle *h, const double *x, const double *v_nm,
+                                      int64_t step) {
+  if (!h || !x || !v_nm) return fail(PIMD_EINVAL, "NULL argument");
+  if (step < 0) return fail(PIMD_EINVAL, "step must be >= 0");
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  pimd_status st = upload_state(h, x, v_nm);
+  if (st != PIMD_OK) return st;
+  h->step = step;
+  CK(cudaMemcpyAsync(h->d_step, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  st = enqueue_forces(h, true);
+  if (st != PIMD_OK) return st;
+  return check_device_errors(h);
+}

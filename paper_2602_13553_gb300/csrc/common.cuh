@@ -1,0 +1,152 @@
+// common.cuh -- device-side building blocks shared by the PIMD kernels:
+// metal-unit constants, the Philox-4x32-10 generator, the Gaussian noise of
+// the PILE_L O step, and the argument structs of every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pimd {
+
+// Metal units (A, ps, eV, amu, K).  h and mvv2e are the values printed in
+// App. C of the paper; Boltzmann's constant (not printed) is CODATA 2018.
+constexpr double kBoltzmann = 8.617333262e-5;   // eV / K
+constexpr double kPlanck = 4.135667403e-3;      // eV ps
+constexpr double kMvv2e = 1.0364269e-4;         // eV per amu A^2 / ps^2
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxBeads = 128;
+constexpr int kMaxNeighbours = 192;     // per molecule, O-O list with skin
+
+// Bits of the device error word (read back at synchronising calls).
+enum : unsigned { kErrNbrOverflow = 1u, kErrNonFinite = 2u };
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2,
+//   c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0),
+// with the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Noise streams of the counter's second word (bits 16..31).
+enum : uint32_t { kStreamO1 = 0u, kStreamO2 = 1u, kStreamInit = 2u };
+
+// Three standard normal deviates for (atom, normal mode, stream, step):
+// counter = (atom, mode | stream << 16, step lo, step hi), key = seed;
+// u = (w + 1/2) 2^-32; Box-Muller: (eta_x, eta_y) = r0 (cos, sin)(2 pi u1),
+// eta_z = r1 cos(2 pi u3), r = sqrt(-2 ln u).
+__device__ __forceinline__ void gauss3(uint64_t seed, uint32_t atom, uint32_t mode, uint32_t stream,
+                                       uint64_t step, double &e0, double &e1, double &e2) {
+  const uint4 w = philox4x32_10(
+      make_uint4(atom, (mode & 0xffffu) | (stream << 16), (uint32_t)step, (uint32_t)(step >> 32)),
+      make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const double s = 2.3283064365386962890625e-10;  // 2^-32
+  const double u0 = ((double)w.x + 0.5) * s;
+  const double u1 = ((double)w.y + 0.5) * s;
+  const double u2 = ((double)w.z + 0.5) * s;
+  const double u3 = ((double)w.w + 0.5) * s;
+  const double r0 = sqrt(-2.0 * log(u0));
+  const double r1 = sqrt(-2.0 * log(u2));
+  double sn, cs;
+  sincospi(2.0 * u1, &sn, &cs);
+  e0 = r0 * cs;
+  e1 = r0 * sn;
+  e2 = r1 * cospi(2.0 * u3);
+}
+
+// Minimum-image component (box edge L > 0; round half to even like rint).
+__device__ __forceinline__ double mic(double d, double L, double invL) {
+  return d - L * rint(d * invL);
+}
+
+// ---------------------------------------------------------------------------
+// Kernel arguments.  Device layout of x, v, F: [N][3][P] (atom, component,
+// bead/mode), i.e. every atom's P beads are contiguous per component.
+// ---------------------------------------------------------------------------
+struct ModeTables {
+  const double *M;     // [P][P]  M[k][j]  (mode k, bead j), Eq. (A1)
+  const double *Mt;    // [P][P]  Mt[j][k] = M[k][j]
+  const double *cA;    // [P] cos(w_k tA)
+  const double *sA;    // [P] sin(w_k tA)/w_k   (tA for k = 0)
+  const double *wsA;   // [P] w_k sin(w_k tA)   (0 for k = 0)
+  const double *c1;    // [P] exp(-tO / tau_k)
+  const double *c2;    // [P] sqrt(1 - c1^2)
+  const double *lam;   // [P] lambda_k (Eq. A2)
+};
+
+struct StepArgs {
+  int N, P, A;                 // atoms, beads, atoms per tile
+  ModeTables mt;
+  const double *inv_mm;        // [N] 1 / (m mvv2e)
+  const double *sigv;          // [N] sqrt(P kB T / (m mvv2e))
+  double *x;                   // [N][3][P] Cartesian positions
+  double *v;                   // [N][3][P] normal-mode velocities
+  const double *F;             // [N][3][P] Cartesian forces
+  const int64_t *step;         // device step counter (step index of this step = *step + step_off)
+  int step_off;
+  double kick;                 // B before A: h/2 (first step of a call) or h (two merged halves)
+  double half;                 // h/2
+  int integrator;              // 0 BAOAB, 1 OBABO
+  int first;                   // OBABO: 1 if no B+O of a previous step is pending
+  int thermo;                  // 1 PILE_L
+  uint64_t seed;
+};
+
+struct ForceArgs {
+  int N, P, nmol;
+  const double *x;             // [N][3][P]
+  double *F;                   // [N][3][P]
+  double *Upart, *Wpart;       // [nblk][P] per-block bead sums of U and Tr Xi
+  const double *kspring;       // harmonic: [N] m mvv2e omega^2
+  double box[3], invbox[3];
+  double kb, r0, kth, th0, eps, sig, rc;
+  const int *nbr;              // [nmol][kMaxNeighbours]
+  const int *nnbr;             // [nmol]
+};
+
+struct NbrArgs {
+  int nmol, P;
+  const double *x;             // [N][3][P]
+  double *cref;                // [nmol][3] centroids of the oxygens at the last build
+  double *blkmax;              // [nblk_check] per-block max of 2 |c - cref| + 2 max_k |x^k - c|
+  int nblk_check;
+  int *nbr, *nnbr;
+  unsigned *err;
+  double box[3], invbox[3];
+  double rlist;                // rc + skin
+  double skin;
+  int force;                   // rebuild unconditionally
+};
+
+struct EstArgs {
+  int N, P, A;
+  ModeTables mt;
+  const double *mass_mm;       // [N] m mvv2e
+  const double *x, *v, *F;
+  double wn2;                  // omega_n^2
+  double *part;                // [nblk][2P + 4]
+};
+
+struct EstFinalArgs {
+  int N, P, nblk_est, nblk_force;
+  const double *part;          // [nblk_est][2P + 4]
+  const double *Upart, *Wpart; // [nblk_force][P]
+  double kT, volume, kB;
+  double *out;                 // [3P + 12]
+  unsigned *err;
+};
+
+}  // namespace pimd
