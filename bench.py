@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 PIMD path (bead-atom-steps/s).
+
+Workload (the plain FP64 configuration): a flexible water-like box of 64
+molecules (192 atoms) in a 12.42 A periodic box, P = 32 beads, T = 300 K,
+dt = 0.5 fs, BAOAB with PILE_L, FP64.  One benchmark step is 1000 MD steps
+with the App. A estimators reduced and copied to the host every 100 steps.
+Inputs are synthetic (seeded placement, see paper_2602_13553_gb300.inputs).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank advances
+its own independent replica (different seed) with no data-path collective:
+weak scaling, replicas only.  ``--impl reference`` times the CPU oracle on the
+host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(nmol=64, L=12.42, P=32, T=300.0, dt=5e-4, md_per_step=1000, est_every=100,
+                tau=1.0)
+WORKLOAD_NAME = ("water-like box, 64 molecules (192 atoms), 12.42 A periodic, P=32 beads, "
+                 "T=300 K, dt=0.5 fs, BAOAB+PILE_L, FP64")
+METRIC = "bead-atom-steps/s"
+FP64_PEAK = 152 * 4 * 2.07e9     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def system(seed):
+    from paper_2602_13553_gb300 import inputs
+    w = WORKLOAD
+    x0, mass = inputs.water_box(w["nmol"], w["L"], w["P"], seed, jitter=0.02)
+    return x0, mass, dict(T=w["T"], dt=w["dt"], potential=1, ff=inputs.WATER_FF,
+                          box=(w["L"],) * 3, seed=seed, tau=w["tau"])
+
+
+def config(extra=None):
+    w = WORKLOAD
+    c = {"workload": WORKLOAD_NAME, "atoms": 3 * w["nmol"], "beads": w["P"],
+         "md_steps_per_bench_step": w["md_per_step"], "estimators_every": w["est_every"],
+         "l2": "flushed (512 MiB write) between timed steps; state 0.44 MB < L2",
+         "data": "synthetic"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def step_flops_per_bead_atom(P):
+    """Algorithmic FP64 flops of the fused step kernel per bead-atom: three
+    dense P-term normal-mode transforms of 3 components (18 P), the merged
+    kick (6), two exact rotations (36) and the O update (9); the Box-Muller
+    noise is not counted."""
+    return 18 * P + 51
+
+
+def force_flops(x, L, rc, rlist):
+    """Algorithmic FP64 flops of one water force launch (all beads) for the
+    positions x [P][N][3]: per molecule and bead, 17 per neighbour-list
+    candidate (minimum-image distance), 19 more per O-O pair inside rc
+    (Lennard-Jones force, energy, virial), 120 for the two bonds and the
+    angle.  Candidates are pairs with centroid distance < rc + skin."""
+    P = x.shape[0]
+    O = x[:, 0::3, :]
+    nmol = O.shape[1]
+    cen = O.mean(axis=0)
+    d = cen[None, :, :] - cen[:, None, :]
+    d -= L * np.rint(d / L)
+    cand = (np.einsum("ijk,ijk->ij", d, d) < rlist * rlist).sum() - nmol
+    inside = 0
+    for k in range(P):
+        e = O[k][None, :, :] - O[k][:, None, :]
+        e -= L * np.rint(e / L)
+        inside += (np.einsum("ijk,ijk->ij", e, e) < rc * rc).sum() - nmol
+    return 17.0 * cand * P + 19.0 * inside + 120.0 * nmol * P
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        t = json.load(open(path)).get(kernel)
+        src = os.path.join(ROOT, "paper_2602_13553_gb300", "csrc", t["source"])
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != t["source_sha256_16"]:
+            return None
+        return float(t["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(target_s=12.0):
+    """The CPU oracle as it stands, on the host cores, on a bounded sample of
+    the same workload (MD steps of the same system, estimators every 100)."""
+    import oracle
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    x0, mass, kw = system(1)
+    sim = oracle.Sim(x0, mass, **kw)
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    sim.run(20)
+    probe = time.perf_counter() - t0
+    n = int(max(20, min(5000, target_s / max(probe / 20, 1e-6))))
+    n = max(100, (n // 100) * 100)
+    t0 = time.perf_counter()
+    done = 0
+    while done < n:
+        sim.run(w["est_every"])
+        sim.estimators()
+        done += w["est_every"]
+    dt = time.perf_counter() - t0
+    value = 3 * w["nmol"] * w["P"] * n / dt
+    return {"value": value, "unit": METRIC, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": "%d MD steps (estimators every 100) of the same 192-atom x 32-bead system, "
+                      "%.1f s wall" % (n, dt)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    w = WORKLOAD
+    x0, mass, kw = system(1)
+    sim = oracle.Sim(x0, mass, **kw)
+    per = w["est_every"]                 # each reference step: 100 MD steps + estimators
+    for _ in range(args.warmup):
+        sim.run(per)
+        sim.estimators()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.run(per)
+        sim.estimators()
+    dt = time.perf_counter() - t0
+    value = 3 * w["nmol"] * w["P"] * per * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"reference_step": "%d MD steps + estimators (bounded sample of the "
+                              "1000-step benchmark step)" % per}),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": "%d x %d MD steps of the benchmark system" % (args.steps, per)},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2602_13553_gb300 import binding, build
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    build.build()
+    w = WORKLOAD
+    seed = 1 + rank
+    x0, mass, kw = system(seed)
+    stream = torch.cuda.Stream()
+    binding.use_torch_allocator()
+    sim = binding.Simulation(x0, mass, stream=stream.cuda_stream, **kw)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    nchunks = w["md_per_step"] // w["est_every"]
+
+    def bench_step():
+        for _ in range(nchunks):
+            sim.step(w["est_every"])
+            sim.estimators()
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(rank & 0xff)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        flush_l2()
+        bench_step()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = sim.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush_l2()
+        ev[i][0].record(stream)
+        bench_step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = sim.kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_rank = 3 * w["nmol"] * w["P"] * w["md_per_step"] * args.steps
+    value = world * units_per_rank / (total_ms / 1e3)
+
+    # --- per-kernel device durations (CUDA events around every launch) -----
+    ksteps = min(args.steps, 10)
+    sim.set_kernel_timing(True)
+    for _ in range(ksteps):
+        flush_l2()
+        bench_step()
+    kt = sim.kernel_times()
+    sim.set_kernel_timing(False)
+    xs, _, _ = sim.get_state()
+
+    # --- end to end through the C ABI with pinned host buffers -------------
+    xh = torch.empty(x0.shape, dtype=torch.float64, pin_memory=True)
+    vh = torch.empty(x0.shape, dtype=torch.float64, pin_memory=True)
+    xa, va, st0 = sim.get_state()
+    xh.numpy()[:] = xa
+    vh.numpy()[:] = va
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state(xh.numpy(), vh.numpy(), st0)
+        bench_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * 3 * w["nmol"] * w["P"] * w["md_per_step"] * e2e_steps / e2e_s
+    P, N = w["P"], 3 * w["nmol"]
+    h2d = 2 * P * N * 3 * 8
+    d2h = nchunks * ((3 * P + 12) * 8 + 4)
+
+    if rank != 0:
+        return 0
+    # dominant kernel and its roofline
+    dom = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
+    share = {k: round(kt[k][0] / max(1e-12, sum(v[0] for v in kt.values())), 4) for k in kt}
+    from paper_2602_13553_gb300 import inputs
+    rc = inputs.WATER_FF[6]
+    if dom == "force":
+        flops = force_flops(xs, w["L"], rc, rc + 1.5)
+        kname = "k_force_water_f64"
+    else:
+        flops = step_flops_per_bead_atom(P) * N * P
+        kname = "k_step_f64" if dom == "step" else dom
+    avg_ms = kt[dom][0] / kt[dom][1]
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    peak = FP64_PEAK / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config({"parallelism": "replicas" if world > 1 else "single"}),
+        "roofline": {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic_for(kname),
+                     "peak_source": "FP64: 152 SMs x 4 flop/clk x 2.07 GHz (GB300 has no fast FP64)",
+                     "avg_launch_ms": avg_ms, "kernel_time_share": share},
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "path": "pimd_set_state (pinned host x, v) + 10 x (pimd_step(100) + pimd_estimators)"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    sim.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

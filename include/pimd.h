@@ -210,6 +210,35 @@ pimd_status pimd_set_state(pimd_handle *h, const double *x, const double *v_nm, 
 /* Release the handle and its device memory (waits for its queued work). */
 void pimd_destroy(pimd_handle *h);
 
+/* ---- measurement ---------------------------------------------------------
+ * Kernel kinds of one step: the fused normal-mode step, the bead-batched
+ * force kernel, the neighbour-list check+build pair, the closing half-kick,
+ * the two estimator passes, and bookkeeping (step counter). */
+enum {
+  PIMD_KIND_STEP = 0,
+  PIMD_KIND_FORCE = 1,
+  PIMD_KIND_NBR = 2,
+  PIMD_KIND_CLOSE = 3,
+  PIMD_KIND_EST = 4,
+  PIMD_KIND_OTHER = 5,
+  PIMD_NKINDS = 6
+};
+
+/* Enable (1) or disable (0) per-launch timing and reset its accumulators.
+ * While enabled, pimd_step launches every kernel individually (no graph
+ * replay) and brackets each launch with CUDA events on the handle's stream,
+ * so the results are per-kernel device durations. */
+pimd_status pimd_set_kernel_timing(pimd_handle *h, int enable);
+
+/* Accumulated milliseconds and launch counts per kind (arrays of
+ * PIMD_NKINDS, either may be NULL) since the last pimd_set_kernel_timing.
+ * Synchronises the handle's stream. */
+pimd_status pimd_kernel_times(pimd_handle *h, double *ms, int64_t *launches);
+
+/* Number of this library's kernels the handle has enqueued so far (nodes of
+ * replayed CUDA graphs included); -1 for a NULL handle. */
+int64_t pimd_kernel_launches(const pimd_handle *h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,7 +83,9 @@ class Estimates(ctypes.Structure):
 # every symbol include/pimd.h declares (checked by the CPU tests)
 EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "pimd_last_error",
            "pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
-           "pimd_set_state", "pimd_destroy")
+           "pimd_set_state", "pimd_destroy", "pimd_set_kernel_timing", "pimd_kernel_times",
+           "pimd_kernel_launches")
+KINDS = ("step", "force", "nbr", "close", "est", "other")
 
 _lock = threading.Lock()
 _lib = None
@@ -121,6 +123,12 @@ def lib():
         L.pimd_set_state.argtypes = [vp, dp, dp, ctypes.c_int64]
         L.pimd_destroy.argtypes = [vp]
         L.pimd_destroy.restype = None
+        L.pimd_set_kernel_timing.argtypes = [vp, ctypes.c_int]
+        L.pimd_set_kernel_timing.restype = ctypes.c_int
+        L.pimd_kernel_times.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
+        L.pimd_kernel_times.restype = ctypes.c_int
+        L.pimd_kernel_launches.argtypes = [vp]
+        L.pimd_kernel_launches.restype = ctypes.c_int64
         for f in ("pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
                   "pimd_set_state"):
             getattr(L, f).restype = ctypes.c_int
@@ -232,6 +240,18 @@ class Simulation:
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         check(lib().pimd_set_state(self._h, _dp(x), _dp(v), int(step)))
+
+    def set_kernel_timing(self, enable: bool) -> None:
+        check(lib().pimd_set_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self) -> dict:
+        ms = (ctypes.c_double * len(KINDS))()
+        n = (ctypes.c_int64 * len(KINDS))()
+        check(lib().pimd_kernel_times(self._h, ms, n))
+        return {k: (ms[i], int(n[i])) for i, k in enumerate(KINDS)}
+
+    def kernel_launches(self) -> int:
+        return int(lib().pimd_kernel_launches(self._h))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

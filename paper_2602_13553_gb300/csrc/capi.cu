@@ -149,8 +149,56 @@ struct pimd_handle {
   // steady-state step graph (kick = h, no pending first step)
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  int64_t graph_kernels = 0;
   bool use_graph = true;
+  bool capturing = false;
+  // accounting: kernels enqueued (graph nodes included) and, when enabled,
+  // CUDA-event timing of every launch by kind
+  int64_t launches = 0;
+  bool timing = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  double t_ms[PIMD_NKINDS] = {0};
+  int64_t t_n[PIMD_NKINDS] = {0};
 };
+
+static pimd_status flush_timing(pimd_handle *h) {
+  if (h->pending.empty()) return PIMD_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto &p : h->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+    h->t_ms[p.first] += ms;
+    h->t_n[p.first] += 1;
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  h->pending.clear();
+  return PIMD_OK;
+}
+
+// Enqueue `nk` kernels of one kind through `fn`, counting them and, in timing
+// mode, bracketing them with events on the handle's stream.
+template <class Fn>
+static pimd_status enqueue(pimd_handle *h, int kind, int nk, Fn &&fn) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool t = h->timing && !h->capturing;
+  if (t) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, h->stream));
+  }
+  CK(fn());
+  if (t) {
+    CK(cudaEventRecord(e1, h->stream));
+    h->pending.push_back({kind, {e0, e1}});
+    if (h->pending.size() >= 4096) {
+      pimd_status st = flush_timing(h);
+      if (st != PIMD_OK) return st;
+    }
+  }
+  h->launches += nk;
+  return PIMD_OK;
+}
 
 static void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s) {
   if (a.alloc) return a.alloc(bytes, (void *)s, a.ctx);
@@ -273,12 +321,13 @@ static NbrArgs nbr_args(pimd_handle *h, bool force) {
 // Forces of the current positions (and the neighbour list they need).
 static pimd_status enqueue_forces(pimd_handle *h, bool force_rebuild) {
   if (h->potential == PIMD_POT_WATERLIKE) {
-    CK(launch_nbr(nbr_args(h, force_rebuild), h->ccur, h->stream));
-    CK(launch_force_water(force_args(h), h->stream));
-  } else {
-    CK(launch_force_harmonic(force_args(h), h->stream));
+    pimd_status st = enqueue(h, PIMD_KIND_NBR, 2, [&] {
+      return launch_nbr(nbr_args(h, force_rebuild), h->ccur, h->stream);
+    });
+    if (st != PIMD_OK) return st;
+    return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_water(force_args(h), h->stream); });
   }
-  return PIMD_OK;
+  return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_harmonic(force_args(h), h->stream); });
 }
 
 // One full step: the fused integrator kernel, the forces of the new
@@ -287,25 +336,29 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
   StepArgs a = step_args(h);
   a.first = first ? 1 : 0;
   a.kick = first ? 0.5 * h->dt : h->dt;
-  CK(launch_step(a, h->threads_step, h->stream));
-  pimd_status st = enqueue_forces(h, false);
+  pimd_status st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a, h->threads_step, h->stream); });
   if (st != PIMD_OK) return st;
-  CK(launch_advance(h->d_step, 1, h->stream));
-  return PIMD_OK;
+  st = enqueue_forces(h, false);
+  if (st != PIMD_OK) return st;
+  return enqueue(h, PIMD_KIND_OTHER, 1, [&] { return launch_advance(h->d_step, 1, h->stream); });
 }
 
 static pimd_status enqueue_close(pimd_handle *h) {
   StepArgs a = step_args(h);
   a.step_off = -1;
-  CK(launch_close(a, h->threads_step, h->stream));
-  return PIMD_OK;
+  return enqueue(h, PIMD_KIND_CLOSE, 1, [&] { return launch_close(a, h->threads_step, h->stream); });
 }
 
 static pimd_status build_graph(pimd_handle *h, int nsteps) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  const int64_t before = h->launches;
   pimd_status st = PIMD_OK;
   for (int s = 0; s < nsteps && st == PIMD_OK; ++s) st = enqueue_step(h, false);
+  h->capturing = false;
+  h->graph_kernels = h->launches - before;
+  h->launches = before;
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   if (st != PIMD_OK) {
     if (g) cudaGraphDestroy(g);
@@ -341,6 +394,10 @@ static pimd_status check_device_errors(pimd_handle *h) {
 static void release(pimd_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto &p : h->pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
   if (h->graph) cudaGraphExecDestroy(h->graph);
   dev_free(h->alloc, h->arena, h->stream);
   if (h->h_est) cudaFreeHost(h->h_est);
@@ -590,7 +647,7 @@ extern "C" pimd_status pimd_step(pimd_handle *h, int64_t n) {
   pimd_status st = enqueue_step(h, true);
   if (st != PIMD_OK) return st;
   int64_t left = n - 1;
-  if (h->use_graph && left >= 4) {
+  if (h->use_graph && !h->timing && left >= 4) {
     const int G = 8;
     if (!h->graph) {
       st = build_graph(h, G);
@@ -598,6 +655,7 @@ extern "C" pimd_status pimd_step(pimd_handle *h, int64_t n) {
     }
     while (left >= h->graph_steps) {
       CK(cudaGraphLaunch(h->graph, h->stream));
+      h->launches += h->graph_kernels;
       left -= h->graph_steps;
     }
   }
@@ -632,7 +690,8 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   a.F = h->F;
   a.wn2 = h->wn * h->wn;
   a.part = h->est_part;
-  CK(launch_est(a, h->threads_est, h->stream));
+  pimd_status st0 = enqueue(h, PIMD_KIND_EST, 1, [&] { return launch_est(a, h->threads_est, h->stream); });
+  if (st0 != PIMD_OK) return st0;
   EstFinalArgs f;
   f.N = h->N;
   f.P = P;
@@ -646,7 +705,8 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   f.volume = (h->potential == PIMD_POT_WATERLIKE) ? h->box[0] * h->box[1] * h->box[2] : 0.0;
   f.out = h->est_out;
   f.err = h->d_err;
-  CK(launch_est_final(f, h->stream));
+  st0 = enqueue(h, PIMD_KIND_EST, 1, [&] { return launch_est_final(f, h->stream); });
+  if (st0 != PIMD_OK) return st0;
   CK(cudaMemcpyAsync(h->h_est, h->est_out, sizeof(double) * (3 * P + 12), cudaMemcpyDeviceToHost,
                      h->stream));
   pimd_status st = check_device_errors(h);
@@ -704,3 +764,28 @@ extern "C" pimd_status pimd_set_state(pimd_handle *h, const double *x, const dou
   if (st != PIMD_OK) return st;
   return check_device_errors(h);
 }
+
+extern "C" pimd_status pimd_set_kernel_timing(pimd_handle *h, int enable) {
+  if (!h) return fail(PIMD_EINVAL, "handle is NULL");
+  pimd_status st = flush_timing(h);
+  if (st != PIMD_OK) return st;
+  for (int k = 0; k < PIMD_NKINDS; ++k) {
+    h->t_ms[k] = 0.0;
+    h->t_n[k] = 0;
+  }
+  h->timing = enable != 0;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_kernel_times(pimd_handle *h, double *ms, int64_t *launches) {
+  if (!h) return fail(PIMD_EINVAL, "handle is NULL");
+  pimd_status st = flush_timing(h);
+  if (st != PIMD_OK) return st;
+  for (int k = 0; k < PIMD_NKINDS; ++k) {
+    if (ms) ms[k] = h->t_ms[k];
+    if (launches) launches[k] = h->t_n[k];
+  }
+  return PIMD_OK;
+}
+
+extern "C" int64_t pimd_kernel_launches(const pimd_handle *h) { return h ? h->launches : -1; }
