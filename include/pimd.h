@@ -239,6 +239,36 @@ pimd_status pimd_kernel_times(pimd_handle *h, double *ms, int64_t *launches);
  * replayed CUDA graphs included); -1 for a NULL handle. */
 int64_t pimd_kernel_launches(const pimd_handle *h);
 
+/* ---- estimators without any allocation -----------------------------------
+ * The paper has no counterpart to this entry point.  It computes the same
+ * App. A outputs as pimd_estimators, but for a state held in the caller's
+ * own device buffers and without allocating any memory: no cudaMalloc, no
+ * cudaFree, no pinned or host heap allocation.  It exists for callers that
+ * cannot let a library allocate device memory: a host application that owns
+ * a fixed device pool reserved at start-up, or a time-stepping loop in which
+ * an allocation would synchronise the device and stall its other streams.
+ * Every intermediate lives in one statically sized device array of 1 MiB
+ * inside this library; every GPU that loads the library holds it until the
+ * process exits.
+ *   x, v_nm, F  device arrays [P][N][3]: Cartesian positions (A), normal-mode
+ *               velocities at integer time (A/ps), Cartesian forces (eV/A)
+ *   mass        device [N] (amu);  U_bead device [P] (eV), bead energies
+ *   vir_sum     sum_k Tr Xi^(k) (eV);  volume in A^3, 0 for no box (NaN
+ *               pressures);  T (K) and sp as at pimd_create
+ *   stream      cudaStream_t the kernels run on; the call synchronises it
+ *   out         host struct; step is set to 0
+ * Limits: 1 <= P <= 128 and 1 <= N with 3 N P < 2^31; other sizes are
+ * EINVAL.  The array is shared by every call on a device and keeps the last
+ * call's contents; each call rewrites all it reads, but calls whose kernels
+ * overlap on one GPU race and must be serialised by the caller.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. */
+pimd_status pimd_estimators_noalloc(int32_t N, int32_t P, double T, double sp, double volume,
+                                    const double *x, const double *v_nm, const double *F,
+                                    const double *mass, const double *U_bead, double vir_sum,
+                                    void *stream, pimd_estimates *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,7 +84,7 @@ class Estimates(ctypes.Structure):
 EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "pimd_last_error",
            "pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
            "pimd_set_state", "pimd_destroy", "pimd_set_kernel_timing", "pimd_kernel_times",
-           "pimd_kernel_launches")
+           "pimd_kernel_launches", "pimd_estimators_noalloc")
 KINDS = ("step", "force", "nbr", "close", "est", "other")
 
 _lock = threading.Lock()

@@ -61,6 +61,10 @@ static pimd_status fail(pimd_status s, const char *fmt, ...) {
 
 extern "C" const char *pimd_last_error(void) { return g_err; }
 
+namespace pimd {
+void set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace pimd
+
 extern "C" const char *pimd_status_string(pimd_status s) {
   switch (s) {
     case PIMD_OK: return "ok";
