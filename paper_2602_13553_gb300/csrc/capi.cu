@@ -23,17 +23,19 @@ size_t est_smem_bytes(int A, int P);
 cudaError_t launch_step(const StepArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_close(const StepArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_advance(int64_t *step, int n, cudaStream_t s);
+cudaError_t launch_to_f32(const double *src, float *dst, size_t n, cudaStream_t s);
 cudaError_t launch_thermal_v(double *v, const double *sigv, uint64_t seed, int N, int P,
                              cudaStream_t s);
 cudaError_t launch_pna_to_nap(const double *src, double *dst, int N, int P, cudaStream_t s);
 cudaError_t launch_nap_to_pna(const double *src, double *dst, int N, int P, cudaStream_t s);
 cudaError_t launch_force_harmonic(const ForceArgs &a, cudaStream_t s);
 cudaError_t launch_force_water(const ForceArgs &a, cudaStream_t s);
-cudaError_t launch_nbr(const NbrArgs &a, double *ccur, cudaStream_t s);
+cudaError_t launch_nbr_build(const NbrArgs &a, const double *ccur, cudaStream_t s);
+cudaError_t launch_centroids(const NbrArgs &a, double *ccur, cudaStream_t s);
 cudaError_t launch_est(const EstArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_est_final(const EstFinalArgs &a, cudaStream_t s);
 int force_blocks(int n_groups, int P);
-int nbr_check_blocks(int nmol);
+int water_lane_groups(int P);
 }  // namespace pimd
 
 using namespace pimd;
@@ -129,13 +131,15 @@ struct pimd_handle {
   size_t arena_bytes = 0;
   // device state, layout [N][3][P]
   double *x = nullptr, *v = nullptr, *F = nullptr, *tmp = nullptr;
+  float *x32 = nullptr;   // FP32 copy of x (water-like: the force kernel's cutoff prefilter)
   double *inv_mm = nullptr, *sigv = nullptr, *mass_mm = nullptr, *kspring = nullptr;
   double *M = nullptr, *Mt = nullptr, *cA = nullptr, *sA = nullptr, *wsA = nullptr;
   double *c1 = nullptr, *c2 = nullptr, *lam = nullptr;
   double *Upart = nullptr, *Wpart = nullptr;
   int nblk_force = 0;
   double *cref = nullptr, *ccur = nullptr, *blkmax = nullptr;
-  int *nbr = nullptr, *nnbr = nullptr;
+  int *nbr = nullptr, *nbr_off = nullptr;
+  int nbr_groups = 1;
   double *est_part = nullptr, *est_out = nullptr;
   int nblk_est = 0;
   int64_t *d_step = nullptr;
@@ -242,13 +246,21 @@ static void build_nm_matrix(int P, std::vector<double> &M) {
     }
 }
 
+// Step-kernel tiles: one thread per (atom, component, mode) task, up to 256
+// tasks per block; small systems use small tiles so that the grid still
+// covers the 152 SMs twice where the atom count allows.
 static int tile_atoms(int N, int P) {
-  const int amax = std::max(1, 256 / P);
-  const int want = (N + 303) / 304;   // >= 2 tiles per SM on 152 SMs while possible
+  const int amax = std::max(1, 256 / (3 * P));
+  const int want = (N + 303) / 304;
   return std::min(amax, std::max(1, want));
 }
 
 static int tile_threads(int A, int P) {
+  int t = ((3 * A * P + 31) / 32) * 32;
+  return std::min(256, std::max(32, t));
+}
+
+static int est_threads(int A, int P) {
   int t = ((A * P + 31) / 32) * 32;
   return std::min(256, std::max(32, t));
 }
@@ -266,6 +278,11 @@ static StepArgs step_args(pimd_handle *h) {
   a.F = h->F;
   a.step = h->d_step;
   a.step_off = 0;
+  const bool water = h->potential == PIMD_POT_WATERLIKE;
+  a.x32 = water ? h->x32 : nullptr;
+  a.cref = water ? h->cref : nullptr;
+  a.ccur = water ? h->ccur : nullptr;
+  a.blkmax = water ? h->blkmax : nullptr;
   a.kick = h->dt;
   a.half = 0.5 * h->dt;
   a.integrator = h->integrator;
@@ -281,6 +298,8 @@ static ForceArgs force_args(pimd_handle *h) {
   a.P = h->P;
   a.nmol = h->nmol;
   a.x = h->x;
+  a.x32 = h->x32;
+  a.step_inc = nullptr;
   a.F = h->F;
   a.Upart = h->Upart;
   a.Wpart = h->Wpart;
@@ -297,7 +316,8 @@ static ForceArgs force_args(pimd_handle *h) {
   a.sig = h->ff[5];
   a.rc = h->ff[6];
   a.nbr = h->nbr;
-  a.nnbr = h->nnbr;
+  a.nbr_off = h->nbr_off;
+  a.nbr_groups = h->nbr_groups;
   return a;
 }
 
@@ -308,9 +328,10 @@ static NbrArgs nbr_args(pimd_handle *h, bool force) {
   a.x = h->x;
   a.cref = h->cref;
   a.blkmax = h->blkmax;
-  a.nblk_check = nbr_check_blocks(h->nmol);
+  a.nblk_check = (h->N + h->A_step - 1) / h->A_step;
   a.nbr = h->nbr;
-  a.nnbr = h->nnbr;
+  a.nbr_off = h->nbr_off;
+  a.nbr_groups = h->nbr_groups;
   a.err = h->d_err;
   for (int d = 0; d < 3; ++d) {
     a.box[d] = h->box[d];
@@ -323,15 +344,29 @@ static NbrArgs nbr_args(pimd_handle *h, bool force) {
 }
 
 // Forces of the current positions (and the neighbour list they need).
-static pimd_status enqueue_forces(pimd_handle *h, bool force_rebuild) {
+// from_outside: the positions were not written by the step kernel (create,
+// set_state), so the centroids are recomputed and the list rebuilt.
+// advance: the force kernel also advances the device step counter.
+static pimd_status enqueue_forces(pimd_handle *h, bool from_outside, bool advance) {
+  ForceArgs fa = force_args(h);
+  fa.step_inc = advance ? h->d_step : nullptr;
   if (h->potential == PIMD_POT_WATERLIKE) {
-    pimd_status st = enqueue(h, PIMD_KIND_NBR, 2, [&] {
-      return launch_nbr(nbr_args(h, force_rebuild), h->ccur, h->stream);
+    pimd_status st;
+    if (from_outside) {
+      st = enqueue(h, PIMD_KIND_OTHER, 2, [&] {
+        cudaError_t e = launch_to_f32(h->x, h->x32, (size_t)h->N * 3 * h->P, h->stream);
+        if (e != cudaSuccess) return e;
+        return launch_centroids(nbr_args(h, true), h->ccur, h->stream);
+      });
+      if (st != PIMD_OK) return st;
+    }
+    st = enqueue(h, PIMD_KIND_NBR, 1, [&] {
+      return launch_nbr_build(nbr_args(h, from_outside), h->ccur, h->stream);
     });
     if (st != PIMD_OK) return st;
-    return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_water(force_args(h), h->stream); });
+    return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_water(fa, h->stream); });
   }
-  return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_harmonic(force_args(h), h->stream); });
+  return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_harmonic(fa, h->stream); });
 }
 
 // One full step: the fused integrator kernel, the forces of the new
@@ -342,9 +377,7 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
   a.kick = first ? 0.5 * h->dt : h->dt;
   pimd_status st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a, h->threads_step, h->stream); });
   if (st != PIMD_OK) return st;
-  st = enqueue_forces(h, false);
-  if (st != PIMD_OK) return st;
-  return enqueue(h, PIMD_KIND_OTHER, 1, [&] { return launch_advance(h->d_step, 1, h->stream); });
+  return enqueue_forces(h, false, true);
 }
 
 static pimd_status enqueue_close(pimd_handle *h) {
@@ -431,6 +464,7 @@ static void carve(pimd_handle *h, Carver &c) {
   h->v = c.take<double>(len);
   h->F = c.take<double>(len);
   h->tmp = c.take<double>(len);
+  if (h->potential == PIMD_POT_WATERLIKE) h->x32 = c.take<float>(len);
   h->inv_mm = c.take<double>(N);
   h->sigv = c.take<double>(N);
   h->mass_mm = c.take<double>(N);
@@ -443,16 +477,17 @@ static void carve(pimd_handle *h, Carver &c) {
   h->c1 = c.take<double>(P);
   h->c2 = c.take<double>(P);
   h->lam = c.take<double>(P);
-  const int groups = h->potential == PIMD_POT_WATERLIKE ? h->nmol : h->N;
-  h->nblk_force = force_blocks(groups, P);
+  // rows of per-bead U / Tr Xi sums: one per molecule (water) or per block
+  h->nblk_force = h->potential == PIMD_POT_WATERLIKE ? h->nmol : force_blocks(h->N, P);
   h->Upart = c.take<double>((size_t)h->nblk_force * P);
   h->Wpart = c.take<double>((size_t)h->nblk_force * P);
   if (h->potential == PIMD_POT_WATERLIKE) {
     h->cref = c.take<double>((size_t)h->nmol * 3);
     h->ccur = c.take<double>((size_t)h->nmol * 3);
-    h->blkmax = c.take<double>(nbr_check_blocks(h->nmol));
+    h->blkmax = c.take<double>(2 * ((N + h->A_step - 1) / h->A_step));
     h->nbr = c.take<int>((size_t)h->nmol * kMaxNeighbours);
-    h->nnbr = c.take<int>(h->nmol);
+    h->nbr_groups = water_lane_groups(P);
+    h->nbr_off = c.take<int>((size_t)h->nmol * (kLJWarps * h->nbr_groups + 1));
   }
   h->nblk_est = (N + h->A_est - 1) / h->A_est;
   h->est_part = c.take<double>((size_t)h->nblk_est * (2 * P + 4));
@@ -556,7 +591,7 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   h->A_step = tile_atoms(N, P);
   h->threads_step = tile_threads(h->A_step, P);
   h->A_est = std::max(1, 256 / P);
-  h->threads_est = tile_threads(h->A_est, P);
+  h->threads_est = est_threads(h->A_est, P);
   const char *ng = getenv("PIMD_NO_GRAPH");
   h->use_graph = !(ng && ng[0] == '1');
 
@@ -627,11 +662,12 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
     CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned), h->stream));
     if (h->potential == PIMD_POT_WATERLIKE) {
       CK(cudaMemsetAsync(h->cref, 0, sizeof(double) * 3 * h->nmol, h->stream));
-      CK(cudaMemsetAsync(h->nnbr, 0, sizeof(int) * h->nmol, h->stream));
+      CK(cudaMemsetAsync(h->nbr_off, 0,
+                         sizeof(int) * h->nmol * (kLJWarps * h->nbr_groups + 1), h->stream));
     }
     pimd_status s2 = upload_state(h, sys->pos, sys->vel);
     if (s2 != PIMD_OK) return s2;
-    s2 = enqueue_forces(h, true);
+    s2 = enqueue_forces(h, true, false);
     if (s2 != PIMD_OK) return s2;
     return check_device_errors(h);
   };
@@ -764,7 +800,7 @@ extern "C" pimd_status pimd_set_state(pimd_handle *h, const double *x, const dou
   if (st != PIMD_OK) return st;
   h->step = step;
   CK(cudaMemcpyAsync(h->d_step, &h->step, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
-  st = enqueue_forces(h, true);
+  st = enqueue_forces(h, true, false);
   if (st != PIMD_OK) return st;
   return check_device_errors(h);
 }

@@ -17,6 +17,8 @@ constexpr double kPi = 3.14159265358979323846;
 
 constexpr int kMaxBeads = 128;
 constexpr int kMaxNeighbours = 192;     // per molecule, O-O list with skin
+constexpr int kLJWarps = 14;            // warps sharing one molecule's O-O neighbour list
+constexpr int kMaxBuckets = 112;        // kLJWarps * max lane groups (8)
 
 // Bits of the device error word (read back at synchronising calls).
 enum : unsigned { kErrNbrOverflow = 1u, kErrNonFinite = 2u };
@@ -67,6 +69,21 @@ __device__ __forceinline__ void gauss3(uint64_t seed, uint32_t atom, uint32_t mo
   e2 = r1 * cospi(2.0 * u3);
 }
 
+// One standard normal deviate of the triple above (component d = 0, 1, 2),
+// computed on its own so that one thread per component needs no exchange.
+__device__ __forceinline__ double gauss1(uint64_t seed, uint32_t atom, uint32_t mode, uint32_t stream,
+                                         uint64_t step, int d) {
+  const uint4 w = philox4x32_10(
+      make_uint4(atom, (mode & 0xffffu) | (stream << 16), (uint32_t)step, (uint32_t)(step >> 32)),
+      make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const double s = 2.3283064365386962890625e-10;  // 2^-32
+  const uint32_t wa = d < 2 ? w.x : w.z;
+  const uint32_t wb = d < 2 ? w.y : w.w;
+  const double r = sqrt(-2.0 * log(((double)wa + 0.5) * s));
+  const double ang = 2.0 * (((double)wb + 0.5) * s);
+  return r * (d == 1 ? sinpi(ang) : cospi(ang));
+}
+
 // Minimum-image component (box edge L > 0; round half to even like rint).
 __device__ __forceinline__ double mic(double d, double L, double invL) {
   return d - L * rint(d * invL);
@@ -97,6 +114,11 @@ struct StepArgs {
   const double *F;             // [N][3][P] Cartesian forces
   const int64_t *step;         // device step counter (step index of this step = *step + step_off)
   int step_off;
+  float *x32;                  // [N][3][P] FP32 copy of x for the force kernel's cutoff prefilter, or null
+  // water-like systems: neighbour-list skin check of the oxygens (atoms 3m)
+  const double *cref;          // [nmol][3] centroids at the last list build, or null
+  double *ccur;                // [nmol][3] current centroids (written)
+  double *blkmax;              // [gridDim.x][2] per-block max |c - cref| and max_k |x^k - c|
   double kick;                 // B before A: h/2 (first step of a call) or h (two merged halves)
   double half;                 // h/2
   int integrator;              // 0 BAOAB, 1 OBABO
@@ -108,22 +130,26 @@ struct StepArgs {
 struct ForceArgs {
   int N, P, nmol;
   const double *x;             // [N][3][P]
+  const float *x32;            // [N][3][P] FP32 copy of x (water prefilter)
+  int64_t *step_inc;           // if not null, block 0 advances the step counter by one
   double *F;                   // [N][3][P]
-  double *Upart, *Wpart;       // [nblk][P] per-block bead sums of U and Tr Xi
+  double *Upart, *Wpart;       // [rows][P] bead sums of U and Tr Xi (rows: blocks or molecules)
   const double *kspring;       // harmonic: [N] m mvv2e omega^2
   double box[3], invbox[3];
   double kb, r0, kth, th0, eps, sig, rc;
-  const int *nbr;              // [nmol][kMaxNeighbours]
-  const int *nnbr;             // [nmol]
+  const int *nbr;              // [nmol][kMaxNeighbours] neighbours grouped by bucket j mod NS
+  const int *nbr_off;          // [nmol][NS + 1] bucket offsets into the molecule's row
+  int nbr_groups;              // G: lane groups per warp; NS = kLJWarps * G buckets
 };
 
 struct NbrArgs {
   int nmol, P;
   const double *x;             // [N][3][P]
   double *cref;                // [nmol][3] centroids of the oxygens at the last build
-  double *blkmax;              // [nblk_check] per-block max of 2 |c - cref| + 2 max_k |x^k - c|
+  const double *blkmax;        // [nblk_check][2] per-block max |c - cref|, max_k |x^k - c|
   int nblk_check;
-  int *nbr, *nnbr;
+  int *nbr, *nbr_off;
+  int nbr_groups;
   unsigned *err;
   double box[3], invbox[3];
   double rlist;                // rc + skin

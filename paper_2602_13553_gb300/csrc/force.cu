@@ -4,14 +4,17 @@
 // estimators of App. A need.
 //
 // Harmonic well: thread (atom i, bead k), F = -m mvv2e w^2 x.
-// Water-like model: thread (molecule m, bead k); the P beads of one molecule
-// sit in adjacent lanes, so each lane's gather of a neighbour's bead is a
-// contiguous segment of that neighbour's bead row.  Bonds and the angle of the
-// molecule are evaluated in place; O-O Lennard-Jones runs over a centroid
-// neighbour list (cutoff + skin) shared by all beads.  Each molecule sums its
-// full neighbour list in index order (no atomics), so forces are
+// Water-like model: one block per (molecule, chunk of beads); the beads of the
+// chunk sit in adjacent lanes, so each lane's gather of a neighbour's bead is
+// a contiguous segment of that neighbour's bead row.  O-O Lennard-Jones runs
+// over a centroid neighbour list (cutoff + skin) shared by all beads.  Each
+// molecule sums its full neighbour list (no atomics), so forces are
 // deterministic and independent of what else is on the GPU.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pimd {
 
@@ -55,162 +58,250 @@ __global__ void __launch_bounds__(256) k_force_harmonic_f64(ForceArgs a) {
   }
   const int groups = min(per, a.N - blockIdx.x * per);
   block_bead_sums(u, w, P, groups, a.Upart, a.Wpart);
+  if (a.step_inc && blockIdx.x == 0 && threadIdx.x == 0) *a.step_inc += 1;
 }
 
-__global__ void __launch_bounds__(256) k_force_water_f64(ForceArgs a) {
+// Water-like model, FP64.  A cluster of 4 blocks x 4 warps serves one
+// (molecule m, chunk of Bk = min(P, 32) beads).  Lane = (group u, bead kl):
+// beads of the chunk in adjacent lanes (coalesced gathers of a neighbour's
+// bead row), G = 32 / Bk groups when P < 32.  Warps s = 0..13 split the
+// molecule's O-O neighbour list: warp s, group u owns bucket b = s G + u,
+// the neighbours j with j mod (14 G) = b, in index order -- every lane of a
+// warp runs the same loop (no divergent filtering), and because a pair's
+// bucket depends on j alone, every sum depends only on the set of
+// interacting pairs: a rebuilt list cannot change a bit.  Warp 14 evaluates
+// the two O-H bonds, warp 15 the H-O-H angle.
+// A neighbour is first tested in FP32 against (rc + 0.05 A)^2 -- a
+// conservative bound, FP32 rounding of a <100 A coordinate being ~1e-5 A --
+// and only survivors are evaluated in FP64 with the exact r < rc test, so the
+// FP64 result is that of an all-FP64 loop; the FP32 image shift is exact for
+// every pair that can be inside rc (their |d| is well below L/2).
+// Reduction: warps and groups in shared memory, then the 4 blocks of the
+// cluster through distributed shared memory in rank order -- deterministic,
+// no atomics, no global scratch.
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f64(ForceArgs a) {
+  __shared__ double sacc[11][128];
+  __shared__ double red[11][32];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
   const int P = a.P;
-  const int per = blockDim.x / P;                  // molecules per block
-  const int m = blockIdx.x * per + threadIdx.x / P;
-  const int k = threadIdx.x % P;
-  double u = 0.0, w = 0.0;
-  if (threadIdx.x < per * P && m < a.nmol) {
+  const int Bk = P < 32 ? P : 32;
+  const int G = a.nbr_groups;
+  const int NS = kLJWarps * G;
+  const int nchunk = (P + Bk - 1) / Bk;
+  const int cid = blockIdx.x / 4;
+  const int m = cid / nchunk, chunk = cid % nchunk;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = rank * 4 + warp;     // 0..kLJWarps-1: LJ buckets; then bonds, angle
+  const int u = lane / Bk, kl = lane % Bk;
+  const int k = chunk * Bk + kl;
+  double acc[11];
+#pragma unroll
+  for (int c = 0; c < 11; ++c) acc[c] = 0.0;
+  if (u < G && k < P && m < a.nmol) {
     const int o = 3 * m;
     const double L0 = a.box[0], L1 = a.box[1], L2 = a.box[2];
     const double i0 = a.invbox[0], i1 = a.invbox[1], i2 = a.invbox[2];
-    const size_t so = (size_t)o * 3 * P + k;     // O, component 0, bead k
+    const size_t so = (size_t)o * 3 * P + k;
     const double xo0 = a.x[so], xo1 = a.x[so + P], xo2 = a.x[so + 2 * P];
-    double dv[2][3], r[2];
-    double fo0 = 0.0, fo1 = 0.0, fo2 = 0.0;
-    double fh[2][3];
+    if (s >= kLJWarps) {
+      // warp kLJWarps: the two O-H bonds; warp kLJWarps + 1: the H-O-H angle
+      if (u == 0) {
+        double dv[2][3], r[2], ir[2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const size_t sh = (size_t)(o + 1 + h) * 3 * P + k;
-      dv[h][0] = mic(a.x[sh] - xo0, L0, i0);
-      dv[h][1] = mic(a.x[sh + P] - xo1, L1, i1);
-      dv[h][2] = mic(a.x[sh + 2 * P] - xo2, L2, i2);
-      r[h] = sqrt(dv[h][0] * dv[h][0] + dv[h][1] * dv[h][1] + dv[h][2] * dv[h][2]);
-      // O-H bond, U = 1/2 kb (r - r0)^2
-      const double dr = r[h] - a.r0;
-      u = fma(0.5 * a.kb * dr, dr, u);
-      const double g = -a.kb * dr / r[h];
+        for (int h = 0; h < 2; ++h) {
+          const size_t sh = (size_t)(o + 1 + h) * 3 * P + k;
+          dv[h][0] = mic(a.x[sh] - xo0, L0, i0);
+          dv[h][1] = mic(a.x[sh + P] - xo1, L1, i1);
+          dv[h][2] = mic(a.x[sh + 2 * P] - xo2, L2, i2);
+          r[h] = sqrt(dv[h][0] * dv[h][0] + dv[h][1] * dv[h][1] + dv[h][2] * dv[h][2]);
+          ir[h] = 1.0 / r[h];
+        }
+        if (s == kLJWarps) {
+          // U = 1/2 kb (r - r0)^2 per bond, force on H = -kb (r - r0) d / r
+          double uu = 0.0, w = 0.0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        fh[h][c] = g * dv[h][c];
-        w = fma(dv[h][c], fh[h][c], w);
+          for (int h = 0; h < 2; ++h) {
+            const double dr = r[h] - a.r0;
+            uu = fma(0.5 * a.kb * dr, dr, uu);
+            const double g = -a.kb * dr * ir[h];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const double fc = g * dv[h][c];
+              acc[3 + 3 * h + c] = fc;
+              acc[c] -= fc;
+              w = fma(dv[h][c], fc, w);
+            }
+          }
+          acc[9] = uu;
+          acc[10] = w;
+        } else {
+          // U = 1/2 kth (theta - th0)^2; F_h = kth (theta - th0)/sin(theta) d cos(theta)/d r_h
+          const double ir01 = ir[0] * ir[1];
+          const double dot = dv[0][0] * dv[1][0] + dv[0][1] * dv[1][1] + dv[0][2] * dv[1][2];
+          const double cth = fmin(1.0, fmax(-1.0, dot * ir01));
+          const double th = acos(cth);
+          const double dth = th - a.th0;
+          const double pref = a.kth * dth / sin(th);
+          double w = 0.0;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int g = 1 - h;
+            const double ch = cth * ir[h] * ir[h];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const double fa = pref * fma(dv[g][c], ir01, -ch * dv[h][c]);
+              acc[3 + 3 * h + c] = fa;
+              acc[c] -= fa;
+              w = fma(dv[h][c], fa, w);
+            }
+          }
+          acc[9] = 0.5 * a.kth * dth * dth;
+          acc[10] = w;
+        }
       }
-    }
-    // H-O-H angle, U = 1/2 kth (theta - th0)^2
-    const double r01 = r[0] * r[1];
-    const double dot = dv[0][0] * dv[1][0] + dv[0][1] * dv[1][1] + dv[0][2] * dv[1][2];
-    double cth = dot / r01;
-    cth = fmin(1.0, fmax(-1.0, cth));
-    const double th = acos(cth);
-    const double dth = th - a.th0;
-    u = fma(0.5 * a.kth * dth, dth, u);
-    const double pref = a.kth * dth / sin(th);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int g = 1 - h;
-      const double inv_rh2 = 1.0 / (r[h] * r[h]);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const double dcos = dv[g][c] / r01 - cth * dv[h][c] * inv_rh2;
-        const double fa = pref * dcos;
-        fh[h][c] += fa;
-        w = fma(dv[h][c], fa, w);
-      }
-    }
-    fo0 = -(fh[0][0] + fh[1][0]);
-    fo1 = -(fh[0][1] + fh[1][1]);
-    fo2 = -(fh[0][2] + fh[1][2]);
-    // O-O Lennard-Jones over the centroid neighbour list; each molecule takes
-    // half of every pair's energy and virial.
+    } else {
+    // O-O Lennard-Jones over bucket b of the neighbour list
+    const int b = s * G + u;          // neighbours j with j mod (kLJWarps G) = b
+    const int *off = a.nbr_off + (size_t)m * (NS + 1);
+    const int q0 = __ldg(off + b), q1 = __ldg(off + b + 1);
+    const int *nl = a.nbr + (size_t)m * kMaxNeighbours;
+    const float xf0 = a.x32[so], xf1 = a.x32[so + P], xf2 = a.x32[so + 2 * P];
+    const float Lf0 = (float)L0, Lf1 = (float)L1, Lf2 = (float)L2;
+    const float if0 = (float)i0, if1 = (float)i1, if2 = (float)i2;
+    const float rpre = (float)(a.rc + 0.05);
+    const float rpre2 = rpre * rpre;
     const double rc2 = a.rc * a.rc;
     const double sig2 = a.sig * a.sig;
     const double e4 = 4.0 * a.eps, e24 = 24.0 * a.eps;
-    const int nn = a.nnbr[m];
-    const int *nl = a.nbr + (size_t)m * kMaxNeighbours;
-    double ulj = 0.0, wlj = 0.0;
-    for (int q = 0; q < nn; ++q) {
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0, ulj = 0.0, wlj = 0.0;
+    for (int q = q0; q < q1; ++q) {
       const int j = __ldg(nl + q);
       const size_t sj = (size_t)(3 * j) * 3 * P + k;
-      const double d0 = mic(a.x[sj] - xo0, L0, i0);
-      const double d1 = mic(a.x[sj + P] - xo1, L1, i1);
-      const double d2 = mic(a.x[sj + 2 * P] - xo2, L2, i2);
+      float d0f = __ldg(a.x32 + sj) - xf0, d1f = __ldg(a.x32 + sj + P) - xf1;
+      float d2f = __ldg(a.x32 + sj + 2 * P) - xf2;
+      const float n0 = rintf(d0f * if0), n1 = rintf(d1f * if1), n2 = rintf(d2f * if2);
+      d0f = fmaf(-n0, Lf0, d0f);
+      d1f = fmaf(-n1, Lf1, d1f);
+      d2f = fmaf(-n2, Lf2, d2f);
+      if (d0f * d0f + d1f * d1f + d2f * d2f >= rpre2) continue;
+      const double d0 = fma(-(double)n0, L0, a.x[sj] - xo0);
+      const double d1 = fma(-(double)n1, L1, a.x[sj + P] - xo1);
+      const double d2 = fma(-(double)n2, L2, a.x[sj + 2 * P] - xo2);
       const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
       if (r2 < rc2) {
-        const double s2 = sig2 / r2;
+        const double inv = 1.0 / r2;
+        const double s2 = sig2 * inv;
         const double s6 = s2 * s2 * s2;
-        ulj = fma(e4, s6 * s6 - s6, ulj);
-        const double fr = e24 * (2.0 * s6 * s6 - s6) / r2;   // force on j = fr * d
-        fo0 = fma(-fr, d0, fo0);
-        fo1 = fma(-fr, d1, fo1);
-        fo2 = fma(-fr, d2, fo2);
+        ulj = fma(e4, fma(s6, s6, -s6), ulj);
+        const double fr = e24 * fma(2.0 * s6, s6, -s6) * inv;   // force on j = fr * d
+        f0 = fma(-fr, d0, f0);
+        f1 = fma(-fr, d1, f1);
+        f2 = fma(-fr, d2, f2);
         wlj = fma(fr, r2, wlj);
       }
     }
-    u = fma(0.5, ulj, u);
-    w = fma(0.5, wlj, w);
-    a.F[so] = fo0;
-    a.F[so + P] = fo1;
-    a.F[so + 2 * P] = fo2;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const size_t sh = (size_t)(o + 1 + h) * 3 * P + k;
-      a.F[sh] = fh[h][0];
-      a.F[sh + P] = fh[h][1];
-      a.F[sh + 2 * P] = fh[h][2];
+    // each molecule takes half of every pair's energy and virial
+    acc[0] = f0;
+    acc[1] = f1;
+    acc[2] = f2;
+    acc[9] = 0.5 * ulj;
+    acc[10] = 0.5 * wlj;
     }
   }
-  const int groups = min(per, a.nmol - blockIdx.x * per);
-  block_bead_sums(u, w, P, groups, a.Upart, a.Wpart);
+#pragma unroll
+  for (int c = 0; c < 11; ++c) sacc[c][threadIdx.x] = acc[c];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
+    const int comp = t / Bk, kk = t % Bk;
+    double sum = 0.0;
+    for (int w = 0; w < 4; ++w)
+      for (int g = 0; g < G; ++g) sum += sacc[comp][w * 32 + g * Bk + kk];
+    red[comp][kk] = sum;
+  }
+  cluster.sync();
+  if (rank == 0 && m < a.nmol) {
+    for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
+      const int comp = t / Bk, kk = t % Bk;
+      const int k2 = chunk * Bk + kk;
+      if (k2 >= P) continue;
+      double sum = 0.0;
+      for (int r = 0; r < 4; ++r) sum += cluster.map_shared_rank(&red[0][0], r)[comp * 32 + kk];
+      if (comp < 9)
+        a.F[(size_t)(3 * m + comp / 3) * 3 * P + (comp % 3) * P + k2] = sum;
+      else if (comp == 9)
+        a.Upart[(size_t)m * P + k2] = sum;
+      else
+        a.Wpart[(size_t)m * P + k2] = sum;
+    }
+    if (a.step_inc && blockIdx.x == 0 && threadIdx.x == 0) *a.step_inc += 1;
+  }
+  // keep every block's shared memory alive until rank 0 has read it
+  cluster.sync();
 }
 
 // --- O-O neighbour list on ring-polymer centroids ---------------------------
 // A pair (m, j) can interact at some bead only if its centroid distance at
 // the last build was below rc + skin, as long as
 //   2 max_m |c_m - c_m(build)| + 2 max_{m,k} |x_O^k - c_m| <= skin
-// (triangle inequality on the minimum-image metric).  The check kernel
-// evaluates the left side every step; the build kernel rebuilds when it
-// exceeds the skin.
-
-__global__ void k_nbr_check(NbrArgs a, double *ccur) {
-  __shared__ double smax[256];
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  double val = 0.0;
-  if (m < a.nmol) {
-    const int P = a.P;
-    const size_t so = (size_t)(3 * m) * 3 * P;
-    double c[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double s = 0.0;
-      for (int k = 0; k < P; ++k) s += a.x[so + d * P + k];
-      c[d] = s / P;
-      ccur[3 * m + d] = c[d];
-    }
-    double dmax2 = 0.0;
-    for (int k = 0; k < P; ++k) {
-      const double e0 = a.x[so + k] - c[0], e1 = a.x[so + P + k] - c[1], e2 = a.x[so + 2 * P + k] - c[2];
-      dmax2 = fmax(dmax2, e0 * e0 + e1 * e1 + e2 * e2);
-    }
-    const double g0 = c[0] - a.cref[3 * m], g1 = c[1] - a.cref[3 * m + 1], g2 = c[2] - a.cref[3 * m + 2];
-    val = 2.0 * sqrt(g0 * g0 + g1 * g1 + g2 * g2) + 2.0 * sqrt(dmax2);
-    if (!(val == val)) val = 1e300;   // NaN positions force a rebuild (and fail later)
+// (triangle inequality on the minimum-image metric: a pair's bead distance
+// is at least its build-time centroid distance minus both centroid drifts
+// and both bead deviations).  The step kernel writes per-block maxima of the
+// two terms and the current centroids; this kernel rebuilds when the bound
+// exceeds the skin (or when forced), listing neighbours in index order.
+__global__ void k_nbr_build(NbrArgs a, const double *ccur) {
+  __shared__ double sd[128], se[128];
+  __shared__ int s_go;
+  double md = 0.0, me = 0.0;
+  for (int b = threadIdx.x; b < a.nblk_check; b += blockDim.x) {
+    md = fmax(md, a.blkmax[2 * b]);
+    me = fmax(me, a.blkmax[2 * b + 1]);
   }
-  smax[threadIdx.x] = val;
+  sd[threadIdx.x] = md;
+  se[threadIdx.x] = me;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) {
+      sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + st]);
+      se[threadIdx.x] = fmax(se[threadIdx.x], se[threadIdx.x + st]);
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) a.blkmax[blockIdx.x] = smax[0];
-}
-
-__global__ void k_nbr_build(NbrArgs a, const double *ccur) {
-  __shared__ int s_go;
-  if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int b = 0; b < a.nblk_check; ++b) mx = fmax(mx, a.blkmax[b]);
-    s_go = a.force || (mx > a.skin);
-  }
+  if (threadIdx.x == 0) s_go = a.force || (2.0 * sd[0] + 2.0 * se[0] > a.skin);
   __syncthreads();
   if (!s_go) return;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= a.nmol) return;
+  const int NS = kLJWarps * a.nbr_groups;
   const double c0 = ccur[3 * m], c1 = ccur[3 * m + 1], c2 = ccur[3 * m + 2];
   const double rl2 = a.rlist * a.rlist;
+  int cnt[kMaxBuckets];
+  for (int b = 0; b < NS; ++b) cnt[b] = 0;
   int n = 0;
+  for (int j = 0; j < a.nmol; ++j) {
+    if (j == m) continue;
+    const double d0 = mic(ccur[3 * j] - c0, a.box[0], a.invbox[0]);
+    const double d1 = mic(ccur[3 * j + 1] - c1, a.box[1], a.invbox[1]);
+    const double d2 = mic(ccur[3 * j + 2] - c2, a.box[2], a.invbox[2]);
+    if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
+      ++cnt[j % NS];
+      ++n;
+    }
+  }
+  int *off = a.nbr_off + (size_t)m * (NS + 1);
+  if (n > kMaxNeighbours) {
+    // leave an empty list and report: the forces of this step are incomplete
+    atomicOr(a.err, kErrNbrOverflow);
+    for (int b = 0; b <= NS; ++b) off[b] = 0;
+    return;
+  }
+  int acc = 0;
+  for (int b = 0; b < NS; ++b) {
+    off[b] = acc;
+    acc += cnt[b];
+    cnt[b] = 0;
+  }
+  off[NS] = acc;
   int *nl = a.nbr + (size_t)m * kMaxNeighbours;
   for (int j = 0; j < a.nmol; ++j) {
     if (j == m) continue;
@@ -218,18 +309,27 @@ __global__ void k_nbr_build(NbrArgs a, const double *ccur) {
     const double d1 = mic(ccur[3 * j + 1] - c1, a.box[1], a.invbox[1]);
     const double d2 = mic(ccur[3 * j + 2] - c2, a.box[2], a.invbox[2]);
     if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
-      if (n < kMaxNeighbours) nl[n] = j;
-      ++n;
+      const int b = j % NS;
+      nl[off[b] + cnt[b]++] = j;
     }
   }
-  if (n > kMaxNeighbours) {
-    atomicOr(a.err, kErrNbrOverflow);
-    n = kMaxNeighbours;
-  }
-  a.nnbr[m] = n;
   a.cref[3 * m] = c0;
   a.cref[3 * m + 1] = c1;
   a.cref[3 * m + 2] = c2;
+}
+
+// Centroids of the oxygens from the positions (used when the positions were
+// set from outside the step kernel: create, set_state), and a forced build.
+__global__ void k_centroids(NbrArgs a, double *ccur) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.nmol) return;
+  const int P = a.P;
+  const size_t so = (size_t)(3 * m) * 3 * P;
+  for (int d = 0; d < 3; ++d) {
+    double s = 0.0;
+    for (int k = 0; k < P; ++k) s += a.x[so + d * P + k];
+    ccur[3 * m + d] = s / P;
+  }
 }
 
 // --- host launchers --------------------------------------------------------
@@ -247,22 +347,37 @@ int force_blocks(int n_groups, int P) {
   return (n_groups + per - 1) / per;
 }
 
+int water_force_blocks(int nmol, int P) {
+  const int Bk = P < 32 ? P : 32;
+  return 4 * nmol * ((P + Bk - 1) / Bk);
+}
+
+// lane groups per warp of the water force kernel: the largest power of two
+// <= min(8, 32 / min(P, 32))
+int water_lane_groups(int P) {
+  const int Bk = P < 32 ? P : 32;
+  int g = 1;
+  while (2 * g <= 8 && 2 * g * Bk <= 32) g *= 2;
+  return g;
+}
+
 cudaError_t launch_force_harmonic(const ForceArgs &a, cudaStream_t s) {
   k_force_harmonic_f64<<<force_blocks(a.N, a.P), force_block_threads(a.P), 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_force_water(const ForceArgs &a, cudaStream_t s) {
-  k_force_water_f64<<<force_blocks(a.nmol, a.P), force_block_threads(a.P), 0, s>>>(a);
+  k_force_water_f64<<<water_force_blocks(a.nmol, a.P), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-int nbr_check_blocks(int nmol) { return (nmol + 127) / 128; }
+cudaError_t launch_nbr_build(const NbrArgs &a, const double *ccur, cudaStream_t s) {
+  k_nbr_build<<<(a.nmol + 127) / 128, 128, 0, s>>>(a, ccur);
+  return cudaGetLastError();
+}
 
-cudaError_t launch_nbr(const NbrArgs &a, double *ccur, cudaStream_t s) {
-  const int nb = nbr_check_blocks(a.nmol);
-  k_nbr_check<<<nb, 128, 0, s>>>(a, ccur);
-  k_nbr_build<<<nb, 128, 0, s>>>(a, ccur);
+cudaError_t launch_centroids(const NbrArgs &a, double *ccur, cudaStream_t s) {
+  k_centroids<<<(a.nmol + 127) / 128, 128, 0, s>>>(a, ccur);
   return cudaGetLastError();
 }
 

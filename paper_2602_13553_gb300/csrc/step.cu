@@ -8,11 +8,13 @@
 // traffic.  Per step and atom tile the kernel reads x, v~, F once and writes
 // x, v~ once, coalesced (every atom's P beads are contiguous per component).
 //
-// Tasks: thread (mode k, atom a) computes the three components of
+// Tasks: thread (mode k, component d, atom a) forms
 //   F~_k = sum_j M[k][j] F_j and q~_k = sum_j M[k][j] x_j        (Eq. A1)
 // applies B / A / O / A (BAOAB) or the pending B O of the previous step then
 // O B A (OBABO) in registers, and stores v~; after a barrier, thread
-// (bead j, atom a) forms x_j = sum_k M[k][j] q~_k (Eq. A3).
+// (bead j, component d, atom a) forms x_j = sum_k M[k][j] q~_k (Eq. A3).
+// For water-like systems the same kernel also measures, per oxygen, the
+// centroid drift since the last neighbour-list build and the bead spread.
 #include "common.cuh"
 
 namespace pimd {
@@ -26,6 +28,15 @@ __device__ __forceinline__ void rotate(double &q, double &v, double c, double s_
   v = vn;
 }
 
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Thread task t = (al * 3 + d) * P + k: atom al of the tile, component d,
+// mode k (forward) or bead j = k (inverse).  This is also the offset of the
+// element in the tile, so loads, stores and shared memory share one index.
 __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   extern __shared__ double sm[];
   const int P = a.P;
@@ -34,6 +45,7 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   double *sV = sX + tileLen;
   double *sF = sV + tileLen;
   double *sQ = sF + tileLen;
+  __shared__ double sred[2][8];
   const int tile0 = blockIdx.x * a.A;
   const int na = min(a.A, a.N - tile0);
   const int len = na * 3 * P;
@@ -46,101 +58,110 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   __syncthreads();
   const uint64_t step = (uint64_t)(*a.step + a.step_off);
   const double *__restrict__ Mt = a.mt.Mt;
-  for (int task = threadIdx.x; task < na * P; task += blockDim.x) {
+  for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int k = task % P;
-    const int al = task / P;
-    const int i = tile0 + al;
-    const double *fx = sF + al * 3 * P;
-    const double *xx = sX + al * 3 * P;
-    double f0 = 0.0, f1 = 0.0, f2 = 0.0, q0 = 0.0, q1 = 0.0, q2 = 0.0;
-    for (int j = 0; j < P; ++j) {
-      const double m = __ldg(Mt + j * P + k);
-      f0 = fma(m, fx[j], f0);
-      f1 = fma(m, fx[P + j], f1);
-      f2 = fma(m, fx[2 * P + j], f2);
-      q0 = fma(m, xx[j], q0);
-      q1 = fma(m, xx[P + j], q1);
-      q2 = fma(m, xx[2 * P + j], q2);
+    const int r = task / P;
+    const int d = r % 3;
+    const int i = tile0 + r / 3;
+    const double *fx = sF + r * P;
+    const double *xx = sX + r * P;
+    // F~_k = (M F)_k and q~_k = (M x)_k, two independent chains each
+    double fa = 0.0, fb = 0.0, qa = 0.0, qb = 0.0;
+    int j = 0;
+    for (; j + 1 < P; j += 2) {
+      const double m0 = __ldg(Mt + j * P + k), m1 = __ldg(Mt + (j + 1) * P + k);
+      fa = fma(m0, fx[j], fa);
+      fb = fma(m1, fx[j + 1], fb);
+      qa = fma(m0, xx[j], qa);
+      qb = fma(m1, xx[j + 1], qb);
     }
-    const double *vv = sV + al * 3 * P;
-    double v0 = vv[k], v1 = vv[P + k], v2 = vv[2 * P + k];
+    if (j < P) {
+      const double m0 = __ldg(Mt + j * P + k);
+      fa = fma(m0, fx[j], fa);
+      qa = fma(m0, xx[j], qa);
+    }
+    const double f = fa + fb;
+    double q = qa + qb;
+    double v = sV[task];
     const double im = __ldg(a.inv_mm + i);
     const double cA = __ldg(a.mt.cA + k), sA = __ldg(a.mt.sA + k), wsA = __ldg(a.mt.wsA + k);
     const double c1 = __ldg(a.mt.c1 + k), c2s = __ldg(a.mt.c2 + k) * __ldg(a.sigv + i);
     if (a.integrator == 0) {
       // B(h/2) of this step, merged with the final B(h/2) of the previous one
-      const double kb = a.kick * im;
-      v0 = fma(kb, f0, v0);
-      v1 = fma(kb, f1, v1);
-      v2 = fma(kb, f2, v2);
-      rotate(q0, v0, cA, sA, wsA);
-      rotate(q1, v1, cA, sA, wsA);
-      rotate(q2, v2, cA, sA, wsA);
-      if (a.thermo) {
-        double e0, e1, e2;
-        gauss3(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, e0, e1, e2);
-        v0 = fma(c1, v0, c2s * e0);
-        v1 = fma(c1, v1, c2s * e1);
-        v2 = fma(c1, v2, c2s * e2);
-      }
-      rotate(q0, v0, cA, sA, wsA);
-      rotate(q1, v1, cA, sA, wsA);
-      rotate(q2, v2, cA, sA, wsA);
+      v = fma(a.kick * im, f, v);
+      rotate(q, v, cA, sA, wsA);
+      if (a.thermo)
+        v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+      rotate(q, v, cA, sA, wsA);
     } else {
       const double kb = a.half * im;
       if (!a.first) {
         // the previous step's closing B(h/2) O(h/2)
-        v0 = fma(kb, f0, v0);
-        v1 = fma(kb, f1, v1);
-        v2 = fma(kb, f2, v2);
-        if (a.thermo) {
-          double e0, e1, e2;
-          gauss3(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, e0, e1, e2);
-          v0 = fma(c1, v0, c2s * e0);
-          v1 = fma(c1, v1, c2s * e1);
-          v2 = fma(c1, v2, c2s * e2);
-        }
+        v = fma(kb, f, v);
+        if (a.thermo)
+          v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, d));
       }
-      if (a.thermo) {
-        double e0, e1, e2;
-        gauss3(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, e0, e1, e2);
-        v0 = fma(c1, v0, c2s * e0);
-        v1 = fma(c1, v1, c2s * e1);
-        v2 = fma(c1, v2, c2s * e2);
-      }
-      v0 = fma(kb, f0, v0);
-      v1 = fma(kb, f1, v1);
-      v2 = fma(kb, f2, v2);
-      rotate(q0, v0, cA, sA, wsA);
-      rotate(q1, v1, cA, sA, wsA);
-      rotate(q2, v2, cA, sA, wsA);
+      if (a.thermo)
+        v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+      v = fma(kb, f, v);
+      rotate(q, v, cA, sA, wsA);
     }
-    double *qq = sQ + al * 3 * P;
-    qq[k] = q0;
-    qq[P + k] = q1;
-    qq[2 * P + k] = q2;
-    double *vg = a.v + base + (size_t)al * 3 * P;
-    vg[k] = v0;
-    vg[P + k] = v1;
-    vg[2 * P + k] = v2;
+    sQ[task] = q;
+    a.v[base + task] = v;
   }
   __syncthreads();
   const double *__restrict__ M = a.mt.M;
-  for (int task = threadIdx.x; task < na * P; task += blockDim.x) {
+  for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int j = task % P;
-    const int al = task / P;
-    const double *qq = sQ + al * 3 * P;
-    double x0 = 0.0, x1 = 0.0, x2 = 0.0;
-    for (int k = 0; k < P; ++k) {
-      const double m = __ldg(M + k * P + j);
-      x0 = fma(m, qq[k], x0);
-      x1 = fma(m, qq[P + k], x1);
-      x2 = fma(m, qq[2 * P + k], x2);
+    const double *qq = sQ + (task / P) * P;
+    double xa = 0.0, xb = 0.0;
+    int k = 0;
+    for (; k + 1 < P; k += 2) {
+      xa = fma(__ldg(M + k * P + j), qq[k], xa);
+      xb = fma(__ldg(M + (k + 1) * P + j), qq[k + 1], xb);
     }
-    double *xg = a.x + base + (size_t)al * 3 * P;
-    xg[j] = x0;
-    xg[P + j] = x1;
-    xg[2 * P + j] = x2;
+    if (k < P) xa = fma(__ldg(M + k * P + j), qq[k], xa);
+    const double xn = xa + xb;
+    a.x[base + task] = xn;
+    if (a.x32) a.x32[base + task] = (float)xn;
+    sX[task] = xn;
+  }
+  if (!a.blkmax) return;
+  // Neighbour-list skin check for the oxygens of this tile: centroid
+  // c = q~_0 / sqrt(P), its drift since the last build and the bead spread.
+  __syncthreads();
+  double vdisp = 0.0, vdev = 0.0;
+  const double rsp = rsqrt((double)P);
+  for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
+    const int al = t / P, k = t % P;
+    const int i = tile0 + al;
+    if (i % 3) continue;
+    const double *xq = sQ + al * 3 * P;
+    const double c0 = xq[0] * rsp, c1 = xq[P] * rsp, c2 = xq[2 * P] * rsp;
+    const double *xs = sX + al * 3 * P;
+    const double e0 = xs[k] - c0, e1 = xs[P + k] - c1, e2 = xs[2 * P + k] - c2;
+    vdev = fmax(vdev, e0 * e0 + e1 * e1 + e2 * e2);
+    if (k == 0) {
+      const int m = i / 3;
+      const double g0 = c0 - a.cref[3 * m], g1 = c1 - a.cref[3 * m + 1], g2 = c2 - a.cref[3 * m + 2];
+      vdisp = fmax(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
+      a.ccur[3 * m] = c0;
+      a.ccur[3 * m + 1] = c1;
+      a.ccur[3 * m + 2] = c2;
+    }
+  }
+  vdisp = warp_max(vdisp);
+  vdev = warp_max(vdev);
+  if ((threadIdx.x & 31) == 0) {
+    sred[0][threadIdx.x >> 5] = vdisp;
+    sred[1][threadIdx.x >> 5] = vdev;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double mx = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) mx = fmax(mx, sred[threadIdx.x][w]);
+    // NaN positions force a rebuild (and fail later at a synchronising call)
+    a.blkmax[2 * blockIdx.x + threadIdx.x] = (mx == mx) ? sqrt(mx) : 1e300;
   }
 }
 
@@ -158,35 +179,31 @@ __global__ void __launch_bounds__(256) k_close_f64(StepArgs a) {
   __syncthreads();
   const uint64_t step = (uint64_t)(*a.step + a.step_off);
   const double *__restrict__ Mt = a.mt.Mt;
-  for (int task = threadIdx.x; task < na * P; task += blockDim.x) {
+  for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int k = task % P;
-    const int al = task / P;
-    const int i = tile0 + al;
-    const double *fx = sF + al * 3 * P;
-    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-    for (int j = 0; j < P; ++j) {
-      const double m = __ldg(Mt + j * P + k);
-      f0 = fma(m, fx[j], f0);
-      f1 = fma(m, fx[P + j], f1);
-      f2 = fma(m, fx[2 * P + j], f2);
+    const int r = task / P;
+    const int d = r % 3;
+    const int i = tile0 + r / 3;
+    const double *fx = sF + r * P;
+    double fa = 0.0, fb = 0.0;
+    int j = 0;
+    for (; j + 1 < P; j += 2) {
+      fa = fma(__ldg(Mt + j * P + k), fx[j], fa);
+      fb = fma(__ldg(Mt + (j + 1) * P + k), fx[j + 1], fb);
     }
-    double *vg = a.v + base + (size_t)al * 3 * P;
-    const double kb = a.half * __ldg(a.inv_mm + i);
-    double v0 = fma(kb, f0, vg[k]);
-    double v1 = fma(kb, f1, vg[P + k]);
-    double v2 = fma(kb, f2, vg[2 * P + k]);
+    if (j < P) fa = fma(__ldg(Mt + j * P + k), fx[j], fa);
+    double v = fma(a.half * __ldg(a.inv_mm + i), fa + fb, a.v[base + task]);
     if (a.integrator == 1 && a.thermo) {
       const double c1 = __ldg(a.mt.c1 + k), c2s = __ldg(a.mt.c2 + k) * __ldg(a.sigv + i);
-      double e0, e1, e2;
-      gauss3(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step, e0, e1, e2);
-      v0 = fma(c1, v0, c2s * e0);
-      v1 = fma(c1, v1, c2s * e1);
-      v2 = fma(c1, v2, c2s * e2);
+      v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step, d));
     }
-    vg[k] = v0;
-    vg[P + k] = v1;
-    vg[2 * P + k] = v2;
+    a.v[base + task] = v;
   }
+}
+
+__global__ void k_to_f32(const double *src, float *dst, size_t n) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = (float)src[t];
 }
 
 __global__ void k_advance(int64_t *step, int n) {
@@ -242,6 +259,11 @@ cudaError_t launch_step(const StepArgs &a, int threads, cudaStream_t s) {
 cudaError_t launch_close(const StepArgs &a, int threads, cudaStream_t s) {
   const int grid = (a.N + a.A - 1) / a.A;
   k_close_f64<<<grid, threads, close_smem_bytes(a.A, a.P), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double *src, float *dst, size_t n, cudaStream_t s) {
+  k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
 
