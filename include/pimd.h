@@ -63,8 +63,14 @@ enum { PIMD_THERMO_NONE = 0, PIMD_THERMO_PILE_L = 1 };
 enum { PIMD_BAOAB = 0, PIMD_OBABO = 1 };
 /* Sec. III.C keyword "method": only nmpimd (normal modes) is implemented */
 enum { PIMD_METHOD_NMPIMD = 0 };
-/* arithmetic of the step and force kernels */
-enum { PIMD_PREC_FP64 = 0 };
+/* arithmetic of the step and force kernels:
+ *   FP64   every quantity in FP64.
+ *   SPLIT  the ring-polymer centroid (position and centroid-mode velocity) in
+ *          FP64; bead deviations from the centroid, internal-mode velocities,
+ *          forces and the normal-mode transforms in FP32; estimator sums in
+ *          FP64.  Values returned by pimd_get_state are the FP64
+ *          reconstructions x = centroid + deviation. */
+enum { PIMD_PREC_FP64 = 0, PIMD_PREC_SPLIT = 1 };
 
 typedef struct pimd_handle pimd_handle;
 

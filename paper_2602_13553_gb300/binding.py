@@ -24,6 +24,7 @@ BAOAB = 0
 OBABO = 1
 METHOD_NMPIMD = 0
 PREC_FP64 = 0
+PREC_SPLIT = 1
 MAX_BEADS = 128
 
 STATUS = {0: "PIMD_OK", 1: "PIMD_EINVAL", 2: "PIMD_ENOMEM", 3: "PIMD_ECUDA", 4: "PIMD_ENONFINITE",

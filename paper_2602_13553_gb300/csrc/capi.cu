@@ -36,6 +36,13 @@ cudaError_t launch_est(const EstArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_est_final(const EstFinalArgs &a, cudaStream_t s);
 int force_blocks(int n_groups, int P);
 int water_lane_groups(int P);
+cudaError_t launch_step_split(const SplitStepArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_close_split(const SplitStepArgs &a, int threads, cudaStream_t s);
+cudaError_t launch_force_split(const SplitForceArgs &a, bool water, cudaStream_t s);
+cudaError_t launch_expand_split(const SplitStepArgs &a, const float *F, double *x, double *v, double *Fd,
+                                cudaStream_t s);
+cudaError_t launch_compress_split(const SplitStepArgs &a, const double *x, const double *v,
+                                  cudaStream_t s);
 }  // namespace pimd
 
 using namespace pimd;
@@ -119,7 +126,7 @@ extern "C" void pimd_params_default(pimd_params *p) {
 // the handle
 // ---------------------------------------------------------------------------
 struct pimd_handle {
-  int N = 0, P = 0, potential = 0, nmol = 0, integrator = 0, thermostat = 0;
+  int N = 0, P = 0, potential = 0, nmol = 0, integrator = 0, thermostat = 0, precision = 0;
   double T = 0, dt = 0, tau = 0, scale = 0, sp = 0;
   uint64_t seed = 0;
   double box[3] = {0, 0, 0};
@@ -132,6 +139,13 @@ struct pimd_handle {
   // device state, layout [N][3][P]
   double *x = nullptr, *v = nullptr, *F = nullptr, *tmp = nullptr;
   float *x32 = nullptr;   // FP32 copy of x (water-like: the force kernel's cutoff prefilter)
+  // split precision: FP64 centroids, FP32 deviations / internal modes / forces
+  // (x, v, F above then only serve as FP64 staging for estimators and state copies)
+  double *xc = nullptr, *v0 = nullptr;
+  float *dev = nullptr, *vk = nullptr, *F32 = nullptr, *xcw = nullptr;
+  float *Mf = nullptr, *Mtf = nullptr, *cAf = nullptr, *sAf = nullptr, *wsAf = nullptr;
+  float *c1f = nullptr, *c2f = nullptr;
+  double tA = 0.0, c1_0 = 0.0, c2_0 = 0.0;
   double *inv_mm = nullptr, *sigv = nullptr, *mass_mm = nullptr, *kspring = nullptr;
   double *M = nullptr, *Mt = nullptr, *cA = nullptr, *sA = nullptr, *wsA = nullptr;
   double *c1 = nullptr, *c2 = nullptr, *lam = nullptr;
@@ -347,7 +361,107 @@ static NbrArgs nbr_args(pimd_handle *h, bool force) {
 // from_outside: the positions were not written by the step kernel (create,
 // set_state), so the centroids are recomputed and the list rebuilt.
 // advance: the force kernel also advances the device step counter.
+static SplitStepArgs split_args(pimd_handle *h) {
+  SplitStepArgs a;
+  a.N = h->N;
+  a.P = h->P;
+  a.A = h->A_step;
+  a.Mf = h->Mf;
+  a.Mtf = h->Mtf;
+  a.cAf = h->cAf;
+  a.sAf = h->sAf;
+  a.wsAf = h->wsAf;
+  a.c1f = h->c1f;
+  a.c2f = h->c2f;
+  a.tA = h->tA;
+  a.c1_0 = h->c1_0;
+  a.c2_0 = h->c2_0;
+  a.inv_mm = h->inv_mm;
+  a.sigv = h->sigv;
+  a.xc = h->xc;
+  a.v0 = h->v0;
+  a.d = h->dev;
+  a.vk = h->vk;
+  a.F = h->F32;
+  const bool water = h->potential == PIMD_POT_WATERLIKE;
+  a.xcw = water ? h->xcw : nullptr;
+  for (int d = 0; d < 3; ++d) {
+    a.box[d] = h->box[d];
+    a.invbox[d] = h->box[d] > 0 ? 1.0 / h->box[d] : 0.0;
+  }
+  a.step = h->d_step;
+  a.step_off = 0;
+  a.cref = water ? h->cref : nullptr;
+  a.ccur = water ? h->ccur : nullptr;
+  a.blkmax = water ? h->blkmax : nullptr;
+  a.kick = h->dt;
+  a.half = 0.5 * h->dt;
+  a.integrator = h->integrator;
+  a.first = 0;
+  a.thermo = h->thermostat == PIMD_THERMO_PILE_L;
+  a.seed = h->seed;
+  return a;
+}
+
+static SplitForceArgs split_force_args(pimd_handle *h) {
+  const ForceArgs f = force_args(h);
+  SplitForceArgs a;
+  a.N = h->N;
+  a.P = h->P;
+  a.nmol = h->nmol;
+  a.xc = h->xc;
+  a.xcw = h->xcw;
+  a.d = h->dev;
+  a.F = h->F32;
+  a.Upart = h->Upart;
+  a.Wpart = h->Wpart;
+  a.step_inc = nullptr;
+  a.kspring = h->kspring;
+  for (int d = 0; d < 3; ++d) {
+    a.box[d] = f.box[d];
+    a.invbox[d] = f.invbox[d];
+  }
+  a.kb = f.kb;
+  a.r0 = f.r0;
+  a.kth = f.kth;
+  a.th0 = f.th0;
+  a.eps = f.eps;
+  a.sig = f.sig;
+  a.rc = f.rc;
+  a.nbr = h->nbr;
+  a.nbr_off = h->nbr_off;
+  a.nbr_groups = h->nbr_groups;
+  return a;
+}
+
+// Split precision: FP64 staging arrays x, v (and F) from the split state.
+static pimd_status expand_split(pimd_handle *h, bool with_forces) {
+  return enqueue(h, PIMD_KIND_OTHER, 1, [&] {
+    return launch_expand_split(split_args(h), h->F32, h->x, h->v, with_forces ? h->F : nullptr,
+                               h->stream);
+  });
+}
+
 static pimd_status enqueue_forces(pimd_handle *h, bool from_outside, bool advance) {
+  if (h->precision == PIMD_PREC_SPLIT) {
+    const bool water = h->potential == PIMD_POT_WATERLIKE;
+    SplitForceArgs sa = split_force_args(h);
+    sa.step_inc = advance ? h->d_step : nullptr;
+    pimd_status st;
+    if (water) {
+      if (from_outside) {
+        st = enqueue(h, PIMD_KIND_OTHER, 1, [&] {
+          return launch_centroids(nbr_args(h, true), h->ccur, h->stream);
+        });
+        if (st != PIMD_OK) return st;
+      }
+      st = enqueue(h, PIMD_KIND_NBR, 1, [&] {
+        return launch_nbr_build(nbr_args(h, from_outside), h->ccur, h->stream);
+      });
+      if (st != PIMD_OK) return st;
+    }
+    return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_split(sa, water, h->stream); });
+  }
   ForceArgs fa = force_args(h);
   fa.step_inc = advance ? h->d_step : nullptr;
   if (h->potential == PIMD_POT_WATERLIKE) {
@@ -372,6 +486,15 @@ static pimd_status enqueue_forces(pimd_handle *h, bool from_outside, bool advanc
 // One full step: the fused integrator kernel, the forces of the new
 // positions, and the step counter.
 static pimd_status enqueue_step(pimd_handle *h, bool first) {
+  if (h->precision == PIMD_PREC_SPLIT) {
+    SplitStepArgs a = split_args(h);
+    a.first = first ? 1 : 0;
+    a.kick = first ? 0.5 * h->dt : h->dt;
+    pimd_status st =
+        enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step_split(a, h->threads_step, h->stream); });
+    if (st != PIMD_OK) return st;
+    return enqueue_forces(h, false, true);
+  }
   StepArgs a = step_args(h);
   a.first = first ? 1 : 0;
   a.kick = first ? 0.5 * h->dt : h->dt;
@@ -381,6 +504,11 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
 }
 
 static pimd_status enqueue_close(pimd_handle *h) {
+  if (h->precision == PIMD_PREC_SPLIT) {
+    SplitStepArgs a = split_args(h);
+    a.step_off = -1;
+    return enqueue(h, PIMD_KIND_CLOSE, 1, [&] { return launch_close_split(a, h->threads_step, h->stream); });
+  }
   StepArgs a = step_args(h);
   a.step_off = -1;
   return enqueue(h, PIMD_KIND_CLOSE, 1, [&] { return launch_close(a, h->threads_step, h->stream); });
@@ -494,6 +622,21 @@ static void carve(pimd_handle *h, Carver &c) {
   h->est_out = c.take<double>(3 * P + 12);
   h->d_step = c.take<int64_t>(1);
   h->d_err = c.take<unsigned>(4);
+  if (h->precision == PIMD_PREC_SPLIT) {
+    h->xc = c.take<double>((size_t)N * 3);
+    h->v0 = c.take<double>((size_t)N * 3);
+    h->dev = c.take<float>(len);
+    h->vk = c.take<float>(len);
+    h->F32 = c.take<float>(len);
+    h->xcw = c.take<float>((size_t)N * 3);
+    h->Mf = c.take<float>((size_t)P * P);
+    h->Mtf = c.take<float>((size_t)P * P);
+    h->cAf = c.take<float>(P);
+    h->sAf = c.take<float>(P);
+    h->wsAf = c.take<float>(P);
+    h->c1f = c.take<float>(P);
+    h->c2f = c.take<float>(P);
+  }
 }
 
 static pimd_status upload_state(pimd_handle *h, const double *x, const double *v) {
@@ -506,6 +649,7 @@ static pimd_status upload_state(pimd_handle *h, const double *x, const double *v
   } else {
     CK(launch_thermal_v(h->v, h->sigv, h->seed, h->N, h->P, h->stream));
   }
+  if (h->precision == PIMD_PREC_SPLIT) CK(launch_compress_split(split_args(h), h->x, h->v, h->stream));
   return PIMD_OK;
 }
 
@@ -532,7 +676,8 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   if (prm.integrator != PIMD_BAOAB && prm.integrator != PIMD_OBABO)
     return fail(PIMD_EINVAL, "unknown integrator %d", prm.integrator);
   if (prm.method != PIMD_METHOD_NMPIMD) return fail(PIMD_EINVAL, "only method nmpimd is implemented");
-  if (prm.precision != PIMD_PREC_FP64) return fail(PIMD_EINVAL, "unknown precision %d", prm.precision);
+  if (prm.precision != PIMD_PREC_FP64 && prm.precision != PIMD_PREC_SPLIT)
+    return fail(PIMD_EINVAL, "unknown precision %d", prm.precision);
   if (prm.fixcom != 0) return fail(PIMD_EINVAL, "fixcom is not implemented");
   if (!(prm.sp > 0.0)) return fail(PIMD_EINVAL, "sp must be > 0");
   if (gamma0 > 0.0) {
@@ -566,6 +711,7 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   h->nmol = sys->potential == PIMD_POT_WATERLIKE ? N / 3 : 0;
   h->integrator = prm.integrator;
   h->thermostat = prm.thermostat;
+  h->precision = prm.precision;
   h->T = T;
   h->dt = dt;
   h->tau = prm.tau;
@@ -657,6 +803,22 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
     release(h);
     return st;
   }
+  if (h->precision == PIMD_PREC_SPLIT) {
+    auto upf = [&](float *dst, const std::vector<double> &src) -> pimd_status {
+      std::vector<float> f(src.begin(), src.end());
+      CK(cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+      return PIMD_OK;
+    };
+    if ((st = upf(h->Mf, M)) || (st = upf(h->Mtf, Mt)) || (st = upf(h->cAf, cA)) ||
+        (st = upf(h->sAf, sA)) || (st = upf(h->wsAf, wsA)) || (st = upf(h->c1f, c1v)) ||
+        (st = upf(h->c2f, c2v))) {
+      release(h);
+      return st;
+    }
+    h->tA = tA;
+    h->c1_0 = c1v[0];
+    h->c2_0 = c2v[0];
+  }
   auto init = [&]() -> pimd_status {
     CK(cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
     CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned), h->stream));
@@ -719,6 +881,10 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   if (!h || !out) return fail(PIMD_EINVAL, "NULL argument");
   if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
   const int P = h->P;
+  if (h->precision == PIMD_PREC_SPLIT) {
+    pimd_status se = expand_split(h, true);
+    if (se != PIMD_OK) return se;
+  }
   EstArgs a;
   a.N = h->N;
   a.P = P;
@@ -779,6 +945,10 @@ extern "C" pimd_status pimd_get_state(pimd_handle *h, double *x, double *v_nm, i
   if (!h) return fail(PIMD_EINVAL, "handle is NULL");
   if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
   const size_t bytes = (size_t)h->N * 3 * h->P * sizeof(double);
+  if (h->precision == PIMD_PREC_SPLIT && (x || v_nm)) {
+    pimd_status se = expand_split(h, false);
+    if (se != PIMD_OK) return se;
+  }
   if (x) {
     CK(launch_nap_to_pna(h->x, h->tmp, h->N, h->P, h->stream));
     CK(cudaMemcpyAsync(x, h->tmp, bytes, cudaMemcpyDeviceToHost, h->stream));

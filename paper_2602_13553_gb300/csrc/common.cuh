@@ -157,6 +157,44 @@ struct NbrArgs {
   int force;                   // rebuild unconditionally
 };
 
+// Split precision (split.cu): FP64 centroid xc, v~_0 [N][3]; FP32 deviations
+// d = x - xc and internal-mode velocities v~_k (k >= 1) [N][3][P]; FP32 forces.
+struct SplitStepArgs {
+  int N, P, A;
+  const float *Mf, *Mtf;       // [P][P] FP32 copies of M and M^T
+  const float *cAf, *sAf, *wsAf, *c1f, *c2f;   // FP32 mode coefficients (k >= 1)
+  double tA, c1_0, c2_0;       // centroid: drift time of one A, O coefficients
+  const double *inv_mm, *sigv; // [N]
+  double *xc, *v0;             // [N][3]
+  float *d, *vk;               // [N][3][P]
+  const float *F;              // [N][3][P]
+  float *xcw;                  // [N][3] centroids wrapped into the box, FP32 (water), or null
+  double box[3], invbox[3];
+  const int64_t *step;
+  int step_off;
+  const double *cref;          // water: [nmol][3] centroids at the last list build, or null
+  double *ccur;
+  double *blkmax;
+  double kick, half;
+  int integrator, first, thermo;
+  uint64_t seed;
+};
+
+struct SplitForceArgs {
+  int N, P, nmol;
+  const double *xc;            // [N][3]
+  const float *xcw;            // [N][3] wrapped FP32 centroids (water)
+  const float *d;              // [N][3][P]
+  float *F;                    // [N][3][P]
+  double *Upart, *Wpart;
+  int64_t *step_inc;
+  const double *kspring;
+  double box[3], invbox[3];
+  double kb, r0, kth, th0, eps, sig, rc;
+  const int *nbr, *nbr_off;
+  int nbr_groups;
+};
+
 struct EstArgs {
   int N, P, A;
   ModeTables mt;
