@@ -245,6 +245,104 @@ pimd_status pimd_kernel_times(pimd_handle *h, double *ms, int64_t *launches);
  * replayed CUDA graphs included); -1 for a NULL handle. */
 int64_t pimd_kernel_launches(const pimd_handle *h);
 
+/* ---- batches of independent systems --------------------------------------
+ * A batch advances many independent water-like ring-polymer systems
+ * ("replicas": their own N, P, T, masses, seed and step count) together in
+ * split precision (PIMD_PREC_SPLIT arithmetic).  Each MD step of the batch
+ * is four kernel launches covering every replica; they are captured once in a
+ * CUDA graph and replayed, and replicas can be added and removed between
+ * calls without re-capture.  Each replica stops after its own step count;
+ * a replica's trajectory does not depend on which other replicas share the
+ * batch.  Same units, layouts and error rules as the single-system calls. */
+typedef struct pimd_batch pimd_batch;
+
+/* Device bytes one replica of n_atoms x P occupies (0 for invalid sizes). */
+size_t pimd_batch_replica_bytes(int32_t n_atoms, int32_t P);
+
+/* Empty batch with room for max_replicas (1..65536) on `stream` (NULL: a
+ * private stream). */
+pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pimd_batch **out);
+
+/* Add one replica: arguments as pimd_create (water-like potential only; the
+ * precision field is ignored, the batch computes in split precision), plus
+ * nsteps >= 0, the number of steps it will run.  Computes its initial
+ * forces; *slot receives its index.  EBUDGET when the batch is full,
+ * ENOMEM when its memory cannot be allocated. */
+pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int32_t P, double T, double dt,
+                           double gamma0, const pimd_params *params, int64_t nsteps, int32_t *slot);
+
+/* Remove a replica and free its memory (synchronises). */
+pimd_status pimd_batch_remove(pimd_batch *b, int32_t slot);
+
+/* Advance every replica with steps left by up to nsteps steps (asynchronous);
+ * afterwards every replica is at integer time. */
+pimd_status pimd_batch_run(pimd_batch *b, int64_t nsteps);
+pimd_status pimd_batch_sync(pimd_batch *b);
+
+/* step[s], steps_left[s] for every slot s < max_replicas (-1 for empty
+ * slots); either array may be NULL.  Synchronises. */
+pimd_status pimd_batch_status(pimd_batch *b, int64_t *step, int64_t *steps_left);
+
+/* App. A estimators of every slot into out[0..max_replicas) (empty slots get
+ * step = -1).  Synchronises. */
+pimd_status pimd_batch_estimators(pimd_batch *b, pimd_estimates *out);
+
+/* State of one replica, as pimd_get_state. */
+pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double *x, double *v_nm, int64_t *step);
+
+/* Pick the step-kernel tile (atoms per block) for every bead count in the
+ * batch by timing candidates with CUDA events while the replicas step
+ * (steps_per_trial steps per candidate; they count toward the replicas'
+ * budgets; trajectories do not depend on the tile).  tiles_out, if not NULL,
+ * receives PIMD_MAX_BEADS + 1 entries: the chosen tile per P (0 = unused). */
+pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t *tiles_out);
+
+int64_t pimd_batch_kernel_launches(const pimd_batch *b);
+void pimd_batch_destroy(pimd_batch *b);
+
+/* ---- serving -----------------------------------------------------------------
+ * A server owns one batch and a worker thread.  Submitted jobs wait in a FIFO
+ * queue; between chunks of chunk_steps MD steps the worker admits queued jobs
+ * while their device memory (pimd_batch_replica_bytes) fits the HBM budget
+ * and a slot is free, so jobs that arrive while others run join the running
+ * batch (continuous batching); finished jobs leave it and free their memory.
+ * All server calls are thread-safe. */
+typedef struct pimd_server pimd_server;
+
+pimd_status pimd_server_create(size_t hbm_budget_bytes, int32_t max_replicas, int64_t chunk_steps,
+                               void *stream, pimd_server **out);
+
+/* Queue a job (arguments as pimd_batch_add; the arrays are copied).  EBUDGET
+ * if the job alone exceeds the budget; EINVAL for invalid arguments. */
+pimd_status pimd_batch_submit(pimd_server *s, const pimd_system *sys, int32_t P, double T, double dt,
+                              double gamma0, const pimd_params *params, int64_t nsteps, uint64_t *job);
+
+/* EPENDING while the job is queued or running; PIMD_OK once done (out, if not
+ * NULL, receives its final estimators); the job's own error otherwise
+ * (ENOMEM, ECUDA, ...); ENOTFOUND for unknown or cancelled jobs. */
+pimd_status pimd_batch_poll(pimd_server *s, uint64_t job, pimd_estimates *out);
+
+/* Cancel a queued or running job (its memory is freed at the next chunk
+ * boundary). */
+pimd_status pimd_batch_cancel(pimd_server *s, uint64_t job);
+
+/* Host wall-clock seconds (since the server was created) at which the job
+ * was submitted, admitted to the GPU and finished (-1 if not yet). */
+pimd_status pimd_server_job_times(pimd_server *s, uint64_t job, double *submitted, double *started,
+                                  double *finished);
+
+typedef struct {
+  int64_t submitted, completed, failed, running, queued;
+  size_t bytes_in_use;
+  int64_t chunks;
+  double bead_atom_steps;   /* total over completed chunks */
+  double gpu_busy_s;        /* wall time the worker spent running chunks */
+} pimd_server_stats;
+pimd_status pimd_server_stats_get(pimd_server *s, pimd_server_stats *out);
+
+/* Stop the worker (queued and running jobs are dropped) and free everything. */
+void pimd_server_destroy(pimd_server *s);
+
 /* ---- estimators without any allocation -----------------------------------
  * The paper has no counterpart to this entry point.  It computes the same
  * App. A outputs as pimd_estimators, but for a state held in the caller's

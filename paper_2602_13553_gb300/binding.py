@@ -85,7 +85,12 @@ class Estimates(ctypes.Structure):
 EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "pimd_last_error",
            "pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
            "pimd_set_state", "pimd_destroy", "pimd_set_kernel_timing", "pimd_kernel_times",
-           "pimd_kernel_launches", "pimd_estimators_noalloc")
+           "pimd_kernel_launches", "pimd_estimators_noalloc",
+           "pimd_batch_replica_bytes", "pimd_batch_create", "pimd_batch_add", "pimd_batch_remove",
+           "pimd_batch_run", "pimd_batch_sync", "pimd_batch_status", "pimd_batch_estimators",
+           "pimd_batch_get_state", "pimd_batch_autotune", "pimd_batch_kernel_launches",
+           "pimd_batch_destroy", "pimd_server_create", "pimd_batch_submit", "pimd_batch_poll",
+           "pimd_batch_cancel", "pimd_server_job_times", "pimd_server_stats_get", "pimd_server_destroy")
 KINDS = ("step", "force", "nbr", "close", "est", "other")
 
 _lock = threading.Lock()
@@ -270,3 +275,198 @@ class Simulation:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---------------------------------------------------------------------------
+# batches and serving
+# ---------------------------------------------------------------------------
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("running", ctypes.c_int64), ("queued", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
+                ("chunks", ctypes.c_int64), ("bead_atom_steps", ctypes.c_double),
+                ("gpu_busy_s", ctypes.c_double)]
+
+
+_batch_ready = False
+
+
+def _batch_lib():
+    global _batch_ready
+    L = lib()
+    if _batch_ready:
+        return L
+    vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    sysp, prmp = ctypes.POINTER(System), ctypes.POINTER(Params)
+    sig = {
+        "pimd_batch_replica_bytes": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_size_t),
+        "pimd_batch_create": ([ctypes.c_int32, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "pimd_batch_add": ([vp, sysp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, prmp,
+                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "pimd_batch_remove": ([vp, ctypes.c_int32], ctypes.c_int),
+        "pimd_batch_run": ([vp, ctypes.c_int64], ctypes.c_int),
+        "pimd_batch_sync": ([vp], ctypes.c_int),
+        "pimd_batch_status": ([vp, i64, i64], ctypes.c_int),
+        "pimd_batch_estimators": ([vp, ctypes.POINTER(Estimates)], ctypes.c_int),
+        "pimd_batch_get_state": ([vp, ctypes.c_int32, dp, dp, i64], ctypes.c_int),
+        "pimd_batch_autotune": ([vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "pimd_batch_kernel_launches": ([vp], ctypes.c_int64),
+        "pimd_batch_destroy": ([vp], None),
+        "pimd_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.c_int64, vp, ctypes.POINTER(vp)],
+                               ctypes.c_int),
+        "pimd_batch_submit": ([vp, sysp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, prmp,
+                               ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "pimd_batch_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(Estimates)], ctypes.c_int),
+        "pimd_batch_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
+        "pimd_server_job_times": ([vp, ctypes.c_uint64, dp, dp, dp], ctypes.c_int),
+        "pimd_server_stats_get": ([vp, ctypes.POINTER(ServerStats)], ctypes.c_int),
+        "pimd_server_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _batch_ready = True
+    return L
+
+
+def make_system(x0, mass, *, potential=POT_WATERLIKE, ff=(0.0,), box=(0.0, 0.0, 0.0), v0=None):
+    """A pimd_system over numpy arrays; the arrays are kept alive on the struct."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
+    s = System()
+    s.n_atoms = x0.shape[1]
+    s.potential = potential
+    s.mass, s.pos, s.vel = _dp(mass), _dp(x0), _dp(v0)
+    for a in range(3):
+        s.box[a] = float(box[a])
+    ffl = list(ff) + [0.0] * (8 - len(ff))
+    for a in range(8):
+        s.ff[a] = float(ffl[a])
+    s._keep = (x0, mass, v0)
+    return s
+
+
+def replica_bytes(n_atoms: int, P: int) -> int:
+    return int(_batch_lib().pimd_batch_replica_bytes(n_atoms, P))
+
+
+class Batch:
+    """Many independent water-like systems advanced together (pimd_batch)."""
+
+    def __init__(self, max_replicas: int, stream=None):
+        L = _batch_lib()
+        h = ctypes.c_void_p()
+        check(L.pimd_batch_create(max_replicas, ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self._h = h
+        self.capacity = max_replicas
+        self.shapes = {}
+
+    def add(self, x0, mass, *, T, dt, nsteps, ff, box, v0=None, gamma0=0.0, **params) -> int:
+        s = make_system(x0, mass, ff=ff, box=box, v0=v0)
+        prm = default_params(**params)
+        slot = ctypes.c_int32()
+        check(_batch_lib().pimd_batch_add(self._h, ctypes.byref(s), x0.shape[0], T, dt, gamma0,
+                                          ctypes.byref(prm), int(nsteps), ctypes.byref(slot)))
+        self.shapes[slot.value] = (x0.shape[0], x0.shape[1])
+        return slot.value
+
+    def remove(self, slot: int) -> None:
+        check(_batch_lib().pimd_batch_remove(self._h, slot))
+        self.shapes.pop(slot, None)
+
+    def run(self, nsteps: int) -> None:
+        check(_batch_lib().pimd_batch_run(self._h, int(nsteps)))
+
+    def sync(self) -> None:
+        check(_batch_lib().pimd_batch_sync(self._h))
+
+    def status(self):
+        st = (ctypes.c_int64 * self.capacity)()
+        left = (ctypes.c_int64 * self.capacity)()
+        check(_batch_lib().pimd_batch_status(self._h, st, left))
+        return np.array(st[:]), np.array(left[:])
+
+    def estimators(self):
+        arr = (Estimates * self.capacity)()
+        check(_batch_lib().pimd_batch_estimators(self._h, arr))
+        return {s: arr[s].as_dict() for s in range(self.capacity) if arr[s].step >= 0}
+
+    def get_state(self, slot: int):
+        P, N = self.shapes[slot]
+        x = np.empty((P, N, 3))
+        v = np.empty((P, N, 3))
+        st = ctypes.c_int64()
+        check(_batch_lib().pimd_batch_get_state(self._h, slot, _dp(x), _dp(v), ctypes.byref(st)))
+        return x, v, int(st.value)
+
+    def autotune(self, steps_per_trial: int = 2):
+        tiles = (ctypes.c_int32 * (MAX_BEADS + 1))()
+        check(_batch_lib().pimd_batch_autotune(self._h, steps_per_trial, tiles))
+        return {P: tiles[P] for P in range(MAX_BEADS + 1) if tiles[P] > 0}
+
+    def kernel_launches(self) -> int:
+        return int(_batch_lib().pimd_batch_kernel_launches(self._h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _batch_lib().pimd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching PIMD job server (pimd_server)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_replicas: int = 256, chunk_steps: int = 100, stream=None):
+        L = _batch_lib()
+        h = ctypes.c_void_p()
+        check(L.pimd_server_create(int(hbm_budget_bytes), max_replicas, chunk_steps,
+                                   ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, x0, mass, *, T, dt, nsteps, ff, box, v0=None, gamma0=0.0, **params) -> int:
+        s = make_system(x0, mass, ff=ff, box=box, v0=v0)
+        prm = default_params(**params)
+        job = ctypes.c_uint64()
+        check(_batch_lib().pimd_batch_submit(self._h, ctypes.byref(s), x0.shape[0], T, dt, gamma0,
+                                             ctypes.byref(prm), int(nsteps), ctypes.byref(job)))
+        return job.value
+
+    def poll(self, job: int):
+        """None while pending; the estimator dict once done; raises on failure."""
+        e = Estimates()
+        st = _batch_lib().pimd_batch_poll(self._h, job, ctypes.byref(e))
+        if st == 6:
+            return None
+        check(st)
+        return e.as_dict()
+
+    def cancel(self, job: int) -> None:
+        check(_batch_lib().pimd_batch_cancel(self._h, job))
+
+    def times(self, job: int):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(_batch_lib().pimd_server_job_times(self._h, job, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        check(_batch_lib().pimd_server_stats_get(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _batch_lib().pimd_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

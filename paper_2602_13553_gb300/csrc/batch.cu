@@ -1,0 +1,1676 @@
+// batch.cu -- many independent ring-polymer systems ("replicas") of uneven
+// size advanced together in split precision, and the serving layer on top.
+//
+// Every replica's state lives in its own device arena and is described by a
+// RepDesc in a device table.  Each MD step is four launches over all
+// replicas -- control, step, neighbour list, forces -- each a persistent grid
+// of fixed size that walks a device-resident work list (step tiles, force
+// clusters, neighbour blocks) whose length it reads from device memory.
+// Because neither grid sizes nor pointers change when replicas join or leave,
+// one CUDA graph of G steps is captured once per batch and replayed for the
+// batch's lifetime: continuous batching without re-capture.  Per-replica
+// step counters, step budgets and the "at integer time" flag live on the
+// device, so every replica runs exactly its own number of steps.
+//
+// A replica's arithmetic never depends on the other replicas or on the tile
+// size: the fused step is per (atom, component, mode) task, the force sums
+// depend only on the replica's interacting pairs (neighbour buckets keyed by
+// index), so a replica's trajectory is bitwise the same alone and in any mix.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "pimd.h"
+#include "runtime.h"
+
+namespace cg = cooperative_groups;
+
+namespace pimd {
+
+cudaError_t launch_pna_to_nap(const double *src, double *dst, int N, int P, cudaStream_t s);
+cudaError_t launch_nap_to_pna(const double *src, double *dst, int N, int P, cudaStream_t s);
+cudaError_t launch_thermal_v(double *v, const double *sigv, uint64_t seed, int N, int P, cudaStream_t s);
+cudaError_t launch_compress_split(const SplitStepArgs &a, const double *x, const double *v, cudaStream_t s);
+cudaError_t launch_expand_split(const SplitStepArgs &a, const float *F, double *x, double *v, double *Fd,
+                                cudaStream_t s);
+cudaError_t launch_centroids(const NbrArgs &a, double *ccur, cudaStream_t s);
+int water_lane_groups(int P);
+
+constexpr int kTileMax = 3 * kMaxBeads;   // largest A * 3 * P of a step tile
+constexpr int kOutStride = 3 * kMaxBeads + 10;  // pimd_estimates layout from K_mode on
+enum { kCtlStep = 0, kCtlLeft = 1, kCtlFirst = 2, kCtlActive = 3, kCtlClose = 4, kCtlWords = 8 };
+
+struct RepDesc {
+  int live, N, P, nmol, A, G, integrator, thermo;
+  int nstep_items, ne, pad0, pad1;
+  uint64_t seed;
+  double dt, tA, c1_0, c2_0, kT, volume, wn2;
+  double box[3], invbox[3];
+  double kb, r0, kth, th0, eps, sig, rc, rlist, skin;
+  long long *ctl;
+  double *xc, *v0;
+  float *d, *vk, *F, *xcw;
+  const double *inv_mm, *sigv, *mass_mm;
+  const float *Mf, *Mtf, *cAf, *sAf, *wsAf, *c1f, *c2f;
+  const double *Mt64, *lam;
+  double *cref, *ccur, *blkmax;
+  int *nbr, *nbr_off;
+  double *Upart, *Wpart, *epart;
+};
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// Per-replica control, one thread per slot.
+//   mode 0 (begin step): apply the previous step's advance, then mark the
+//                        replica active for this step if it has steps left
+//   mode 1 (finalize):   apply the last advance; a replica that stepped since
+//                        its last closing kick needs one now
+//   mode 2 (after close): the closed replicas are at integer time again
+__global__ void k_bctl(const RepDesc *reps, int nslots, int mode) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nslots || !reps[r].live) return;
+  long long *c = reps[r].ctl;
+  if (mode < 2 && c[kCtlActive]) {
+    c[kCtlStep] += 1;
+    c[kCtlLeft] -= 1;
+    c[kCtlFirst] = 0;
+    c[kCtlActive] = 0;
+  }
+  if (mode == 0) c[kCtlActive] = c[kCtlLeft] > 0;
+  if (mode == 1) c[kCtlClose] = c[kCtlFirst] == 0;
+  if (mode == 2 && c[kCtlClose]) {
+    c[kCtlFirst] = 1;
+    c[kCtlClose] = 0;
+  }
+}
+
+__device__ __forceinline__ float gauss1f_b(uint64_t seed, uint32_t atom, uint32_t mode, uint32_t stream,
+                                           uint64_t step, int d) {
+  const uint4 w = philox4x32_10(
+      make_uint4(atom, (mode & 0xffffu) | (stream << 16), (uint32_t)step, (uint32_t)(step >> 32)),
+      make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const uint32_t wa = d < 2 ? w.x : w.z;
+  const uint32_t wb = d < 2 ? w.y : w.w;
+  const float s = 5.9604644775390625e-8f;  // 2^-24
+  const float r = sqrtf(-2.0f * __logf(((float)(wa >> 8) + 0.5f) * s));
+  const float ang = 2.0f * (((float)(wb >> 8) + 0.5f) * s);
+  float sn, cs;
+  sincospif(ang, &sn, &cs);
+  return r * (d == 1 ? sn : cs);
+}
+
+__device__ __forceinline__ void rotb(float &q, float &v, float c, float s_over_w, float w_s) {
+  const float qn = fmaf(c, q, s_over_w * v);
+  const float vn = fmaf(-w_s, q, c * v);
+  q = qn;
+  v = vn;
+}
+
+__device__ __forceinline__ float wrapb(double x, double L, double invL) {
+  return (float)(x - L * floor(x * invL));
+}
+
+__device__ __forceinline__ float micb(float d, float L, float invL) { return fmaf(-rintf(d * invL), L, d); }
+
+// The split-precision fused step (same arithmetic as the single-system split
+// kernel) over work items (replica, tile).
+__global__ void __launch_bounds__(256) k_bstep(const RepDesc *reps, const int2 *items, const int *count) {
+  __shared__ float sD[kTileMax], sV[kTileMax], sF[kTileMax], sQ[kTileMax];
+  __shared__ double sred[2][8];
+  const int n = *count;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 w = items[it];
+    const RepDesc &R = reps[w.x];
+    if (!R.ctl[kCtlActive]) continue;
+    const int P = R.P, A = R.A, N = R.N;
+    const int tile0 = w.y * A;
+    const int na = min(A, N - tile0);
+    const int len = na * 3 * P;
+    const size_t base = (size_t)tile0 * 3 * P;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+      sD[t] = R.d[base + t];
+      sV[t] = R.vk[base + t];
+      sF[t] = R.F[base + t];
+    }
+    __syncthreads();
+    const uint64_t step = (uint64_t)R.ctl[kCtlStep];
+    const int first = (int)R.ctl[kCtlFirst];
+    const float hd = (float)R.dt, half = 0.5f * hd;
+    const float kick = first ? half : hd;
+    for (int task = threadIdx.x; task < len; task += blockDim.x) {
+      const int k = task % P;
+      const int r = task / P;
+      const int c = r % 3;
+      const int i = tile0 + r / 3;
+      const float *fx = sF + r * P;
+      const float *xx = sD + r * P;
+      float fa = 0.f, fb = 0.f, qa = 0.f, qb = 0.f;
+      int j = 0;
+      for (; j + 1 < P; j += 2) {
+        const float m0 = __ldg(R.Mtf + j * P + k), m1 = __ldg(R.Mtf + (j + 1) * P + k);
+        fa = fmaf(m0, fx[j], fa);
+        fb = fmaf(m1, fx[j + 1], fb);
+        qa = fmaf(m0, xx[j], qa);
+        qb = fmaf(m1, xx[j + 1], qb);
+      }
+      if (j < P) {
+        const float m0 = __ldg(R.Mtf + j * P + k);
+        fa = fmaf(m0, fx[j], fa);
+        qa = fmaf(m0, xx[j], qa);
+      }
+      const float f = fa + fb;
+      if (k == 0) {
+        sQ[task] = f;
+        continue;
+      }
+      float q = qa + qb;
+      float v = sV[task];
+      const float im = (float)__ldg(R.inv_mm + i);
+      const float cA = __ldg(R.cAf + k), sA = __ldg(R.sAf + k), wsA = __ldg(R.wsAf + k);
+      const float c1 = __ldg(R.c1f + k), c2s = __ldg(R.c2f + k) * (float)__ldg(R.sigv + i);
+      if (R.integrator == 0) {
+        v = fmaf(kick * im, f, v);
+        rotb(q, v, cA, sA, wsA);
+        if (R.thermo) v = fmaf(c1, v, c2s * gauss1f_b(R.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
+        rotb(q, v, cA, sA, wsA);
+      } else {
+        const float kb = half * im;
+        if (!first) {
+          v = fmaf(kb, f, v);
+          if (R.thermo)
+            v = fmaf(c1, v, c2s * gauss1f_b(R.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, c));
+        }
+        if (R.thermo) v = fmaf(c1, v, c2s * gauss1f_b(R.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
+        v = fmaf(kb, f, v);
+        rotb(q, v, cA, sA, wsA);
+      }
+      sQ[task] = q;
+      R.vk[base + task] = v;
+    }
+    __syncthreads();
+    const double rsp = rsqrt((double)P);
+    for (int t = threadIdx.x; t < na * 3; t += blockDim.x) {
+      const int al = t / 3, c = t % 3;
+      const int i = tile0 + al;
+      const size_t ic = (size_t)i * 3 + c;
+      const double f0 = (double)sQ[t * P];
+      double x = R.xc[ic], v = R.v0[ic];
+      const double im = __ldg(R.inv_mm + i);
+      const double dr = R.tA * rsp;
+      const double c2s = R.c2_0 * __ldg(R.sigv + i);
+      if (R.integrator == 0) {
+        v = fma((first ? 0.5 : 1.0) * R.dt * im, f0, v);
+        x = fma(dr, v, x);
+        if (R.thermo) v = fma(R.c1_0, v, c2s * (double)gauss1f_b(R.seed, (uint32_t)i, 0u, kStreamO1, step, c));
+        x = fma(dr, v, x);
+      } else {
+        const double kb = 0.5 * R.dt * im;
+        if (!first) {
+          v = fma(kb, f0, v);
+          if (R.thermo)
+            v = fma(R.c1_0, v, c2s * (double)gauss1f_b(R.seed, (uint32_t)i, 0u, kStreamO2, step - 1, c));
+        }
+        if (R.thermo) v = fma(R.c1_0, v, c2s * (double)gauss1f_b(R.seed, (uint32_t)i, 0u, kStreamO1, step, c));
+        v = fma(kb, f0, v);
+        x = fma(dr, v, x);
+      }
+      R.xc[ic] = x;
+      R.v0[ic] = v;
+      R.xcw[ic] = wrapb(x, R.box[c], R.invbox[c]);
+      sQ[t * P] = 0.f;
+    }
+    __syncthreads();
+    for (int task = threadIdx.x; task < len; task += blockDim.x) {
+      const int j = task % P;
+      const float *qq = sQ + (task / P) * P;
+      float xa = 0.f, xb = 0.f;
+      int k = 1;
+      for (; k + 1 < P; k += 2) {
+        xa = fmaf(__ldg(R.Mf + k * P + j), qq[k], xa);
+        xb = fmaf(__ldg(R.Mf + (k + 1) * P + j), qq[k + 1], xb);
+      }
+      if (k < P) xa = fmaf(__ldg(R.Mf + k * P + j), qq[k], xa);
+      const float dn = xa + xb;
+      R.d[base + task] = dn;
+      sD[task] = dn;
+    }
+    __syncthreads();
+    double vdisp = 0.0, vdev = 0.0;
+    for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
+      const int al = t / P, k = t % P;
+      const int i = tile0 + al;
+      if (i % 3) continue;
+      const float *ds = sD + al * 3 * P;
+      const float e0 = ds[k], e1 = ds[P + k], e2 = ds[2 * P + k];
+      vdev = fmax(vdev, (double)(e0 * e0 + e1 * e1 + e2 * e2));
+      if (k == 0) {
+        const int m = i / 3;
+        const double c0 = R.xc[3 * (size_t)i], c1 = R.xc[3 * (size_t)i + 1], c2 = R.xc[3 * (size_t)i + 2];
+        const double g0 = c0 - R.cref[3 * m], g1 = c1 - R.cref[3 * m + 1], g2 = c2 - R.cref[3 * m + 2];
+        vdisp = fmax(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
+        R.ccur[3 * m] = c0;
+        R.ccur[3 * m + 1] = c1;
+        R.ccur[3 * m + 2] = c2;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      vdisp = fmax(vdisp, __shfl_down_sync(0xffffffffu, vdisp, o));
+      vdev = fmax(vdev, __shfl_down_sync(0xffffffffu, vdev, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sred[0][threadIdx.x >> 5] = vdisp;
+      sred[1][threadIdx.x >> 5] = vdev;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double mx = 0.0;
+      for (int ww = 0; ww < (int)((blockDim.x + 31) / 32); ++ww) mx = fmax(mx, sred[threadIdx.x][ww]);
+      R.blkmax[2 * w.y + threadIdx.x] = (mx == mx) ? sqrt(mx) + 1e-4 : 1e300;
+    }
+    __syncthreads();
+  }
+}
+
+// Closing B(h/2) (O(h/2) for OBABO) of the replicas that stepped since their
+// last closing kick, over step items.
+__global__ void __launch_bounds__(256) k_bclose(const RepDesc *reps, const int2 *items, const int *count) {
+  __shared__ float sF[kTileMax];
+  const int n = *count;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 w = items[it];
+    const RepDesc &R = reps[w.x];
+    if (!R.ctl[kCtlClose]) continue;
+    const int P = R.P, A = R.A;
+    const int tile0 = w.y * A;
+    const int na = min(A, R.N - tile0);
+    const int len = na * 3 * P;
+    const size_t base = (size_t)tile0 * 3 * P;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) sF[t] = R.F[base + t];
+    __syncthreads();
+    const uint64_t step = (uint64_t)R.ctl[kCtlStep] - 1;
+    for (int task = threadIdx.x; task < len; task += blockDim.x) {
+      const int k = task % P;
+      const int r = task / P;
+      const int c = r % 3;
+      const int i = tile0 + r / 3;
+      const float *fx = sF + r * P;
+      float fa = 0.f, fb = 0.f;
+      int j = 0;
+      for (; j + 1 < P; j += 2) {
+        fa = fmaf(__ldg(R.Mtf + j * P + k), fx[j], fa);
+        fb = fmaf(__ldg(R.Mtf + (j + 1) * P + k), fx[j + 1], fb);
+      }
+      if (j < P) fa = fmaf(__ldg(R.Mtf + j * P + k), fx[j], fa);
+      const float f = fa + fb;
+      if (k == 0) {
+        const size_t ic = (size_t)i * 3 + c;
+        double v = fma(0.5 * R.dt * __ldg(R.inv_mm + i), (double)f, R.v0[ic]);
+        if (R.integrator == 1 && R.thermo)
+          v = fma(R.c1_0, v, R.c2_0 * __ldg(R.sigv + i) *
+                                 (double)gauss1f_b(R.seed, (uint32_t)i, 0u, kStreamO2, step, c));
+        R.v0[ic] = v;
+        continue;
+      }
+      float v = fmaf(0.5f * (float)R.dt * (float)__ldg(R.inv_mm + i), f, R.vk[base + task]);
+      if (R.integrator == 1 && R.thermo) {
+        const float c1 = __ldg(R.c1f + k), c2s = __ldg(R.c2f + k) * (float)__ldg(R.sigv + i);
+        v = fmaf(c1, v, c2s * gauss1f_b(R.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step, c));
+      }
+      R.vk[base + task] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Neighbour lists, work items (replica, block of 128 molecules).  The skin
+// criterion of the single-system build is evaluated per replica over its own
+// step tiles; force_all rebuilds unconditionally (new replicas).
+__global__ void k_bnbr(const RepDesc *reps, const int2 *items, const int *count, int force_all) {
+  __shared__ double sd[128], se[128];
+  __shared__ int s_go;
+  const int n = *count;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 w = items[it];
+    const RepDesc &R = reps[w.x];
+    if (!force_all && !R.ctl[kCtlActive]) continue;
+    double md = 0.0, me = 0.0;
+    for (int b = threadIdx.x; b < R.nstep_items; b += blockDim.x) {
+      md = fmax(md, R.blkmax[2 * b]);
+      me = fmax(me, R.blkmax[2 * b + 1]);
+    }
+    sd[threadIdx.x] = md;
+    se[threadIdx.x] = me;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + st]);
+        se[threadIdx.x] = fmax(se[threadIdx.x], se[threadIdx.x + st]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) s_go = force_all || (2.0 * sd[0] + 2.0 * se[0] > R.skin);
+    __syncthreads();
+    const int m = w.y * 128 + threadIdx.x;
+    if (s_go && m < R.nmol) {
+      const int NS = kLJWarps * R.G;
+      const double c0 = R.ccur[3 * m], c1 = R.ccur[3 * m + 1], c2 = R.ccur[3 * m + 2];
+      const double rl2 = R.rlist * R.rlist;
+      int cnt[kMaxBuckets];
+      for (int b = 0; b < NS; ++b) cnt[b] = 0;
+      int nn = 0;
+      for (int j = 0; j < R.nmol; ++j) {
+        if (j == m) continue;
+        const double d0 = mic(R.ccur[3 * j] - c0, R.box[0], R.invbox[0]);
+        const double d1 = mic(R.ccur[3 * j + 1] - c1, R.box[1], R.invbox[1]);
+        const double d2 = mic(R.ccur[3 * j + 2] - c2, R.box[2], R.invbox[2]);
+        if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
+          ++cnt[j % NS];
+          ++nn;
+        }
+      }
+      int *off = R.nbr_off + (size_t)m * (NS + 1);
+      if (nn > kMaxNeighbours) {
+        R.ctl[kCtlWords - 1] |= kErrNbrOverflow;
+        for (int b = 0; b <= NS; ++b) off[b] = 0;
+      } else {
+        int acc = 0;
+        for (int b = 0; b < NS; ++b) {
+          off[b] = acc;
+          acc += cnt[b];
+          cnt[b] = 0;
+        }
+        off[NS] = acc;
+        int *nl = R.nbr + (size_t)m * kMaxNeighbours;
+        for (int j = 0; j < R.nmol; ++j) {
+          if (j == m) continue;
+          const double d0 = mic(R.ccur[3 * j] - c0, R.box[0], R.invbox[0]);
+          const double d1 = mic(R.ccur[3 * j + 1] - c1, R.box[1], R.invbox[1]);
+          const double d2 = mic(R.ccur[3 * j + 2] - c2, R.box[2], R.invbox[2]);
+          if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
+            const int b = j % NS;
+            nl[off[b] + cnt[b]++] = j;
+          }
+        }
+        R.cref[3 * m] = c0;
+        R.cref[3 * m + 1] = c1;
+        R.cref[3 * m + 2] = c2;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Water-like forces in FP32 over cluster work items (replica, molecule,
+// bead chunk): the decomposition of the single-system split kernel.
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128)
+    k_bforce(const RepDesc *reps, const int4 *items, const int *count, int force_all) {
+  __shared__ float sacc[9][128];
+  __shared__ double saccd[2][128];
+  __shared__ float red[9][32];
+  __shared__ double redd[2][32];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int n = *count;
+  const int ncl = gridDim.x >> 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = rank * 4 + warp;
+  for (int it = blockIdx.x >> 2; it < n; it += ncl) {
+    const int4 w = items[it];
+    const RepDesc &R = reps[w.x];
+    if (!force_all && !R.ctl[kCtlActive]) continue;
+    const int P = R.P, m = w.y, chunk = w.z;
+    const int Bk = P < 32 ? P : 32;
+    const int G = R.G;
+    const int NS = kLJWarps * G;
+    const int u = lane / Bk, kl = lane % Bk;
+    const int k = chunk * Bk + kl;
+    float acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
+    double ue = 0.0, we = 0.0;
+    if (u < G && k < P) {
+      const int o = 3 * m;
+      const float L0 = (float)R.box[0], L1 = (float)R.box[1], L2 = (float)R.box[2];
+      const float i0 = (float)R.invbox[0], i1 = (float)R.invbox[1], i2 = (float)R.invbox[2];
+      const size_t so = (size_t)o * 3 * P + k;
+      const float co0 = R.xcw[3 * o], co1 = R.xcw[3 * o + 1], co2 = R.xcw[3 * o + 2];
+      const float do0 = R.d[so], do1 = R.d[so + P], do2 = R.d[so + 2 * P];
+      if (s >= kLJWarps) {
+        if (u == 0) {
+          float dv[2][3], r[2], ir[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int hh = o + 1 + h;
+            const size_t sh = (size_t)hh * 3 * P + k;
+            dv[h][0] = micb(R.xcw[3 * hh] - co0, L0, i0) + (R.d[sh] - do0);
+            dv[h][1] = micb(R.xcw[3 * hh + 1] - co1, L1, i1) + (R.d[sh + P] - do1);
+            dv[h][2] = micb(R.xcw[3 * hh + 2] - co2, L2, i2) + (R.d[sh + 2 * P] - do2);
+            r[h] = sqrtf(dv[h][0] * dv[h][0] + dv[h][1] * dv[h][1] + dv[h][2] * dv[h][2]);
+            ir[h] = 1.f / r[h];
+          }
+          float uu = 0.f, ww = 0.f;
+          if (s == kLJWarps) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float dr = r[h] - (float)R.r0;
+              uu = fmaf(0.5f * (float)R.kb * dr, dr, uu);
+              const float g = -(float)R.kb * dr * ir[h];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const float fc = g * dv[h][c];
+                acc[3 + 3 * h + c] = fc;
+                acc[c] -= fc;
+                ww = fmaf(dv[h][c], fc, ww);
+              }
+            }
+          } else {
+            const float ir01 = ir[0] * ir[1];
+            const float dot = dv[0][0] * dv[1][0] + dv[0][1] * dv[1][1] + dv[0][2] * dv[1][2];
+            const float cth = fminf(1.f, fmaxf(-1.f, dot * ir01));
+            const float th = acosf(cth);
+            const float dth = th - (float)R.th0;
+            const float pref = (float)R.kth * dth / sinf(th);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int g = 1 - h;
+              const float ch = cth * ir[h] * ir[h];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const float fa = pref * fmaf(dv[g][c], ir01, -ch * dv[h][c]);
+                acc[3 + 3 * h + c] = fa;
+                acc[c] -= fa;
+                ww = fmaf(dv[h][c], fa, ww);
+              }
+            }
+            uu = 0.5f * (float)R.kth * dth * dth;
+          }
+          ue = uu;
+          we = ww;
+        }
+      } else {
+        const int b = s * G + u;
+        const int *off = R.nbr_off + (size_t)m * (NS + 1);
+        const int q0 = __ldg(off + b), q1 = __ldg(off + b + 1);
+        const int *nl = R.nbr + (size_t)m * kMaxNeighbours;
+        const float rc2 = (float)(R.rc * R.rc);
+        const float sig2 = (float)(R.sig * R.sig);
+        const float e4 = (float)(4.0 * R.eps), e24 = (float)(24.0 * R.eps);
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, ulj = 0.f, wlj = 0.f;
+        for (int q = q0; q < q1; ++q) {
+          const int j = __ldg(nl + q);
+          const size_t sj = (size_t)(3 * j) * 3 * P + k;
+          const float d0 = micb(__ldg(R.xcw + 9 * j) - co0, L0, i0) + (__ldg(R.d + sj) - do0);
+          const float d1 = micb(__ldg(R.xcw + 9 * j + 1) - co1, L1, i1) + (__ldg(R.d + sj + P) - do1);
+          const float d2 = micb(__ldg(R.xcw + 9 * j + 2) - co2, L2, i2) + (__ldg(R.d + sj + 2 * P) - do2);
+          const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+          if (r2 < rc2) {
+            const float inv = 1.f / r2;
+            const float s2 = sig2 * inv;
+            const float s6 = s2 * s2 * s2;
+            ulj = fmaf(e4, fmaf(s6, s6, -s6), ulj);
+            const float fr = e24 * fmaf(2.f * s6, s6, -s6) * inv;
+            f0 = fmaf(-fr, d0, f0);
+            f1 = fmaf(-fr, d1, f1);
+            f2 = fmaf(-fr, d2, f2);
+            wlj = fmaf(fr, r2, wlj);
+          }
+        }
+        acc[0] = f0;
+        acc[1] = f1;
+        acc[2] = f2;
+        ue = 0.5 * (double)ulj;
+        we = 0.5 * (double)wlj;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sacc[c][threadIdx.x] = acc[c];
+    saccd[0][threadIdx.x] = ue;
+    saccd[1][threadIdx.x] = we;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
+      const int comp = t / Bk, kk = t % Bk;
+      if (comp < 9) {
+        float sum = 0.f;
+        for (int ww = 0; ww < 4; ++ww)
+          for (int g = 0; g < G; ++g) sum += sacc[comp][ww * 32 + g * Bk + kk];
+        red[comp][kk] = sum;
+      } else {
+        double sum = 0.0;
+        for (int ww = 0; ww < 4; ++ww)
+          for (int g = 0; g < G; ++g) sum += saccd[comp - 9][ww * 32 + g * Bk + kk];
+        redd[comp - 9][kk] = sum;
+      }
+    }
+    cluster.sync();
+    if (rank == 0) {
+      for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
+        const int comp = t / Bk, kk = t % Bk;
+        const int k2 = chunk * Bk + kk;
+        if (k2 >= P) continue;
+        if (comp < 9) {
+          float sum = 0.f;
+          for (int rr = 0; rr < 4; ++rr) sum += cluster.map_shared_rank(&red[0][0], rr)[comp * 32 + kk];
+          R.F[(size_t)(3 * m + comp / 3) * 3 * P + (comp % 3) * P + k2] = sum;
+        } else {
+          double sum = 0.0;
+          for (int rr = 0; rr < 4; ++rr) sum += cluster.map_shared_rank(&redd[0][0], rr)[(comp - 9) * 32 + kk];
+          if (comp == 9)
+            R.Upart[(size_t)m * P + k2] = sum;
+          else
+            R.Wpart[(size_t)m * P + k2] = sum;
+        }
+      }
+    }
+    cluster.sync();
+  }
+}
+
+// Estimators, pass 1: work items (replica, e-block); e-block b walks the
+// replica's tiles b, b + ne, ... in FP64 (x = xc + d; q~_k from the FP64
+// matrix and the FP32 deviations; r - r_c = d - mean_j d_j).
+__global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *items, const int *count) {
+  __shared__ double sK[128], sS[128];
+  __shared__ double sred[3][4];
+  const int n = *count;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 w = items[it];
+    const RepDesc &R = reps[w.x];
+    const int P = R.P, A = R.A, N = R.N;
+    const int ntask = A * P;
+    double kk = 0.0, ss = 0.0, rF = 0.0, rcF = 0.0, mv0 = 0.0;
+    for (int tile = w.y; tile < R.nstep_items; tile += R.ne) {
+      const int tile0 = tile * A;
+      for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+        const int k = task % P, al = task / P;
+        const int i = tile0 + al;
+        if (i >= N) continue;
+        const double mm = __ldg(R.mass_mm + i);
+        double v2 = 0.0, q2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          const size_t row = ((size_t)i * 3 + c) * P;
+          const double v = k == 0 ? R.v0[(size_t)i * 3 + c] : (double)R.vk[row + k];
+          v2 += v * v;
+          double q = 0.0, dm = 0.0;
+          for (int j = 0; j < P; ++j) {
+            const double dj = (double)R.d[row + j];
+            q = fma(__ldg(R.Mt64 + j * P + k), dj, q);
+            dm += dj;
+          }
+          if (k > 0) q2 += q * q;
+          const double dk = (double)R.d[row + k];
+          const double xk = R.xc[(size_t)i * 3 + c] + dk;
+          const double fk = (double)R.F[row + k];
+          rF += xk * fk;
+          rcF += (dk - dm / P) * fk;
+        }
+        kk += 0.5 * mm * v2;
+        ss += 0.5 * mm * R.wn2 * __ldg(R.lam + k) * q2;
+        if (k == 0) mv0 += mm * v2;
+      }
+    }
+    // per-mode sums: tile tasks never exceed the 128 threads (A P <= 85), so
+    // thread t always held task t, i.e. mode t mod P; sum over atoms in order
+    double *out = R.epart + (size_t)w.y * (2 * P + 4);
+    sK[threadIdx.x] = kk;
+    sS[threadIdx.x] = ss;
+    __syncthreads();
+    for (int k = threadIdx.x; k < P; k += blockDim.x) {
+      double a = 0.0, b2 = 0.0;
+      for (int t = k; t < ntask; t += P) {
+        a += sK[t];
+        b2 += sS[t];
+      }
+      out[k] = a;
+      out[P + k] = b2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rF += __shfl_down_sync(0xffffffffu, rF, o);
+      rcF += __shfl_down_sync(0xffffffffu, rcF, o);
+      mv0 += __shfl_down_sync(0xffffffffu, mv0, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      sred[0][threadIdx.x >> 5] = rF;
+      sred[1][threadIdx.x >> 5] = rcF;
+      sred[2][threadIdx.x >> 5] = mv0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double sum = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) sum += sred[threadIdx.x][ww];
+      out[2 * P + threadIdx.x] = sum;
+    }
+    if (threadIdx.x == 3) out[2 * P + 3] = 0.0;
+    __syncthreads();
+  }
+}
+
+// Control words of every slot gathered into one array (one copy to the host).
+__global__ void k_bgather_ctl(const RepDesc *reps, int nslots, long long *out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nslots) return;
+  for (int w = 0; w < kCtlWords; ++w) out[(size_t)r * kCtlWords + w] = reps[r].live ? reps[r].ctl[w] : -1;
+}
+
+__device__ double neumaier_b(const double *p, int n, size_t stride) {
+  double s = 0.0, c = 0.0;
+  for (int b = 0; b < n; ++b) {
+    const double x = p[(size_t)b * stride];
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  return s + c;
+}
+
+// Estimators, pass 2: one block per replica; output in the pimd_estimates
+// layout from K_mode on.
+__global__ void k_best_final(const RepDesc *reps, int nslots, double *eout) {
+  __shared__ double tot[2 * kMaxBeads + 4];
+  __shared__ double U[kMaxBeads], Wv[kMaxBeads];
+  const int r = blockIdx.x;
+  if (r >= nslots) return;
+  const RepDesc &R = reps[r];
+  if (!R.live) return;
+  const int P = R.P;
+  const int W = 2 * P + 4;
+  for (int s = threadIdx.x; s < W; s += blockDim.x) tot[s] = neumaier_b(R.epart + s, R.ne, W);
+  for (int k = threadIdx.x; k < P; k += blockDim.x) {
+    U[k] = neumaier_b(R.Upart + k, R.nmol, P);
+    Wv[k] = neumaier_b(R.Wpart + k, R.nmol, P);
+  }
+  double *o = eout + (size_t)r * kOutStride;
+  for (int k = threadIdx.x; k < 3 * kMaxBeads; k += blockDim.x) o[k] = 0.0;
+  __syncthreads();
+  if (threadIdx.x) return;
+  double Kt = 0.0, St = 0.0, Ut = 0.0, Wt = 0.0;
+  for (int k = 0; k < P; ++k) {
+    o[k] = tot[k];
+    o[kMaxBeads + k] = tot[P + k];
+    o[2 * kMaxBeads + k] = U[k];
+    Kt += tot[k];
+    St += tot[P + k];
+    Ut += U[k];
+    Wt += Wv[k];
+  }
+  const double rF = tot[2 * P], rcF = tot[2 * P + 1], mv0 = tot[2 * P + 2];
+  const double Nd = R.N, Pd = P, kT = R.kT, V = R.volume, spring = 2.0 * St;
+  double *g = o + 3 * kMaxBeads;
+  g[0] = Kt + St + Ut;
+  g[1] = 1.5 * Pd * Nd * kT - 0.5 * spring / Pd;
+  g[2] = -rF / (2.0 * Pd);
+  g[3] = 1.5 * Nd * kT - rcF / (2.0 * Pd);
+  g[4] = (3.0 * Pd * Nd * kT - spring / Pd + Wt / Pd) / (3.0 * V);
+  g[5] = (2.0 * Kt + Wt) / (3.0 * V);
+  g[6] = (mv0 - rcF + Wt) / (3.0 * Pd * V);
+  g[7] = 2.0 * Kt / (3.0 * Nd * Pd * kBoltzmann);
+  g[8] = V;
+  g[9] = Wt;
+}
+
+}  // namespace pimd
+
+// ===========================================================================
+// host side: the batch engine
+// ===========================================================================
+namespace pimd {
+
+namespace {
+
+struct Replica {
+  bool live = false;
+  int N = 0, P = 0, nmol = 0, A = 1, G = 1, ntiles = 0, ne = 0;
+  size_t bytes = 0;
+  void *arena = nullptr;
+  RepDesc desc{};
+  std::vector<int2> items_step, items_nbr, items_est;
+  std::vector<int4> items_clu;
+  int2 *d_items_step = nullptr, *d_items_nbr = nullptr;
+  int4 *d_items_clu = nullptr;
+  int *d_counts = nullptr;   // [4] own item counts: step, cluster, nbr, est
+};
+
+template <typename T>
+T *carve_ptr(char *base, size_t &off, size_t count) {
+  off = (off + 255) & ~(size_t)255;
+  T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+  off += count * sizeof(T);
+  return p;
+}
+
+// Lay out (base == nullptr: size) a replica arena and fill the descriptor
+// pointers.  Step tiles may use any A >= 1, so per-tile arrays are sized for
+// A = 1 (one tile per atom).
+size_t layout_replica(Replica &r, char *base) {
+  const size_t N = r.N, P = r.P, len = N * 3 * P, nmol = r.nmol;
+  const int NS = kLJWarps * r.G;
+  RepDesc &d = r.desc;
+  size_t off = 0;
+  d.ctl = carve_ptr<long long>(base, off, kCtlWords);
+  d.xc = carve_ptr<double>(base, off, N * 3);
+  d.v0 = carve_ptr<double>(base, off, N * 3);
+  d.d = carve_ptr<float>(base, off, len);
+  d.vk = carve_ptr<float>(base, off, len);
+  d.F = carve_ptr<float>(base, off, len);
+  d.xcw = carve_ptr<float>(base, off, N * 3);
+  d.inv_mm = carve_ptr<double>(base, off, N);
+  d.sigv = carve_ptr<double>(base, off, N);
+  d.mass_mm = carve_ptr<double>(base, off, N);
+  d.Mf = carve_ptr<float>(base, off, P * P);
+  d.Mtf = carve_ptr<float>(base, off, P * P);
+  d.cAf = carve_ptr<float>(base, off, P);
+  d.sAf = carve_ptr<float>(base, off, P);
+  d.wsAf = carve_ptr<float>(base, off, P);
+  d.c1f = carve_ptr<float>(base, off, P);
+  d.c2f = carve_ptr<float>(base, off, P);
+  d.Mt64 = carve_ptr<double>(base, off, P * P);
+  d.lam = carve_ptr<double>(base, off, P);
+  d.cref = carve_ptr<double>(base, off, nmol * 3);
+  d.ccur = carve_ptr<double>(base, off, nmol * 3);
+  d.blkmax = carve_ptr<double>(base, off, 2 * N);
+  d.nbr = carve_ptr<int>(base, off, nmol * kMaxNeighbours);
+  d.nbr_off = carve_ptr<int>(base, off, nmol * (NS + 1));
+  d.Upart = carve_ptr<double>(base, off, nmol * P);
+  d.Wpart = carve_ptr<double>(base, off, nmol * P);
+  d.epart = carve_ptr<double>(base, off, 8 * (2 * P + 4));
+  r.d_items_step = carve_ptr<int2>(base, off, N);
+  r.d_items_nbr = carve_ptr<int2>(base, off, (nmol + 127) / 128);
+  r.d_items_clu = carve_ptr<int4>(base, off, nmol * ((P + 31) / 32));
+  r.d_counts = carve_ptr<int>(base, off, 4);
+  return off + 256;
+}
+
+int default_tile(int P) { return std::max(1, 256 / (3 * P)); }
+
+}  // namespace
+}  // namespace pimd
+
+using namespace pimd;
+
+struct pimd_batch {
+  int capacity = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevAllocator alloc;
+  std::vector<Replica> reps;
+  RepDesc *d_reps = nullptr;
+  int *d_counts = nullptr;                 // [4]: step, cluster, nbr, est items (all replicas)
+  int2 *d_step = nullptr, *d_nbr = nullptr, *d_est = nullptr;
+  int4 *d_clu = nullptr;
+  size_t cap_step = 0, cap_clu = 0, cap_nbr = 0, cap_est = 0;
+  double *d_eout = nullptr, *h_eout = nullptr;
+  long long *d_ctl = nullptr, *h_ctl = nullptr;   // gathered per-replica control words
+  double *stg_x = nullptr, *stg_v = nullptr, *stg_t = nullptr;
+  size_t stg_len = 0;
+  int grid_step = 0, grid_clu = 0, grid_nbr = 0, grid_est = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 8;
+  bool dirty = true;
+  int64_t launches = 0;
+  int tileA[PIMD_MAX_BEADS + 1] = {0};     // autotuned step tile per P (0 = default)
+  std::vector<int2> h_step, h_nbr, h_est;
+  std::vector<int4> h_clu;
+  int h_counts[4] = {0, 0, 0, 0};
+};
+
+namespace hostside {
+
+#define BK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(PIMD_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                 \
+  } while (0)
+
+template <typename T>
+pimd_status grow(pimd_batch *b, T **ptr, size_t *cap, size_t need) {
+  if (need <= *cap && *ptr) return PIMD_OK;
+  size_t nc = std::max<size_t>(need, std::max<size_t>(1024, 2 * *cap));
+  BK(cudaStreamSynchronize(b->stream));
+  dev_free(b->alloc, *ptr, b->stream);
+  *ptr = (T *)dev_alloc(b->alloc, nc * sizeof(T), b->stream);
+  if (!*ptr) return fail(PIMD_ENOMEM, "batch work-list allocation failed");
+  *cap = nc;
+  if (b->graph) {   // the captured kernels point at the old array
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return PIMD_OK;
+}
+
+void replica_items(pimd_batch *b, int slot, Replica &r) {
+  r.A = b->tileA[r.P] > 0 ? b->tileA[r.P] : default_tile(r.P);
+  r.ntiles = (r.N + r.A - 1) / r.A;
+  r.ne = std::min(r.ntiles, 8);
+  r.items_step.clear();
+  for (int t = 0; t < r.ntiles; ++t) r.items_step.push_back(make_int2(slot, t));
+  r.items_nbr.clear();
+  for (int mb = 0; mb < (r.nmol + 127) / 128; ++mb) r.items_nbr.push_back(make_int2(slot, mb));
+  r.items_clu.clear();
+  const int nchunk = (r.P + 31) / 32;
+  for (int m = 0; m < r.nmol; ++m)
+    for (int c = 0; c < nchunk; ++c) r.items_clu.push_back(make_int4(slot, m, c, 0));
+  r.items_est.clear();
+  for (int e = 0; e < r.ne; ++e) r.items_est.push_back(make_int2(slot, e));
+  r.desc.A = r.A;
+  r.desc.nstep_items = r.ntiles;
+  r.desc.ne = r.ne;
+}
+
+// Upload the descriptor table and the concatenated work lists (stream-ordered
+// after every earlier launch that reads them).
+pimd_status upload(pimd_batch *b) {
+  b->h_step.clear();
+  b->h_clu.clear();
+  b->h_nbr.clear();
+  b->h_est.clear();
+  std::vector<RepDesc> descs(b->capacity);
+  for (int s = 0; s < b->capacity; ++s) {
+    Replica &r = b->reps[s];
+    if (r.live) {
+      b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
+      b->h_clu.insert(b->h_clu.end(), r.items_clu.begin(), r.items_clu.end());
+      b->h_nbr.insert(b->h_nbr.end(), r.items_nbr.begin(), r.items_nbr.end());
+      b->h_est.insert(b->h_est.end(), r.items_est.begin(), r.items_est.end());
+      descs[s] = r.desc;
+    } else {
+      std::memset(&descs[s], 0, sizeof(RepDesc));
+    }
+  }
+  pimd_status st;
+  if ((st = grow(b, &b->d_step, &b->cap_step, b->h_step.size() + 1)) ||
+      (st = grow(b, &b->d_clu, &b->cap_clu, b->h_clu.size() + 1)) ||
+      (st = grow(b, &b->d_nbr, &b->cap_nbr, b->h_nbr.size() + 1)) ||
+      (st = grow(b, &b->d_est, &b->cap_est, b->h_est.size() + 1)))
+    return st;
+  b->h_counts[0] = (int)b->h_step.size();
+  b->h_counts[1] = (int)b->h_clu.size();
+  b->h_counts[2] = (int)b->h_nbr.size();
+  b->h_counts[3] = (int)b->h_est.size();
+  if (!b->h_step.empty())
+    BK(cudaMemcpyAsync(b->d_step, b->h_step.data(), b->h_step.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  if (!b->h_clu.empty())
+    BK(cudaMemcpyAsync(b->d_clu, b->h_clu.data(), b->h_clu.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+  if (!b->h_nbr.empty())
+    BK(cudaMemcpyAsync(b->d_nbr, b->h_nbr.data(), b->h_nbr.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  if (!b->h_est.empty())
+    BK(cudaMemcpyAsync(b->d_est, b->h_est.data(), b->h_est.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
+  BK(cudaMemcpyAsync(b->d_counts, b->h_counts, sizeof(b->h_counts), cudaMemcpyHostToDevice, b->stream));
+  BK(cudaMemcpyAsync(b->d_reps, descs.data(), sizeof(RepDesc) * b->capacity, cudaMemcpyHostToDevice, b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  b->dirty = false;
+  return PIMD_OK;
+}
+
+// One MD step of every active replica.
+cudaError_t launch_one_step(pimd_batch *b, cudaEvent_t e0, cudaEvent_t e1) {
+  k_bctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, 0);
+  if (e0) cudaEventRecord(e0, b->stream);
+  k_bstep<<<b->grid_step, 256, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+  if (e1) cudaEventRecord(e1, b->stream);
+  k_bnbr<<<b->grid_nbr, 128, 0, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, 0);
+  k_bforce<<<4 * b->grid_clu, 128, 0, b->stream>>>(b->d_reps, b->d_clu, b->d_counts + 1, 0);
+  return cudaGetLastError();
+}
+
+pimd_status capture(pimd_batch *b) {
+  cudaGraph_t g = nullptr;
+  BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < b->graph_steps && e == cudaSuccess; ++s) e = launch_one_step(b, nullptr, nullptr);
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(PIMD_ECUDA, "batch graph capture failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return fail(PIMD_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  return PIMD_OK;
+}
+
+pimd_status ensure_staging(pimd_batch *b, size_t len) {
+  if (len <= b->stg_len && b->stg_x) return PIMD_OK;
+  BK(cudaStreamSynchronize(b->stream));
+  dev_free(b->alloc, b->stg_x, b->stream);
+  b->stg_x = (double *)dev_alloc(b->alloc, 3 * len * sizeof(double), b->stream);
+  if (!b->stg_x) {
+    b->stg_len = 0;
+    return fail(PIMD_ENOMEM, "batch staging allocation failed");
+  }
+  b->stg_v = b->stg_x + len;
+  b->stg_t = b->stg_v + len;
+  b->stg_len = len;
+  return PIMD_OK;
+}
+
+SplitStepArgs replica_split_args(const Replica &r) {
+  SplitStepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.N = r.N;
+  a.P = r.P;
+  a.A = r.A;
+  a.xc = r.desc.xc;
+  a.v0 = r.desc.v0;
+  a.d = r.desc.d;
+  a.vk = r.desc.vk;
+  a.F = r.desc.F;
+  a.xcw = r.desc.xcw;
+  for (int c = 0; c < 3; ++c) {
+    a.box[c] = r.desc.box[c];
+    a.invbox[c] = r.desc.invbox[c];
+  }
+  return a;
+}
+
+}  // namespace hostside
+using namespace hostside;
+
+size_t batch_replica_bytes(int N, int P) {
+  Replica r;
+  r.N = N;
+  r.P = P;
+  r.nmol = N / 3;
+  r.G = water_lane_groups(P);
+  return layout_replica(r, nullptr);
+}
+
+extern "C" size_t pimd_batch_replica_bytes(int32_t n_atoms, int32_t P) {
+  if (n_atoms <= 0 || P < 1 || P > PIMD_MAX_BEADS) return 0;
+  return batch_replica_bytes(n_atoms, P);
+}
+
+extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pimd_batch **out) {
+  if (!out) return fail(PIMD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_replicas < 1 || max_replicas > 65536) return fail(PIMD_EINVAL, "max_replicas outside 1..65536");
+  pimd_batch *b = new pimd_batch();
+  b->capacity = max_replicas;
+  b->reps.resize(max_replicas);
+  b->alloc = current_allocator();
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return fail(PIMD_ECUDA, "cudaStreamCreate failed");
+    }
+    b->own_stream = true;
+  }
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // persistent grids sized to the SM count (resident blocks per SM)
+  b->grid_step = nsm * 4;
+  b->grid_clu = nsm * 4;
+  b->grid_nbr = nsm * 2;
+  b->grid_est = nsm * 2;
+  auto fail_free = [&](pimd_status st) {
+    pimd_batch_destroy(b);
+    return st;
+  };
+  b->d_reps = (RepDesc *)dev_alloc(b->alloc, sizeof(RepDesc) * max_replicas, b->stream);
+  b->d_counts = (int *)dev_alloc(b->alloc, 4 * sizeof(int), b->stream);
+  b->d_eout = (double *)dev_alloc(b->alloc, sizeof(double) * kOutStride * max_replicas, b->stream);
+  b->d_ctl = (long long *)dev_alloc(b->alloc, sizeof(long long) * kCtlWords * max_replicas, b->stream);
+  if (!b->d_reps || !b->d_counts || !b->d_eout || !b->d_ctl)
+    return fail_free(fail(PIMD_ENOMEM, "batch allocation failed"));
+  if (cudaMallocHost(&b->h_eout, sizeof(double) * kOutStride * max_replicas) != cudaSuccess ||
+      cudaMallocHost(&b->h_ctl, sizeof(long long) * kCtlWords * max_replicas) != cudaSuccess)
+    return fail_free(fail(PIMD_ENOMEM, "pinned allocation failed"));
+  pimd_status st = upload(b);
+  if (st != PIMD_OK) return fail_free(st);
+  *out = b;
+  return PIMD_OK;
+}
+
+extern "C" void pimd_batch_destroy(pimd_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto &r : b->reps)
+    if (r.arena) dev_free(b->alloc, r.arena, b->stream);
+  dev_free(b->alloc, b->d_reps, b->stream);
+  dev_free(b->alloc, b->d_counts, b->stream);
+  dev_free(b->alloc, b->d_eout, b->stream);
+  dev_free(b->alloc, b->d_ctl, b->stream);
+  dev_free(b->alloc, b->d_step, b->stream);
+  dev_free(b->alloc, b->d_clu, b->stream);
+  dev_free(b->alloc, b->d_nbr, b->stream);
+  dev_free(b->alloc, b->d_est, b->stream);
+  dev_free(b->alloc, b->stg_x, b->stream);
+  if (b->h_eout) cudaFreeHost(b->h_eout);
+  if (b->h_ctl) cudaFreeHost(b->h_ctl);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int32_t P, double T, double dt,
+                                      double gamma0, const pimd_params *params, int64_t nsteps,
+                                      int32_t *slot_out) {
+  if (!b || !slot_out) return fail(PIMD_EINVAL, "NULL argument");
+  pimd_params prm;
+  pimd_status st = validate_create(sys, P, T, dt, gamma0, params, &prm);
+  if (st != PIMD_OK) return st;
+  if (sys->potential != PIMD_POT_WATERLIKE)
+    return fail(PIMD_EINVAL, "the batch engine runs water-like systems");
+  if (nsteps < 0) return fail(PIMD_EINVAL, "nsteps must be >= 0");
+  // no batch kernel may be in flight while a new descriptor goes live
+  BK(cudaStreamSynchronize(b->stream));
+  int slot = -1;
+  for (int s = 0; s < b->capacity; ++s)
+    if (!b->reps[s].live) {
+      slot = s;
+      break;
+    }
+  if (slot < 0) return fail(PIMD_EBUDGET, "batch is full (%d replicas)", b->capacity);
+  Replica r;
+  r.N = sys->n_atoms;
+  r.P = P;
+  r.nmol = r.N / 3;
+  r.G = water_lane_groups(P);
+  r.bytes = layout_replica(r, nullptr);
+  r.arena = dev_alloc(b->alloc, r.bytes, b->stream);
+  if (!r.arena) return fail(PIMD_ENOMEM, "replica allocation of %zu bytes failed", r.bytes);
+  layout_replica(r, (char *)r.arena);
+  replica_items(b, slot, r);
+  RepDesc &d = r.desc;
+  HostTables tb;
+  build_tables(P, T, dt, prm, tb);
+  d.live = 1;
+  d.N = r.N;
+  d.P = P;
+  d.nmol = r.nmol;
+  d.G = r.G;
+  d.integrator = prm.integrator;
+  d.thermo = prm.thermostat == PIMD_THERMO_PILE_L;
+  d.seed = prm.seed;
+  d.dt = dt;
+  d.tA = tb.tA;
+  d.c1_0 = tb.c1[0];
+  d.c2_0 = tb.c2[0];
+  d.kT = kBoltzmann * T;
+  d.volume = sys->box[0] * sys->box[1] * sys->box[2];
+  d.wn2 = tb.wn * tb.wn;
+  for (int c = 0; c < 3; ++c) {
+    d.box[c] = sys->box[c];
+    d.invbox[c] = 1.0 / sys->box[c];
+  }
+  d.kb = sys->ff[0];
+  d.r0 = sys->ff[1];
+  d.kth = sys->ff[2];
+  d.th0 = sys->ff[3];
+  d.eps = sys->ff[4];
+  d.sig = sys->ff[5];
+  d.rc = sys->ff[6];
+  d.skin = 1.5;
+  d.rlist = d.rc + d.skin;
+  auto cleanup = [&](pimd_status s2) {
+    cudaStreamSynchronize(b->stream);
+    dev_free(b->alloc, r.arena, b->stream);
+    return s2;
+  };
+  // tables and per-atom constants
+  const int N = r.N;
+  std::vector<double> inv_mm(N), sigv(N), mass_mm(N);
+  for (int i = 0; i < N; ++i) {
+    const double mm = sys->mass[i] * kMvv2e;
+    mass_mm[i] = mm;
+    inv_mm[i] = 1.0 / mm;
+    sigv[i] = std::sqrt(P * kBoltzmann * T / mm);
+  }
+  std::vector<float> Mf(tb.M.begin(), tb.M.end()), Mtf(tb.Mt.begin(), tb.Mt.end());
+  std::vector<float> cAf(tb.cA.begin(), tb.cA.end()), sAf(tb.sA.begin(), tb.sA.end());
+  std::vector<float> wsAf(tb.wsA.begin(), tb.wsA.end()), c1f(tb.c1.begin(), tb.c1.end());
+  std::vector<float> c2f(tb.c2.begin(), tb.c2.end());
+  long long ctl[kCtlWords] = {0, (long long)nsteps, 1, 0, 0, 0, 0, 0};
+  int counts[4] = {(int)r.items_step.size(), (int)r.items_clu.size(), (int)r.items_nbr.size(),
+                   (int)r.items_est.size()};
+  const struct {
+    void *dst;
+    const void *src;
+    size_t bytes;
+  } ups[] = {
+      {d.ctl, ctl, sizeof(ctl)},
+      {(void *)d.inv_mm, inv_mm.data(), N * sizeof(double)},
+      {(void *)d.sigv, sigv.data(), N * sizeof(double)},
+      {(void *)d.mass_mm, mass_mm.data(), N * sizeof(double)},
+      {(void *)d.Mf, Mf.data(), Mf.size() * sizeof(float)},
+      {(void *)d.Mtf, Mtf.data(), Mtf.size() * sizeof(float)},
+      {(void *)d.cAf, cAf.data(), P * sizeof(float)},
+      {(void *)d.sAf, sAf.data(), P * sizeof(float)},
+      {(void *)d.wsAf, wsAf.data(), P * sizeof(float)},
+      {(void *)d.c1f, c1f.data(), P * sizeof(float)},
+      {(void *)d.c2f, c2f.data(), P * sizeof(float)},
+      {(void *)d.Mt64, tb.Mt.data(), (size_t)P * P * sizeof(double)},
+      {(void *)d.lam, tb.lam.data(), P * sizeof(double)},
+      {r.d_items_step, r.items_step.data(), r.items_step.size() * sizeof(int2)},
+      {r.d_items_nbr, r.items_nbr.data(), r.items_nbr.size() * sizeof(int2)},
+      {r.d_items_clu, r.items_clu.data(), r.items_clu.size() * sizeof(int4)},
+      {r.d_counts, counts, sizeof(counts)},
+      {b->d_reps + slot, &d, sizeof(RepDesc)},
+  };
+  for (const auto &u : ups)
+    if (u.bytes && cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+      return cleanup(fail(PIMD_ECUDA, "replica upload failed"));
+  const size_t len = (size_t)N * 3 * P;
+  if ((st = ensure_staging(b, len)) != PIMD_OK) return cleanup(st);
+  cudaError_t e = cudaMemcpyAsync(b->stg_t, sys->pos, len * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = launch_pna_to_nap(b->stg_t, b->stg_x, N, P, b->stream);
+  if (e == cudaSuccess) {
+    if (sys->vel) {
+      e = cudaMemcpyAsync(b->stg_t, sys->vel, len * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+      if (e == cudaSuccess) e = launch_pna_to_nap(b->stg_t, b->stg_v, N, P, b->stream);
+    } else {
+      e = launch_thermal_v(b->stg_v, d.sigv, d.seed, N, P, b->stream);
+    }
+  }
+  if (e == cudaSuccess) e = launch_compress_split(replica_split_args(r), b->stg_x, b->stg_v, b->stream);
+  if (e == cudaSuccess) {
+    NbrArgs na;
+    std::memset(&na, 0, sizeof(na));
+    na.nmol = r.nmol;
+    na.P = P;
+    na.x = b->stg_x;
+    e = launch_centroids(na, d.ccur, b->stream);
+  }
+  // initial neighbour list and forces of this replica only
+  if (e == cudaSuccess) {
+    k_bnbr<<<std::max(1, (int)r.items_nbr.size()), 128, 0, b->stream>>>(b->d_reps, r.d_items_nbr,
+                                                                        r.d_counts + 2, 1);
+    k_bforce<<<4 * std::max(1, (int)std::min<size_t>(r.items_clu.size(), b->grid_clu)), 128, 0, b->stream>>>(
+        b->d_reps, r.d_items_clu, r.d_counts + 1, 1);
+    b->launches += 2;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    // the slot's descriptor was uploaded: mark it dead again
+    RepDesc z;
+    std::memset(&z, 0, sizeof(z));
+    cudaMemcpyAsync(b->d_reps + slot, &z, sizeof(z), cudaMemcpyHostToDevice, b->stream);
+    return cleanup(fail(PIMD_ECUDA, "replica initialisation failed: %s", cudaGetErrorString(e)));
+  }
+  r.live = true;
+  b->reps[slot] = r;
+  b->dirty = true;
+  *slot_out = slot;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_remove(pimd_batch *b, int32_t slot) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->reps[slot].live)
+    return fail(PIMD_ENOTFOUND, "no replica in slot %d", slot);
+  BK(cudaStreamSynchronize(b->stream));
+  Replica &r = b->reps[slot];
+  RepDesc z;
+  std::memset(&z, 0, sizeof(z));
+  BK(cudaMemcpyAsync(b->d_reps + slot, &z, sizeof(z), cudaMemcpyHostToDevice, b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  dev_free(b->alloc, r.arena, b->stream);
+  r = Replica();
+  b->dirty = true;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_run(pimd_batch *b, int64_t nsteps) {
+  if (!b || nsteps < 0) return fail(PIMD_EINVAL, "invalid argument");
+  pimd_status st;
+  if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
+  if (nsteps == 0) return PIMD_OK;
+  int64_t left = nsteps;
+  if (left >= b->graph_steps) {
+    if (!b->graph && (st = capture(b)) != PIMD_OK) return st;
+    while (left >= b->graph_steps) {
+      BK(cudaGraphLaunch(b->graph, b->stream));
+      b->launches += 4 * b->graph_steps;
+      left -= b->graph_steps;
+    }
+  }
+  for (; left > 0; --left) {
+    BK(launch_one_step(b, nullptr, nullptr));
+    b->launches += 4;
+  }
+  const int cg = (b->capacity + 127) / 128;
+  k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1);
+  k_bclose<<<b->grid_step, 256, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+  k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2);
+  b->launches += 3;
+  BK(cudaGetLastError());
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_sync(pimd_batch *b) {
+  if (!b) return fail(PIMD_EINVAL, "batch is NULL");
+  BK(cudaStreamSynchronize(b->stream));
+  return PIMD_OK;
+}
+
+// Per-slot step counter and steps left (-1 for empty slots); arrays of
+// max_replicas entries, either may be NULL.  Synchronises.
+extern "C" pimd_status pimd_batch_status(pimd_batch *b, int64_t *step, int64_t *steps_left) {
+  if (!b) return fail(PIMD_EINVAL, "batch is NULL");
+  pimd_status st;
+  if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
+  k_bgather_ctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, b->d_ctl);
+  BK(cudaGetLastError());
+  BK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(long long) * kCtlWords * b->capacity, cudaMemcpyDeviceToHost,
+                     b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  for (int s = 0; s < b->capacity; ++s) {
+    const long long *c = b->h_ctl + (size_t)s * kCtlWords;
+    if (step) step[s] = b->reps[s].live ? c[kCtlStep] : -1;
+    if (steps_left) steps_left[s] = b->reps[s].live ? c[kCtlLeft] : -1;
+    if (b->reps[s].live && (c[kCtlWords - 1] & kErrNbrOverflow))
+      return fail(PIMD_EOVERFLOW, "replica %d: neighbour list overflow", s);
+  }
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_estimators(pimd_batch *b, pimd_estimates *out) {
+  if (!b || !out) return fail(PIMD_EINVAL, "NULL argument");
+  pimd_status st;
+  if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
+  if (b->h_counts[3] > 0) {
+    k_best<<<std::min(b->grid_est, b->h_counts[3]), 128, 0, b->stream>>>(b->d_reps, b->d_est, b->d_counts + 3);
+    k_best_final<<<b->capacity, 128, 0, b->stream>>>(b->d_reps, b->capacity, b->d_eout);
+    b->launches += 2;
+    BK(cudaGetLastError());
+  }
+  if ((st = pimd_batch_status(b, nullptr, nullptr)) != PIMD_OK) return st;
+  BK(cudaMemcpyAsync(b->h_eout, b->d_eout, sizeof(double) * kOutStride * b->capacity, cudaMemcpyDeviceToHost,
+                     b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  for (int s = 0; s < b->capacity; ++s) {
+    pimd_estimates &e = out[s];
+    std::memset(&e, 0, sizeof(e));
+    if (!b->reps[s].live) {
+      e.step = -1;
+      continue;
+    }
+    std::memcpy(e.K_mode, b->h_eout + (size_t)s * kOutStride, sizeof(double) * kOutStride);
+    e.step = b->h_ctl[(size_t)s * kCtlWords + kCtlStep];
+    e.P = b->reps[s].P;
+    e.N = b->reps[s].N;
+    if (!std::isfinite(e.H)) return fail(PIMD_ENONFINITE, "replica %d: non-finite estimator sum", s);
+  }
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double *x, double *v_nm,
+                                            int64_t *step) {
+  if (!b || slot < 0 || slot >= b->capacity || !b->reps[slot].live)
+    return fail(PIMD_ENOTFOUND, "no replica in slot %d", slot);
+  const Replica &r = b->reps[slot];
+  const size_t len = (size_t)r.N * 3 * r.P;
+  pimd_status st = ensure_staging(b, len);
+  if (st != PIMD_OK) return st;
+  BK(launch_expand_split(replica_split_args(r), r.desc.F, b->stg_x, b->stg_v, nullptr, b->stream));
+  if (x) {
+    BK(launch_nap_to_pna(b->stg_x, b->stg_t, r.N, r.P, b->stream));
+    BK(cudaMemcpyAsync(x, b->stg_t, len * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  if (v_nm) {
+    BK(launch_nap_to_pna(b->stg_v, b->stg_t, r.N, r.P, b->stream));
+    BK(cudaMemcpyAsync(v_nm, b->stg_t, len * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  }
+  long long c[kCtlWords];
+  BK(cudaMemcpyAsync(c, r.desc.ctl, sizeof(c), cudaMemcpyDeviceToHost, b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  if (step) *step = c[kCtlStep];
+  return PIMD_OK;
+}
+
+extern "C" int64_t pimd_batch_kernel_launches(const pimd_batch *b) { return b ? b->launches : -1; }
+
+// Autotuner of the step-kernel tile: for each bead count present, try tiles
+// A = Amax, Amax/2, ..., 1 (A atoms x 3 components x P modes per block) while
+// the replicas keep stepping, time the step kernel with CUDA events, keep the
+// fastest.  A replica's arithmetic does not depend on A, so tuning changes no
+// trajectory; the tuning steps count toward the replicas' step budgets.
+extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t *tiles_out) {
+  if (!b) return fail(PIMD_EINVAL, "batch is NULL");
+  if (steps_per_trial < 1) steps_per_trial = 2;
+  std::vector<int> classes;
+  for (auto &r : b->reps)
+    if (r.live && std::find(classes.begin(), classes.end(), r.P) == classes.end()) classes.push_back(r.P);
+  std::sort(classes.begin(), classes.end());
+  cudaEvent_t e0, e1;
+  BK(cudaEventCreate(&e0));
+  BK(cudaEventCreate(&e1));
+  auto time_step = [&](float *ms_out) -> pimd_status {
+    pimd_status st;
+    if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
+    float total = 0.f;
+    for (int s = 0; s < steps_per_trial; ++s) {
+      BK(launch_one_step(b, e0, e1));
+      BK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      BK(cudaEventElapsedTime(&ms, e0, e1));
+      total += ms;
+    }
+    b->launches += 4 * steps_per_trial;
+    *ms_out = total;
+    return PIMD_OK;
+  };
+  pimd_status st = PIMD_OK;
+  for (int P : classes) {
+    const int amax = default_tile(P);
+    int best = amax;
+    float best_ms = 1e30f;
+    for (int A = amax; A >= 1; A = (A == 1) ? 0 : std::max(1, A / 2)) {
+      b->tileA[P] = A;
+      for (int s = 0; s < b->capacity; ++s)
+        if (b->reps[s].live && b->reps[s].P == P) replica_items(b, s, b->reps[s]);
+      b->dirty = true;
+      float ms = 0.f;
+      if ((st = time_step(&ms)) != PIMD_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = A;
+      }
+    }
+    if (st != PIMD_OK) break;
+    b->tileA[P] = best;
+    for (int s = 0; s < b->capacity; ++s)
+      if (b->reps[s].live && b->reps[s].P == P) replica_items(b, s, b->reps[s]);
+    b->dirty = true;
+  }
+  // finish the tuning steps: closing kick, back at integer time
+  if (st == PIMD_OK) st = pimd_batch_run(b, 0);
+  if (st == PIMD_OK) {
+    const int cg = (b->capacity + 127) / 128;
+    k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1);
+    k_bclose<<<b->grid_step, 256, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+    k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2);
+    b->launches += 3;
+    if (cudaGetLastError() != cudaSuccess) st = fail(PIMD_ECUDA, "autotune close failed");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (tiles_out)
+    for (int P = 0; P <= PIMD_MAX_BEADS; ++P) tiles_out[P] = b->tileA[P];
+  return st;
+}
+
+// ===========================================================================
+// serving: FIFO admission by HBM budget, continuous batching, worker thread
+// ===========================================================================
+namespace pimd {
+namespace serving {
+
+enum JobState { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
+
+struct Job {
+  uint64_t id = 0;
+  int state = kQueued;
+  pimd_status status = PIMD_OK;
+  // copies of the submitted arrays
+  int32_t n_atoms = 0, potential = 0, P = 0;
+  std::vector<double> mass, pos, vel;
+  double box[3] = {0, 0, 0}, ff[8] = {0};
+  double T = 0, dt = 0, gamma0 = 0;
+  pimd_params params{};
+  int64_t nsteps = 0;
+  size_t bytes = 0;
+  int slot = -1;
+  bool cancel = false;
+  int64_t steps_seen = 0;
+  pimd_estimates result{};
+  double t_submit = -1, t_start = -1, t_end = -1;
+};
+
+}  // namespace serving
+}  // namespace pimd
+
+struct pimd_server {
+  pimd_batch *batch = nullptr;
+  size_t budget = 0, used = 0;
+  int64_t chunk = 100;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<uint64_t> queue;
+  std::map<uint64_t, pimd::serving::Job> jobs;
+  uint64_t next_id = 1;
+  std::thread worker;
+  bool stop = false;
+  std::chrono::steady_clock::time_point t0;
+  pimd_server_stats stats{};
+  std::vector<int64_t> st_step, st_left;
+  std::vector<pimd_estimates> est;
+};
+
+namespace {
+
+double now_s(pimd_server *s) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+void server_loop(pimd_server *s) {
+  using namespace pimd::serving;
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (!s->stop) {
+    // admission: FIFO while the head fits the budget and a slot is free
+    while (!s->queue.empty()) {
+      const uint64_t id = s->queue.front();
+      Job &j = s->jobs[id];
+      if (j.cancel) {
+        s->queue.pop_front();
+        j.state = kCancelled;
+        continue;
+      }
+      if (s->used + j.bytes > s->budget) break;
+      pimd_system sys;
+      sys.n_atoms = j.n_atoms;
+      sys.potential = j.potential;
+      sys.mass = j.mass.data();
+      sys.pos = j.pos.data();
+      sys.vel = j.vel.empty() ? nullptr : j.vel.data();
+      std::memcpy(sys.box, j.box, sizeof(sys.box));
+      std::memcpy(sys.ff, j.ff, sizeof(sys.ff));
+      int32_t slot = -1;
+      const pimd_status st = pimd_batch_add(s->batch, &sys, j.P, j.T, j.dt, j.gamma0, &j.params, j.nsteps, &slot);
+      if (st == PIMD_EBUDGET) break;   // no free slot: wait for a job to leave
+      s->queue.pop_front();
+      if (st != PIMD_OK) {
+        j.state = kFailed;
+        j.status = st;
+        j.t_end = now_s(s);
+        s->stats.failed++;
+        continue;
+      }
+      j.state = kRunning;
+      j.slot = slot;
+      j.t_start = now_s(s);
+      s->used += j.bytes;
+    }
+    int running = 0;
+    for (auto &kv : s->jobs)
+      if (kv.second.state == kRunning) ++running;
+    s->stats.running = running;
+    s->stats.queued = (int64_t)s->queue.size();
+    s->stats.bytes_in_use = s->used;
+    if (!running) {
+      s->cv.wait_for(lk, std::chrono::milliseconds(20));
+      continue;
+    }
+    // one chunk outside the lock: submissions and polls proceed meanwhile
+    lk.unlock();
+    const double t_run = now_s(s);
+    pimd_status st = pimd_batch_run(s->batch, s->chunk);
+    if (st == PIMD_OK) st = pimd_batch_status(s->batch, s->st_step.data(), s->st_left.data());
+    bool any_done = false;
+    if (st == PIMD_OK)
+      for (int k = 0; k < (int)s->st_left.size(); ++k) any_done |= (s->st_left[k] == 0);
+    if (st == PIMD_OK && any_done) st = pimd_batch_estimators(s->batch, s->est.data());
+    const double t_after = now_s(s);
+    lk.lock();
+    s->stats.chunks++;
+    s->stats.gpu_busy_s += t_after - t_run;
+    for (auto &kv : s->jobs) {
+      Job &j = kv.second;
+      if (j.state != kRunning) continue;
+      if (st == PIMD_OK) {
+        const int64_t done = s->st_step[j.slot];
+        s->stats.bead_atom_steps += (double)j.n_atoms * j.P * (double)(done - j.steps_seen);
+        j.steps_seen = done;
+      }
+      const bool finished = st == PIMD_OK && s->st_left[j.slot] == 0;
+      if (st != PIMD_OK || finished || j.cancel) {
+        if (st != PIMD_OK) {
+          j.state = kFailed;
+          j.status = st;
+          s->stats.failed++;
+        } else if (j.cancel) {
+          j.state = kCancelled;
+        } else {
+          j.state = kDone;
+          j.result = s->est[j.slot];
+          s->stats.completed++;
+        }
+        j.t_end = t_after;
+        pimd_batch_remove(s->batch, j.slot);
+        s->used -= j.bytes;
+        j.slot = -1;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" pimd_status pimd_server_create(size_t hbm_budget_bytes, int32_t max_replicas, int64_t chunk_steps,
+                                          void *stream, pimd_server **out) {
+  if (!out) return fail(PIMD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (hbm_budget_bytes == 0 || chunk_steps < 1) return fail(PIMD_EINVAL, "budget and chunk must be > 0");
+  pimd_server *s = new pimd_server();
+  pimd_status st = pimd_batch_create(max_replicas, stream, &s->batch);
+  if (st != PIMD_OK) {
+    delete s;
+    return st;
+  }
+  s->budget = hbm_budget_bytes;
+  s->chunk = chunk_steps;
+  s->t0 = std::chrono::steady_clock::now();
+  s->st_step.assign(max_replicas, -1);
+  s->st_left.assign(max_replicas, -1);
+  s->est.resize(max_replicas);
+  s->worker = std::thread(server_loop, s);
+  *out = s;
+  return PIMD_OK;
+}
+
+extern "C" void pimd_server_destroy(pimd_server *s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  pimd_batch_destroy(s->batch);
+  delete s;
+}
+
+extern "C" pimd_status pimd_batch_submit(pimd_server *s, const pimd_system *sys, int32_t P, double T, double dt,
+                                         double gamma0, const pimd_params *params, int64_t nsteps,
+                                         uint64_t *job) {
+  using namespace pimd::serving;
+  if (!s || !job) return fail(PIMD_EINVAL, "NULL argument");
+  pimd_params prm;
+  pimd_status st = validate_create(sys, P, T, dt, gamma0, params, &prm);
+  if (st != PIMD_OK) return st;
+  if (sys->potential != PIMD_POT_WATERLIKE) return fail(PIMD_EINVAL, "the server runs water-like systems");
+  if (nsteps < 0) return fail(PIMD_EINVAL, "nsteps must be >= 0");
+  const size_t bytes = pimd_batch_replica_bytes(sys->n_atoms, P);
+  if (bytes > s->budget) return fail(PIMD_EBUDGET, "job needs %zu bytes, budget is %zu", bytes, s->budget);
+  Job j;
+  j.n_atoms = sys->n_atoms;
+  j.potential = sys->potential;
+  j.P = P;
+  const size_t len = (size_t)P * sys->n_atoms * 3;
+  j.mass.assign(sys->mass, sys->mass + sys->n_atoms);
+  j.pos.assign(sys->pos, sys->pos + len);
+  if (sys->vel) j.vel.assign(sys->vel, sys->vel + len);
+  std::memcpy(j.box, sys->box, sizeof(j.box));
+  std::memcpy(j.ff, sys->ff, sizeof(j.ff));
+  j.T = T;
+  j.dt = dt;
+  j.gamma0 = 0.0;
+  j.params = prm;            // tau already reflects gamma0
+  j.nsteps = nsteps;
+  j.bytes = bytes;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    j.id = s->next_id++;
+    j.t_submit = now_s(s);
+    s->jobs[j.id] = std::move(j);
+    s->queue.push_back(s->next_id - 1);
+    s->stats.submitted++;
+    *job = s->next_id - 1;
+  }
+  s->cv.notify_all();
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_poll(pimd_server *s, uint64_t job, pimd_estimates *out) {
+  using namespace pimd::serving;
+  if (!s) return fail(PIMD_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job);
+  if (it == s->jobs.end() || it->second.state == kCancelled) return fail(PIMD_ENOTFOUND, "unknown job %llu", (unsigned long long)job);
+  const Job &j = it->second;
+  if (j.state == kQueued || j.state == kRunning) return PIMD_EPENDING;
+  if (j.state == kFailed) return fail(j.status, "job %llu failed", (unsigned long long)job);
+  if (out) *out = j.result;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_batch_cancel(pimd_server *s, uint64_t job) {
+  if (!s) return fail(PIMD_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job);
+  if (it == s->jobs.end()) return fail(PIMD_ENOTFOUND, "unknown job %llu", (unsigned long long)job);
+  it->second.cancel = true;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_server_job_times(pimd_server *s, uint64_t job, double *submitted, double *started,
+                                             double *finished) {
+  if (!s) return fail(PIMD_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job);
+  if (it == s->jobs.end()) return fail(PIMD_ENOTFOUND, "unknown job %llu", (unsigned long long)job);
+  if (submitted) *submitted = it->second.t_submit;
+  if (started) *started = it->second.t_start;
+  if (finished) *finished = it->second.t_end;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_server_stats_get(pimd_server *s, pimd_server_stats *out) {
+  if (!s || !out) return fail(PIMD_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  return PIMD_OK;
+}

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "pimd.h"
+#include "runtime.h"
 
 namespace pimd {
 size_t step_smem_bytes(int A, int P);
@@ -52,13 +53,15 @@ using namespace pimd;
 // ---------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
 
-static pimd_status fail(pimd_status s, const char *fmt, ...) {
+namespace pimd {
+pimd_status fail(pimd_status s, const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
   return s;
 }
+}  // namespace pimd
 
 #define CK(call)                                                                     \
   do {                                                                               \
@@ -93,13 +96,15 @@ extern "C" const char *pimd_status_string(pimd_status s) {
 // ---------------------------------------------------------------------------
 // device allocator (optional external callbacks, e.g. a caching allocator)
 // ---------------------------------------------------------------------------
-struct Allocator {
-  pimd_alloc_fn alloc = nullptr;
-  pimd_free_fn release = nullptr;
-  void *ctx = nullptr;
-};
 static std::mutex g_alloc_mu;
-static Allocator g_alloc;
+static DevAllocator g_alloc;
+
+namespace pimd {
+DevAllocator current_allocator() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc;
+}
+}  // namespace pimd
 
 extern "C" void pimd_set_allocator(pimd_alloc_fn alloc, pimd_free_fn release, void *ctx) {
   std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -133,7 +138,7 @@ struct pimd_handle {
   double ff[8] = {0};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  Allocator alloc;
+  DevAllocator alloc;
   void *arena = nullptr;
   size_t arena_bytes = 0;
   // device state, layout [N][3][P]
@@ -222,7 +227,8 @@ static pimd_status enqueue(pimd_handle *h, int kind, int nk, Fn &&fn) {
   return PIMD_OK;
 }
 
-static void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s) {
+namespace pimd {
+void *dev_alloc(const DevAllocator &a, size_t bytes, cudaStream_t s) {
   if (a.alloc) return a.alloc(bytes, (void *)s, a.ctx);
   void *p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -232,13 +238,14 @@ static void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t s) {
   return p;
 }
 
-static void dev_free(const Allocator &a, void *p, cudaStream_t s) {
+void dev_free(const DevAllocator &a, void *p, cudaStream_t s) {
   if (!p) return;
   if (a.release)
     a.release(p, (void *)s, a.ctx);
   else
     cudaFree(p);
 }
+}  // namespace pimd
 
 // Eq. (A1), with cos rows 1 <= i <= floor((P-1)/2), the alternating row at
 // i = P/2 for even P, and sin rows i > P/2.
@@ -653,11 +660,9 @@ static pimd_status upload_state(pimd_handle *h, const double *x, const double *v
   return PIMD_OK;
 }
 
-extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, double dt,
-                                   double gamma0, const pimd_params *params, void *stream,
-                                   pimd_handle **out) {
-  if (!out) return fail(PIMD_EINVAL, "out is NULL");
-  *out = nullptr;
+namespace pimd {
+pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double dt, double gamma0,
+                            const pimd_params *params, pimd_params *out) {
   if (!sys) return fail(PIMD_EINVAL, "sys is NULL");
   pimd_params prm;
   if (params)
@@ -704,6 +709,56 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
       return fail(PIMD_EINVAL, "invalid water-like force-field parameters");
   }
 
+  *out = prm;
+  return PIMD_OK;
+}
+
+void build_tables(int P, double T, double dt, const pimd_params &prm, HostTables &t) {
+  build_nm_matrix(P, t.M);
+  t.Mt.assign((size_t)P * P, 0.0);
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) t.Mt[(size_t)j * P + i] = t.M[(size_t)i * P + j];
+  const double hbar = prm.sp * kPlanck / (2.0 * kPi);
+  t.wn = P * kBoltzmann * T / hbar;                      // Eq. (2)
+  t.tA = prm.integrator == PIMD_BAOAB ? 0.5 * dt : dt;
+  t.tO = prm.integrator == PIMD_BAOAB ? dt : 0.5 * dt;
+  t.cA.resize(P);
+  t.sA.resize(P);
+  t.wsA.resize(P);
+  t.c1.resize(P);
+  t.c2.resize(P);
+  t.lam.resize(P);
+  for (int k = 0; k < P; ++k) {
+    const double s = std::sin(kPi * k / P);
+    t.lam[k] = 4.0 * s * s;                               // Eq. (A2)
+    const double wk = 2.0 * t.wn * std::fabs(s);          // w_k = sqrt(lam_k) w_n
+    if (k == 0 || wk == 0.0) {
+      t.cA[k] = 1.0;
+      t.sA[k] = t.tA;
+      t.wsA[k] = 0.0;
+    } else {
+      t.cA[k] = std::cos(wk * t.tA);
+      t.sA[k] = std::sin(wk * t.tA) / wk;
+      t.wsA[k] = wk * std::sin(wk * t.tA);
+    }
+    const double tauk = (k == 0) ? prm.tau : prm.scale / (2.0 * wk);
+    t.c1[k] = std::exp(-t.tO / tauk);
+    t.c2[k] = std::sqrt(1.0 - t.c1[k] * t.c1[k]);
+  }
+}
+}  // namespace pimd
+
+extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, double dt,
+                                   double gamma0, const pimd_params *params, void *stream,
+                                   pimd_handle **out) {
+  if (!out) return fail(PIMD_EINVAL, "out is NULL");
+  *out = nullptr;
+  pimd_params prm;
+  {
+    pimd_status vs = validate_create(sys, P, T, dt, gamma0, params, &prm);
+    if (vs != PIMD_OK) return vs;
+  }
+  const int N = sys->n_atoms;
   pimd_handle *h = new pimd_handle();
   h->N = N;
   h->P = P;
@@ -721,10 +776,7 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   for (int d = 0; d < 3; ++d) h->box[d] = sys->box[d];
   for (int q = 0; q < 8; ++q) h->ff[q] = sys->ff[q];
   h->rlist = h->ff[6] + h->skin;
-  {
-    std::lock_guard<std::mutex> lk(g_alloc_mu);
-    h->alloc = g_alloc;
-  }
+  h->alloc = current_allocator();
   if (stream) {
     h->stream = (cudaStream_t)stream;
   } else {
@@ -758,31 +810,12 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   }
 
   // ---- host tables (App. B, App. D), FP64 ----
-  std::vector<double> M, Mt((size_t)P * P), cA(P), sA(P), wsA(P), c1v(P), c2v(P), lam(P);
-  build_nm_matrix(P, M);
-  for (int i = 0; i < P; ++i)
-    for (int j = 0; j < P; ++j) Mt[(size_t)j * P + i] = M[(size_t)i * P + j];
-  const double hbar = prm.sp * kPlanck / (2.0 * kPi);
-  h->wn = P * kBoltzmann * T / hbar;                     // Eq. (2)
-  const double tA = prm.integrator == PIMD_BAOAB ? 0.5 * dt : dt;
-  const double tO = prm.integrator == PIMD_BAOAB ? dt : 0.5 * dt;
-  for (int k = 0; k < P; ++k) {
-    const double s = std::sin(kPi * k / P);
-    lam[k] = 4.0 * s * s;                                 // Eq. (A2)
-    const double wk = 2.0 * h->wn * std::fabs(s);         // w_k = sqrt(lam_k) w_n
-    if (k == 0 || wk == 0.0) {
-      cA[k] = 1.0;
-      sA[k] = tA;
-      wsA[k] = 0.0;
-    } else {
-      cA[k] = std::cos(wk * tA);
-      sA[k] = std::sin(wk * tA) / wk;
-      wsA[k] = wk * std::sin(wk * tA);
-    }
-    const double tauk = (k == 0) ? prm.tau : prm.scale / (2.0 * wk);
-    c1v[k] = std::exp(-tO / tauk);
-    c2v[k] = std::sqrt(1.0 - c1v[k] * c1v[k]);
-  }
+  HostTables tb;
+  build_tables(P, T, dt, prm, tb);
+  h->wn = tb.wn;
+  const std::vector<double> &M = tb.M, &Mt = tb.Mt, &cA = tb.cA, &sA = tb.sA, &wsA = tb.wsA;
+  const std::vector<double> &c1v = tb.c1, &c2v = tb.c2, &lam = tb.lam;
+  const double tA = tb.tA;
   std::vector<double> inv_mm(N), sigv(N), mass_mm(N), ksp(N);
   for (int i = 0; i < N; ++i) {
     const double mm = sys->mass[i] * kMvv2e;

@@ -1,0 +1,43 @@
+// runtime.h -- host-side pieces shared by the single-system handle (capi.cu)
+// and the multi-replica batch / server (batch.cu): argument validation, the
+// precomputed mode tables, and error reporting.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "pimd.h"
+
+namespace pimd {
+
+// Per-mode tables of App. B / App. D for one (P, T, dt, params), FP64.
+struct HostTables {
+  std::vector<double> M, Mt;            // [P][P] Eq. (A1) and its transpose
+  std::vector<double> cA, sA, wsA;      // exact A step of length tA
+  std::vector<double> c1, c2;           // O step of length tO
+  std::vector<double> lam;              // Eq. (A2)
+  double wn = 0.0, tA = 0.0, tO = 0.0;  // Eq. (2), A and O durations
+};
+
+void build_tables(int P, double T, double dt, const pimd_params &prm, HostTables &t);
+
+// Checks of pimd_create (shared by pimd_create and the batch/server);
+// fills *prm with the effective parameters (defaults, gamma0 -> tau).
+pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double dt, double gamma0,
+                            const pimd_params *params, pimd_params *prm);
+
+// Device memory through the optional pimd_set_allocator hooks (else cudaMalloc).
+struct DevAllocator {
+  pimd_alloc_fn alloc = nullptr;
+  pimd_free_fn release = nullptr;
+  void *ctx = nullptr;
+};
+DevAllocator current_allocator();
+void *dev_alloc(const DevAllocator &a, size_t bytes, cudaStream_t s);
+void dev_free(const DevAllocator &a, void *p, cudaStream_t s);
+
+pimd_status fail(pimd_status s, const char *fmt, ...);
+void set_last_error(const char *msg);
+
+}  // namespace pimd

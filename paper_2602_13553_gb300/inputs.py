@@ -37,6 +37,15 @@ AMU_G = 1.66053906660e-24          # g per amu
 WATER_FF = (45.0, 1.0, 3.3, math.radians(104.5), 6.7e-3, 3.166, 6.0)
 
 
+def water_ff_for_box(L: float):
+    """The water-like force field for a cubic box of edge L: the 6 A O-O cutoff,
+    capped at 0.48 L in boxes too small for minimum-image interactions at 6 A
+    (the 32-molecule boxes of the mixes are 9.86 A)."""
+    ff = list(WATER_FF)
+    ff[6] = min(ff[6], 0.48 * L)
+    return tuple(ff)
+
+
 def rng(seed: int) -> np.random.Generator:
     return np.random.default_rng(np.random.PCG64(int(seed)))
 

@@ -1,0 +1,117 @@
+"""The multi-replica batch engine (split precision): agreement with the FP64
+oracle, bitwise independence of a replica from the rest of the batch,
+per-replica step budgets, membership changes between runs, autotuning."""
+import numpy as np
+import pytest
+
+from paper_2602_13553_gb300 import inputs
+from tests._gpu import pimd  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def rep(nmol, P, seed, T=300.0, deut=False):
+    L = inputs.box_length(nmol)
+    x0, mass = inputs.water_box(nmol, L, P, seed, jitter=0.02, deuterium=deut)
+    return dict(x0=x0, mass=mass, T=T, dt=5e-4, ff=inputs.water_ff_for_box(L), box=(L, L, L), seed=seed)
+
+
+def add(b, r, nsteps, **kw):
+    return b.add(r["x0"], r["mass"], T=r["T"], dt=r["dt"], nsteps=nsteps, ff=r["ff"], box=r["box"],
+                 seed=r["seed"], **kw)
+
+
+MIX = [rep(40, 8, 11, 200.0), rep(70, 16, 12, 350.0, True), rep(100, 32, 13), rep(32, 64, 14, 120.0, True),
+       rep(150, 8, 15, 390.0), rep(64, 32, 16)]
+
+
+def test_batch_agrees_with_oracle(orc, pimd):
+    b = pimd.Batch(8)
+    slots = [add(b, r, 40) for r in MIX[:3]]
+    b.run(40)
+    for s, r in zip(slots, MIX[:3]):
+        c = orc.Sim(r["x0"], r["mass"], T=r["T"], dt=r["dt"], potential=1, ff=r["ff"], box=r["box"],
+                    seed=r["seed"])
+        c.run(40)
+        x, v, st = b.get_state(s)
+        assert st == 40
+        assert np.max(np.abs(x - c.x)) < 1e-4
+        e = b.estimators()[s]
+        ec = c.estimators()
+        for k in ("K_CV", "T_ring"):
+            assert abs(e[k] - ec[k]) < 1e-3 * abs(ec[k]), k
+    b.close()
+
+
+def test_replica_alone_and_in_mix_are_bitwise_equal(pimd):
+    alone = pimd.Batch(2)
+    s0 = add(alone, MIX[2], 60)
+    alone.run(60)
+    xa, va, _ = alone.get_state(s0)
+    ea = alone.estimators()[s0]
+    mixed = pimd.Batch(8)
+    slots = [add(mixed, r, 60) for r in MIX]
+    mixed.run(60)
+    xm, vm, _ = mixed.get_state(slots[2])
+    em = mixed.estimators()[slots[2]]
+    assert np.array_equal(xa, xm) and np.array_equal(va, vm)
+    for k in ("H", "K_CV", "P_CV", "K_PR"):
+        assert abs(ea[k] - em[k]) <= 1e-12 * abs(ea[k]), k
+
+
+def test_step_budgets_per_replica(pimd):
+    budgets = [13, 40, 77]
+    b = pimd.Batch(4)
+    slots = [add(b, r, n) for r, n in zip(MIX[:3], budgets)]
+    b.run(50)
+    b.run(50)
+    st, left = b.status()
+    for s, n in zip(slots, budgets):
+        assert st[s] == n and left[s] == 0
+    for s, r, n in zip(slots, MIX[:3], budgets):
+        # same call boundaries: every run() ends with a closing half-kick
+        solo = pimd.Batch(1)
+        t = add(solo, r, n)
+        solo.run(50)
+        solo.run(50)
+        xs, vs, _ = solo.get_state(t)
+        xb, vb, _ = b.get_state(s)
+        assert np.array_equal(xs, xb) and np.array_equal(vs, vb)
+
+
+def test_membership_changes_between_runs(pimd):
+    b = pimd.Batch(4)
+    a = add(b, MIX[0], 1000)
+    b.run(20)
+    c = add(b, MIX[1], 40)
+    b.run(20)
+    b.remove(a)
+    b.run(20)
+    x, v, st = b.get_state(c)
+    assert st == 40
+    solo = pimd.Batch(1)
+    t = add(solo, MIX[1], 40)
+    solo.run(20)
+    solo.run(20)
+    xs, vs, _ = solo.get_state(t)
+    assert np.array_equal(xs, x) and np.array_equal(vs, v)
+
+
+def test_autotune_changes_no_trajectory(pimd):
+    reps = MIX[:3]
+    tuned = pimd.Batch(4)
+    slots = [add(tuned, r, 200) for r in reps]
+    tiles = tuned.autotune(1)
+    st, _ = tuned.status()
+    used = int(st[slots[0]])
+    assert set(tiles) == {8, 16, 32} and all(t >= 1 for t in tiles.values())
+    tuned.run(30)
+    plain = pimd.Batch(4)
+    pslots = [add(plain, r, 200) for r in reps]
+    plain.run(used)
+    plain.run(30)
+    for s, p in zip(slots, pslots):
+        x1, v1, s1 = tuned.get_state(s)
+        x2, v2, s2 = plain.get_state(p)
+        assert s1 == s2 == used + 30
+        assert np.array_equal(x1, x2) and np.array_equal(v1, v2)

@@ -1,0 +1,121 @@
+"""The continuous-batching server: results identical alone and in a mix,
+FIFO admission under the HBM budget, oversized jobs, cancellation, and
+injected allocation refusals (host-side fault injection)."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2602_13553_gb300 import inputs
+from tests._gpu import pimd  # noqa: F401
+from tests.test_gpu_batch import MIX
+
+pytestmark = pytest.mark.gpu
+
+
+def submit(srv, r, nsteps):
+    return srv.submit(r["x0"], r["mass"], T=r["T"], dt=r["dt"], nsteps=nsteps, ff=r["ff"], box=r["box"],
+                      seed=r["seed"])
+
+
+def wait(srv, jobs, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(jobs):
+        for j in jobs:
+            if j not in out:
+                res = srv.poll(j)
+                if res is not None:
+                    out[j] = res
+        assert time.time() - t0 < timeout, "jobs did not finish"
+        time.sleep(0.005)
+    return out
+
+
+def test_result_same_alone_and_in_mix(pimd):
+    srv = pimd.Server(8 << 30, max_replicas=16, chunk_steps=25)
+    ja = submit(srv, MIX[2], 130)
+    alone = wait(srv, [ja])[ja]
+    srv.close()
+    srv = pimd.Server(8 << 30, max_replicas=16, chunk_steps=25)
+    early = [submit(srv, MIX[0], 300), submit(srv, MIX[4], 90)]
+    time.sleep(0.05)                      # the mix is already running when the job arrives
+    jb = submit(srv, MIX[2], 130)
+    late = [submit(srv, r, 60 + 10 * i) for i, r in enumerate(MIX[3:])]
+    res = wait(srv, early + [jb] + late)
+    mixed = res[jb]
+    assert mixed["step"] == alone["step"] == 130
+    for k in ("H", "K_CV", "P_CV", "K_PR", "T_ring"):
+        assert abs(mixed[k] - alone[k]) <= 1e-12 * abs(alone[k]), k
+    st = srv.stats()
+    assert st["completed"] == 2 + 1 + len(late) and st["failed"] == 0
+    srv.close()
+
+
+def test_fifo_admission_under_budget(pimd):
+    r = MIX[1]
+    need = pimd.replica_bytes(r["x0"].shape[1], r["x0"].shape[0])
+    srv = pimd.Server(int(need * 1.5), max_replicas=8, chunk_steps=20)
+    jobs = [submit(srv, r, 40) for _ in range(3)]
+    wait(srv, jobs)
+    times = [srv.times(j) for j in jobs]
+    for (s0, a0, f0), (s1, a1, f1) in zip(times, times[1:]):
+        assert a1 >= f0 - 1e-9          # one job at a time fits the budget
+    srv.close()
+
+
+def test_oversized_job_and_cancel(pimd):
+    r = MIX[0]
+    need = pimd.replica_bytes(r["x0"].shape[1], r["x0"].shape[0])
+    srv = pimd.Server(need // 2, max_replicas=4, chunk_steps=20)
+    with pytest.raises(pimd.PimdError) as ei:
+        submit(srv, r, 10)
+    assert ei.value.status == 8        # PIMD_EBUDGET
+    srv.close()
+    srv = pimd.Server(8 << 30, max_replicas=4, chunk_steps=20)
+    j = submit(srv, MIX[1], 10 ** 7)
+    time.sleep(0.1)
+    srv.cancel(j)
+    time.sleep(0.2)
+    with pytest.raises(pimd.PimdError) as ei:
+        srv.poll(j)
+    assert ei.value.status == 7        # PIMD_ENOTFOUND once cancelled
+    assert srv.stats()["bytes_in_use"] == 0
+    srv.close()
+
+
+def test_allocation_refusal_fails_only_that_job(pimd):
+    """Fault injection on the host: an allocator hook that refuses large
+    requests makes that job fail with ENOMEM; the server keeps serving."""
+    import ctypes
+    import torch
+    big = MIX[4]
+    limit = pimd.replica_bytes(big["x0"].shape[1], big["x0"].shape[0]) - 1
+
+    def alloc(nbytes, stream, ctx):
+        if nbytes > limit:
+            return None
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+
+    def free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = pimd.ALLOC_FN(alloc), pimd.FREE_FN(free)
+    pimd.lib().pimd_set_allocator(fa, ff, None)
+    try:
+        srv = pimd.Server(8 << 30, max_replicas=4, chunk_steps=20)
+        jbad = submit(srv, big, 40)
+        jok = submit(srv, MIX[0], 40)
+        t0 = time.time()
+        while True:
+            try:
+                r = srv.poll(jbad)
+            except pimd.PimdError as e:
+                assert e.status == 2   # PIMD_ENOMEM
+                break
+            assert r is None and time.time() - t0 < 60
+            time.sleep(0.01)
+        assert wait(srv, [jok])[jok]["step"] == 40
+        srv.close()
+    finally:
+        pimd.reset_allocator()
