@@ -47,6 +47,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the plain FP64 workload (default: --steps)")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-step-scale", type=float, default=0.1)
     return ap.parse_args()
 
 
@@ -169,6 +176,127 @@ def traffic_for(kernel):
         return float(t["bytes_per_launch"])
     except Exception:
         return None
+
+
+def hbm_peak():
+    """Measured copy bandwidth of this GPU pool (GB/s), else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def batched_bench(stream, steps, warmup):
+    """The batched workload: 256 independent water-like replicas (32-512
+    molecules log-uniform at 1 g/cm^3, P in {8,16,32,64}, T in [100,400] K,
+    H or D), split precision, one batch; each timed step is 100 MD steps of
+    every replica plus the estimators of all of them."""
+    import torch
+    from paper_2602_13553_gb300 import binding, inputs
+    reps = inputs.replica_mix(256, seed=1)
+    b = binding.Batch(256, stream=stream.cuda_stream)
+    units = 0
+    step_bytes = 0.0
+    force_bytes = 0.0
+    for r in reps:
+        x0, mass = inputs.water_box(r.nmol, r.L, r.P, r.seed, jitter=0.02, deuterium=r.deuterium)
+        b.add(x0, mass, T=r.T, dt=5e-4, nsteps=10 ** 12, ff=inputs.water_ff_for_box(r.L),
+              box=(r.L,) * 3, seed=r.seed)
+        N = 3 * r.nmol
+        units += N * r.P
+        # compulsory HBM bytes per launch: step reads d, v~, F and writes d, v~
+        # (FP32, 60 B per bead-atom) plus 124 B per atom (FP64 centroid position
+        # and velocity read+write, wrapped FP32 centroid, two FP64 constants);
+        # force reads d and writes F (24 B per bead-atom), 12 B per atom of
+        # centroids, 16 B per molecule-bead of energy/virial rows
+        step_bytes += 60.0 * N * r.P + 124.0 * N
+        force_bytes += 24.0 * N * r.P + 12.0 * N + 16.0 * r.nmol * r.P
+    tiles = b.autotune(1)
+    for _ in range(warmup):
+        b.run(100)
+        b.estimators()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = b.kernel_launches()
+    for i in range(steps):
+        ev[i][0].record(stream)
+        b.run(100)
+        b.estimators()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = b.kernel_launches() - l0
+    ms = sum(a.elapsed_time(c) for a, c in ev)
+    value = units * 100.0 * steps / (ms / 1e3)
+    stp, _, rb = b.status(rebuilds=True)
+    live = stp >= 0
+    rebuild_rate = float(rb[live].sum() / max(1, stp[live].sum()))
+    kt = b.time_kernels(10)
+    dom = "step" if kt["step"] >= kt["force"] else "force"
+    per_ms = kt[dom] / 10.0
+    bytes_ = step_bytes if dom == "step" else force_bytes
+    peak, src = hbm_peak()
+    achieved = bytes_ / (per_ms / 1e3) / 1e9
+    b.close()
+    tot = sum(kt.values())
+    return {
+        "workload": "256 water-like replicas, 32-512 molecules log-uniform, P in {8,16,32,64}, "
+                    "T 100-400 K, H/D, split precision",
+        "value": value, "unit": METRIC, "ms_per_step": ms / steps, "md_steps_per_step": 100,
+        "bead_atoms": units, "steps": steps, "gpu_launches": int(launches), "dtype": "f32+f64 split",
+        "autotuned_tiles": {str(k): v for k, v in tiles.items()},
+        "nbr_rebuilds_per_replica_step": rebuild_rate,
+        "vs_plain_fp64": None,
+        "roofline": {"bound": "hbm", "kernel": "k_bstep" if dom == "step" else "k_bforce",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": src, "algorithmic_bytes_per_launch": bytes_,
+                     "avg_launch_ms": per_ms, "traffic": traffic_for("k_bstep" if dom == "step" else "k_bforce"),
+                     "kernel_time_share": {k: round(v / tot, 4) for k, v in kt.items()}},
+    }
+
+
+def serve_bench(stream, n_jobs, step_scale):
+    """The serving workload: a Poisson stream of water-like jobs at 50 jobs/s
+    (96-12288 atoms, P 4-128, 1k-50k steps, all log-uniform) against a 150 GB
+    budget; the first n_jobs of the trace, step counts scaled by step_scale."""
+    from paper_2602_13553_gb300 import binding, inputs
+    trace = inputs.serving_trace(n_jobs, 50.0, seed=1)
+    systems = []
+    for j in trace:
+        L = inputs.box_length(j.nmol)
+        x0, mass = inputs.water_box(j.nmol, L, j.P, j.seed % (2 ** 31), jitter=0.02)
+        systems.append((x0, mass, L, max(1, int(round(j.nsteps * step_scale)))))
+    srv = binding.Server(150 * 10 ** 9, max_replicas=512, chunk_steps=100, stream=stream.cuda_stream)
+    ids = []
+    t0 = time.perf_counter()
+    for j, (x0, mass, L, n) in zip(trace, systems):
+        delay = j.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(x0, mass, T=j.T, dt=5e-4, nsteps=n, ff=inputs.water_ff_for_box(L),
+                              box=(L,) * 3, seed=j.seed))
+    pending = set(ids)
+    while pending:
+        for jid in list(pending):
+            if srv.poll(jid) is not None:
+                pending.discard(jid)
+        time.sleep(0.01)
+    lat, first, last = [], None, None
+    for jid in ids:
+        sub, start, end = srv.times(jid)
+        lat.append(end - sub)
+        first = sub if first is None else min(first, sub)
+        last = end if last is None else max(last, end)
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {
+        "workload": "Poisson water-like jobs at 50/s, first %d of the trace, steps x %g" % (n_jobs, step_scale),
+        "jobs": n_jobs, "completed": int(st["completed"]), "failed": int(st["failed"]),
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "aggregate": st["bead_atom_steps"] / (last - first), "unit": METRIC,
+        "makespan_s": last - first, "gpu_busy_s": st["gpu_busy_s"], "chunks": int(st["chunks"]),
+        "hbm_budget_gb": 150,
+    }
 
 
 def cpu_baseline(target_s=12.0):
@@ -359,6 +487,11 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if world == 1 and not args.no_batched:
+        line["batched"] = batched_bench(stream, args.batched_steps, 3)
+        line["batched"]["vs_plain_fp64"] = line["batched"]["value"] / value
+    if world == 1 and not args.no_serve:
+        line["serve"] = serve_bench(stream, args.serve_jobs, args.serve_step_scale)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

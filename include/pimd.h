@@ -279,9 +279,10 @@ pimd_status pimd_batch_remove(pimd_batch *b, int32_t slot);
 pimd_status pimd_batch_run(pimd_batch *b, int64_t nsteps);
 pimd_status pimd_batch_sync(pimd_batch *b);
 
-/* step[s], steps_left[s] for every slot s < max_replicas (-1 for empty
- * slots); either array may be NULL.  Synchronises. */
-pimd_status pimd_batch_status(pimd_batch *b, int64_t *step, int64_t *steps_left);
+/* step[s], steps_left[s] and rebuilds[s] (neighbour-list builds so far) for
+ * every slot s < max_replicas (-1 for empty slots); any array may be NULL.
+ * Synchronises. */
+pimd_status pimd_batch_status(pimd_batch *b, int64_t *step, int64_t *steps_left, int64_t *rebuilds);
 
 /* App. A estimators of every slot into out[0..max_replicas) (empty slots get
  * step = -1).  Synchronises. */
@@ -297,7 +298,13 @@ pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double *x, double 
  * receives PIMD_MAX_BEADS + 1 entries: the chosen tile per P (0 = unused). */
 pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t *tiles_out);
 
+/* Kernel accounting: kernels enqueued so far (graph nodes included), and
+ * nsteps real steps launched one kernel at a time with CUDA events around
+ * each of the step's four kernels: ms[0..3] receive the summed device
+ * milliseconds of the control, fused-step, neighbour-list and force kernels.
+ * The timed steps leave the replicas at integer time, like pimd_batch_run. */
 int64_t pimd_batch_kernel_launches(const pimd_batch *b);
+pimd_status pimd_batch_time_kernels(pimd_batch *b, int32_t nsteps, double *ms);
 void pimd_batch_destroy(pimd_batch *b);
 
 /* ---- serving -----------------------------------------------------------------

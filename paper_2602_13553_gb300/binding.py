@@ -89,6 +89,7 @@ EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "p
            "pimd_batch_replica_bytes", "pimd_batch_create", "pimd_batch_add", "pimd_batch_remove",
            "pimd_batch_run", "pimd_batch_sync", "pimd_batch_status", "pimd_batch_estimators",
            "pimd_batch_get_state", "pimd_batch_autotune", "pimd_batch_kernel_launches",
+           "pimd_batch_time_kernels",
            "pimd_batch_destroy", "pimd_server_create", "pimd_batch_submit", "pimd_batch_poll",
            "pimd_batch_cancel", "pimd_server_job_times", "pimd_server_stats_get", "pimd_server_destroy")
 KINDS = ("step", "force", "nbr", "close", "est", "other")
@@ -305,11 +306,12 @@ def _batch_lib():
         "pimd_batch_remove": ([vp, ctypes.c_int32], ctypes.c_int),
         "pimd_batch_run": ([vp, ctypes.c_int64], ctypes.c_int),
         "pimd_batch_sync": ([vp], ctypes.c_int),
-        "pimd_batch_status": ([vp, i64, i64], ctypes.c_int),
+        "pimd_batch_status": ([vp, i64, i64, i64], ctypes.c_int),
         "pimd_batch_estimators": ([vp, ctypes.POINTER(Estimates)], ctypes.c_int),
         "pimd_batch_get_state": ([vp, ctypes.c_int32, dp, dp, i64], ctypes.c_int),
         "pimd_batch_autotune": ([vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "pimd_batch_kernel_launches": ([vp], ctypes.c_int64),
+        "pimd_batch_time_kernels": ([vp, ctypes.c_int32, dp], ctypes.c_int),
         "pimd_batch_destroy": ([vp], None),
         "pimd_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.c_int64, vp, ctypes.POINTER(vp)],
                                ctypes.c_int),
@@ -381,10 +383,13 @@ class Batch:
     def sync(self) -> None:
         check(_batch_lib().pimd_batch_sync(self._h))
 
-    def status(self):
+    def status(self, rebuilds: bool = False):
         st = (ctypes.c_int64 * self.capacity)()
         left = (ctypes.c_int64 * self.capacity)()
-        check(_batch_lib().pimd_batch_status(self._h, st, left))
+        rb = (ctypes.c_int64 * self.capacity)()
+        check(_batch_lib().pimd_batch_status(self._h, st, left, rb))
+        if rebuilds:
+            return np.array(st[:]), np.array(left[:]), np.array(rb[:])
         return np.array(st[:]), np.array(left[:])
 
     def estimators(self):
@@ -407,6 +412,11 @@ class Batch:
 
     def kernel_launches(self) -> int:
         return int(_batch_lib().pimd_batch_kernel_launches(self._h))
+
+    def time_kernels(self, nsteps: int) -> dict:
+        ms = (ctypes.c_double * 4)()
+        check(_batch_lib().pimd_batch_time_kernels(self._h, int(nsteps), ms))
+        return dict(zip(("ctl", "step", "nbr", "force"), list(ms)))
 
     def close(self) -> None:
         if getattr(self, "_h", None):

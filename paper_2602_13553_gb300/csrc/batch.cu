@@ -47,9 +47,12 @@ cudaError_t launch_expand_split(const SplitStepArgs &a, const float *F, double *
 cudaError_t launch_centroids(const NbrArgs &a, double *ccur, cudaStream_t s);
 int water_lane_groups(int P);
 
-constexpr int kTileMax = 3 * kMaxBeads;   // largest A * 3 * P of a step tile
+constexpr int kTileMax = 3 * 512;   // largest A * 3 * P of a step tile (A P <= 512)
+constexpr int kBatchMaxMol = 4096;   // molecules per replica (centroids staged in shared memory)
+constexpr int kNbrMolPerItem = 32;   // molecules per neighbour-list work item
+constexpr size_t kNbrSmem = 3 * kBatchMaxMol * sizeof(float);
 constexpr int kOutStride = 3 * kMaxBeads + 10;  // pimd_estimates layout from K_mode on
-enum { kCtlStep = 0, kCtlLeft = 1, kCtlFirst = 2, kCtlActive = 3, kCtlClose = 4, kCtlWords = 8 };
+enum { kCtlStep = 0, kCtlLeft = 1, kCtlFirst = 2, kCtlActive = 3, kCtlClose = 4, kCtlRebuilds = 5, kCtlWords = 8 };
 
 struct RepDesc {
   int live, N, P, nmol, A, G, integrator, thermo;
@@ -125,49 +128,252 @@ __device__ __forceinline__ float wrapb(double x, double L, double invL) {
 
 __device__ __forceinline__ float micb(float d, float L, float invL) { return fmaf(-rintf(d * invL), L, d); }
 
+// Three standard normal deviates of (atom, mode, stream, step) in FP32 from
+// one Philox call (the same words and mapping as gauss1f_b per component).
+__device__ __forceinline__ void gauss3f_b(uint64_t seed, uint32_t atom, uint32_t mode, uint32_t stream,
+                                          uint64_t step, float &e0, float &e1, float &e2) {
+  const uint4 w = philox4x32_10(
+      make_uint4(atom, (mode & 0xffffu) | (stream << 16), (uint32_t)step, (uint32_t)(step >> 32)),
+      make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const float s = 5.9604644775390625e-8f;  // 2^-24
+  const float r0 = sqrtf(-2.0f * __logf(((float)(w.x >> 8) + 0.5f) * s));
+  const float r1 = sqrtf(-2.0f * __logf(((float)(w.z >> 8) + 0.5f) * s));
+  float sn, cs;
+  sincospif(2.0f * (((float)(w.y >> 8) + 0.5f) * s), &sn, &cs);
+  e0 = r0 * cs;
+  e1 = r0 * sn;
+  e2 = r1 * cospif(2.0f * (((float)(w.w >> 8) + 0.5f) * s));
+}
+
+// Register-blocked inner part of the batched step for P divisible by 4:
+// thread task (atom al, mode group g) forms F~ and q~ of modes 4g..4g+3 for
+// all three components -- one float4 of M^T feeds 24 FMAs -- then updates
+// those modes with one Philox draw per (atom, mode); mode 0 goes to the FP64
+// centroid update in place.  The inverse runs per (atom, bead group).
+__device__ __forceinline__ void bstep_blocked(const RepDesc *__restrict__ Rp, int P, int tile0, int na,
+                                              size_t base, float *sD, float *sV, float *sF, float *sQ,
+                                              uint64_t step, int first) {
+  const int NG = P >> 2;
+  const float4 *__restrict__ Mt4 = reinterpret_cast<const float4 *>(Rp->Mtf);
+  const float4 *__restrict__ M4 = reinterpret_cast<const float4 *>(Rp->Mf);
+  const float *__restrict__ cAf = Rp->cAf;
+  const float *__restrict__ sAf = Rp->sAf;
+  const float *__restrict__ wsAf = Rp->wsAf;
+  const float *__restrict__ c1f = Rp->c1f;
+  const float *__restrict__ c2f = Rp->c2f;
+  const double *__restrict__ inv_mm = Rp->inv_mm;
+  const double *__restrict__ sigv = Rp->sigv;
+  float *__restrict__ vkg = Rp->vk;
+  double *__restrict__ xcg = Rp->xc;
+  double *__restrict__ v0g = Rp->v0;
+  float *__restrict__ xcw = Rp->xcw;
+  const int integ = Rp->integrator, thermo = Rp->thermo;
+  const uint64_t seed = Rp->seed;
+  const double dt = Rp->dt;
+  const float hd = (float)dt, half = 0.5f * hd;
+  const float kick = first ? half : hd;
+  for (int task = threadIdx.x; task < na * NG; task += blockDim.x) {
+    const int al = task / NG, g = task - al * NG;
+    const int i = tile0 + al;
+    const float *fr = sF + al * 3 * P;
+    const float *xr = sD + al * 3 * P;
+    float f[3][4], q[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) f[c][t] = q[c][t] = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < P; ++j) {
+      const float4 m = __ldg(Mt4 + j * NG + g);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float fj = fr[c * P + j], xj = xr[c * P + j];
+        f[c][0] = fmaf(m.x, fj, f[c][0]);
+        f[c][1] = fmaf(m.y, fj, f[c][1]);
+        f[c][2] = fmaf(m.z, fj, f[c][2]);
+        f[c][3] = fmaf(m.w, fj, f[c][3]);
+        q[c][0] = fmaf(m.x, xj, q[c][0]);
+        q[c][1] = fmaf(m.y, xj, q[c][1]);
+        q[c][2] = fmaf(m.z, xj, q[c][2]);
+        q[c][3] = fmaf(m.w, xj, q[c][3]);
+      }
+    }
+    const float im = (float)__ldg(inv_mm + i);
+    const float sg = (float)__ldg(sigv + i);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int k = 4 * g + t;
+      if (k == 0) {
+        // centroid, FP64: q~_0 = sqrt(P) xc
+        const double dr = Rp->tA * rsqrt((double)P);
+        const double imd = __ldg(inv_mm + i), c2s = Rp->c2_0 * __ldg(sigv + i);
+        float e[3] = {0.f, 0.f, 0.f}, e2[3] = {0.f, 0.f, 0.f};
+        if (thermo) gauss3f_b(seed, (uint32_t)i, 0u, kStreamO1, step, e[0], e[1], e[2]);
+        if (thermo && integ == 1 && !first)
+          gauss3f_b(seed, (uint32_t)i, 0u, kStreamO2, step - 1, e2[0], e2[1], e2[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const size_t ic = (size_t)i * 3 + c;
+          double x = xcg[ic], v = v0g[ic];
+          const double f0 = (double)f[c][0];
+          if (integ == 0) {
+            v = fma((first ? 0.5 : 1.0) * dt * imd, f0, v);
+            x = fma(dr, v, x);
+            if (thermo) v = fma(Rp->c1_0, v, c2s * (double)e[c]);
+            x = fma(dr, v, x);
+          } else {
+            const double kb = 0.5 * dt * imd;
+            if (!first) {
+              v = fma(kb, f0, v);
+              if (thermo) v = fma(Rp->c1_0, v, c2s * (double)e2[c]);
+            }
+            if (thermo) v = fma(Rp->c1_0, v, c2s * (double)e[c]);
+            v = fma(kb, f0, v);
+            x = fma(dr, v, x);
+          }
+          xcg[ic] = x;
+          v0g[ic] = v;
+          xcw[ic] = wrapb(x, Rp->box[c], Rp->invbox[c]);
+          sQ[(al * 3 + c) * P] = 0.f;
+        }
+        continue;
+      }
+      const float cA = __ldg(cAf + k), sA = __ldg(sAf + k), wsA = __ldg(wsAf + k);
+      const float c1 = __ldg(c1f + k), c2s = __ldg(c2f + k) * sg;
+      float e[3] = {0.f, 0.f, 0.f}, e2[3] = {0.f, 0.f, 0.f};
+      if (thermo) gauss3f_b(seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, e[0], e[1], e[2]);
+      if (thermo && integ == 1 && !first)
+        gauss3f_b(seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, e2[0], e2[1], e2[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int sidx = (al * 3 + c) * P + k;
+        float v = sV[sidx];
+        float qq = q[c][t];
+        const float ff = f[c][t];
+        if (integ == 0) {
+          v = fmaf(kick * im, ff, v);
+          rotb(qq, v, cA, sA, wsA);
+          if (thermo) v = fmaf(c1, v, c2s * e[c]);
+          rotb(qq, v, cA, sA, wsA);
+        } else {
+          const float kb = half * im;
+          if (!first) {
+            v = fmaf(kb, ff, v);
+            if (thermo) v = fmaf(c1, v, c2s * e2[c]);
+          }
+          if (thermo) v = fmaf(c1, v, c2s * e[c]);
+          v = fmaf(kb, ff, v);
+          rotb(qq, v, cA, sA, wsA);
+        }
+        sQ[sidx] = qq;
+        vkg[base + sidx] = v;
+      }
+    }
+  }
+  __syncthreads();
+  float *__restrict__ dg = Rp->d;
+  for (int task = threadIdx.x; task < na * NG; task += blockDim.x) {
+    const int al = task / NG, g = task - al * NG;
+    const float *qr = sQ + al * 3 * P;
+    float x[3][4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) x[c][t] = 0.f;
+#pragma unroll 4
+    for (int k = 1; k < P; ++k) {
+      const float4 m = __ldg(M4 + k * NG + g);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float qk = qr[c * P + k];
+        x[c][0] = fmaf(m.x, qk, x[c][0]);
+        x[c][1] = fmaf(m.y, qk, x[c][1]);
+        x[c][2] = fmaf(m.z, qk, x[c][2]);
+        x[c][3] = fmaf(m.w, qk, x[c][3]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int o = (al * 3 + c) * P + 4 * g;
+      *reinterpret_cast<float4 *>(dg + base + o) = make_float4(x[c][0], x[c][1], x[c][2], x[c][3]);
+      sD[o] = x[c][0];
+      sD[o + 1] = x[c][1];
+      sD[o + 2] = x[c][2];
+      sD[o + 3] = x[c][3];
+    }
+  }
+}
+
 // The split-precision fused step (same arithmetic as the single-system split
-// kernel) over work items (replica, tile).
-__global__ void __launch_bounds__(256) k_bstep(const RepDesc *reps, const int2 *items, const int *count) {
+// kernel) over work items (replica, tile).  Every descriptor field an item
+// needs is read once into registers (restrict-qualified), and the task index
+// split (mode, row) uses shifts when P is a power of two.
+__global__ void __launch_bounds__(128, 4) k_bstep(const RepDesc *__restrict__ reps, const int2 *__restrict__ items,
+                                               const int *__restrict__ count) {
   __shared__ float sD[kTileMax], sV[kTileMax], sF[kTileMax], sQ[kTileMax];
-  __shared__ double sred[2][8];
+  __shared__ double sred[2][4];
   const int n = *count;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = items[it];
-    const RepDesc &R = reps[w.x];
-    if (!R.ctl[kCtlActive]) continue;
-    const int P = R.P, A = R.A, N = R.N;
+    const RepDesc *__restrict__ Rp = reps + w.x;
+    long long *__restrict__ ctl = Rp->ctl;
+    if (!ctl[kCtlActive]) continue;
+    const int P = Rp->P, A = Rp->A, N = Rp->N, integ = Rp->integrator, thermo = Rp->thermo;
+    const int lg = (P & (P - 1)) == 0 ? __ffs(P) - 1 : -1;
+    const uint64_t seed = Rp->seed;
+    const float *__restrict__ Mtf = Rp->Mtf;
+    const float *__restrict__ Mf = Rp->Mf;
+    const float *__restrict__ cAf = Rp->cAf;
+    const float *__restrict__ sAf = Rp->sAf;
+    const float *__restrict__ wsAf = Rp->wsAf;
+    const float *__restrict__ c1f = Rp->c1f;
+    const float *__restrict__ c2f = Rp->c2f;
+    const double *__restrict__ inv_mm = Rp->inv_mm;
+    const double *__restrict__ sigv = Rp->sigv;
+    float *__restrict__ dg = Rp->d;
+    float *__restrict__ vkg = Rp->vk;
+    const float *__restrict__ Fg = Rp->F;
+    double *__restrict__ xcg = Rp->xc;
+    double *__restrict__ v0g = Rp->v0;
+    float *__restrict__ xcw = Rp->xcw;
+    const double dt = Rp->dt, tA = Rp->tA, c1_0 = Rp->c1_0, c2_0 = Rp->c2_0;
     const int tile0 = w.y * A;
     const int na = min(A, N - tile0);
     const int len = na * 3 * P;
     const size_t base = (size_t)tile0 * 3 * P;
     for (int t = threadIdx.x; t < len; t += blockDim.x) {
-      sD[t] = R.d[base + t];
-      sV[t] = R.vk[base + t];
-      sF[t] = R.F[base + t];
+      sD[t] = dg[base + t];
+      sV[t] = vkg[base + t];
+      sF[t] = Fg[base + t];
     }
     __syncthreads();
-    const uint64_t step = (uint64_t)R.ctl[kCtlStep];
-    const int first = (int)R.ctl[kCtlFirst];
-    const float hd = (float)R.dt, half = 0.5f * hd;
+    const uint64_t step = (uint64_t)ctl[kCtlStep];
+    const int first = (int)ctl[kCtlFirst];
+    const float hd = (float)dt, half = 0.5f * hd;
     const float kick = first ? half : hd;
+    if ((P & 3) == 0) {
+      bstep_blocked(Rp, P, tile0, na, base, sD, sV, sF, sQ, step, first);
+    } else {
     for (int task = threadIdx.x; task < len; task += blockDim.x) {
-      const int k = task % P;
-      const int r = task / P;
+      const int k = lg >= 0 ? (task & (P - 1)) : task % P;
+      const int r = lg >= 0 ? (task >> lg) : task / P;
       const int c = r % 3;
       const int i = tile0 + r / 3;
       const float *fx = sF + r * P;
       const float *xx = sD + r * P;
       float fa = 0.f, fb = 0.f, qa = 0.f, qb = 0.f;
+      const float *mcol = Mtf + k;
       int j = 0;
+#pragma unroll 4
       for (; j + 1 < P; j += 2) {
-        const float m0 = __ldg(R.Mtf + j * P + k), m1 = __ldg(R.Mtf + (j + 1) * P + k);
+        const float m0 = __ldg(mcol + j * P), m1 = __ldg(mcol + (j + 1) * P);
         fa = fmaf(m0, fx[j], fa);
         fb = fmaf(m1, fx[j + 1], fb);
         qa = fmaf(m0, xx[j], qa);
         qb = fmaf(m1, xx[j + 1], qb);
       }
       if (j < P) {
-        const float m0 = __ldg(R.Mtf + j * P + k);
+        const float m0 = __ldg(mcol + j * P);
         fa = fmaf(m0, fx[j], fa);
         qa = fmaf(m0, xx[j], qa);
       }
@@ -178,27 +384,26 @@ __global__ void __launch_bounds__(256) k_bstep(const RepDesc *reps, const int2 *
       }
       float q = qa + qb;
       float v = sV[task];
-      const float im = (float)__ldg(R.inv_mm + i);
-      const float cA = __ldg(R.cAf + k), sA = __ldg(R.sAf + k), wsA = __ldg(R.wsAf + k);
-      const float c1 = __ldg(R.c1f + k), c2s = __ldg(R.c2f + k) * (float)__ldg(R.sigv + i);
-      if (R.integrator == 0) {
+      const float im = (float)__ldg(inv_mm + i);
+      const float cA = __ldg(cAf + k), sA = __ldg(sAf + k), wsA = __ldg(wsAf + k);
+      const float c1 = __ldg(c1f + k), c2s = __ldg(c2f + k) * (float)__ldg(sigv + i);
+      if (integ == 0) {
         v = fmaf(kick * im, f, v);
         rotb(q, v, cA, sA, wsA);
-        if (R.thermo) v = fmaf(c1, v, c2s * gauss1f_b(R.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
+        if (thermo) v = fmaf(c1, v, c2s * gauss1f_b(seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
         rotb(q, v, cA, sA, wsA);
       } else {
         const float kb = half * im;
         if (!first) {
           v = fmaf(kb, f, v);
-          if (R.thermo)
-            v = fmaf(c1, v, c2s * gauss1f_b(R.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, c));
+          if (thermo) v = fmaf(c1, v, c2s * gauss1f_b(seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, c));
         }
-        if (R.thermo) v = fmaf(c1, v, c2s * gauss1f_b(R.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
+        if (thermo) v = fmaf(c1, v, c2s * gauss1f_b(seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
         v = fmaf(kb, f, v);
         rotb(q, v, cA, sA, wsA);
       }
       sQ[task] = q;
-      R.vk[base + task] = v;
+      vkg[base + task] = v;
     }
     __syncthreads();
     const double rsp = rsqrt((double)P);
@@ -207,79 +412,88 @@ __global__ void __launch_bounds__(256) k_bstep(const RepDesc *reps, const int2 *
       const int i = tile0 + al;
       const size_t ic = (size_t)i * 3 + c;
       const double f0 = (double)sQ[t * P];
-      double x = R.xc[ic], v = R.v0[ic];
-      const double im = __ldg(R.inv_mm + i);
-      const double dr = R.tA * rsp;
-      const double c2s = R.c2_0 * __ldg(R.sigv + i);
-      if (R.integrator == 0) {
-        v = fma((first ? 0.5 : 1.0) * R.dt * im, f0, v);
+      double x = xcg[ic], v = v0g[ic];
+      const double im = __ldg(inv_mm + i);
+      const double dr = tA * rsp;
+      const double c2s = c2_0 * __ldg(sigv + i);
+      if (integ == 0) {
+        v = fma((first ? 0.5 : 1.0) * dt * im, f0, v);
         x = fma(dr, v, x);
-        if (R.thermo) v = fma(R.c1_0, v, c2s * (double)gauss1f_b(R.seed, (uint32_t)i, 0u, kStreamO1, step, c));
+        if (thermo) v = fma(c1_0, v, c2s * (double)gauss1f_b(seed, (uint32_t)i, 0u, kStreamO1, step, c));
         x = fma(dr, v, x);
       } else {
-        const double kb = 0.5 * R.dt * im;
+        const double kb = 0.5 * dt * im;
         if (!first) {
           v = fma(kb, f0, v);
-          if (R.thermo)
-            v = fma(R.c1_0, v, c2s * (double)gauss1f_b(R.seed, (uint32_t)i, 0u, kStreamO2, step - 1, c));
+          if (thermo) v = fma(c1_0, v, c2s * (double)gauss1f_b(seed, (uint32_t)i, 0u, kStreamO2, step - 1, c));
         }
-        if (R.thermo) v = fma(R.c1_0, v, c2s * (double)gauss1f_b(R.seed, (uint32_t)i, 0u, kStreamO1, step, c));
+        if (thermo) v = fma(c1_0, v, c2s * (double)gauss1f_b(seed, (uint32_t)i, 0u, kStreamO1, step, c));
         v = fma(kb, f0, v);
         x = fma(dr, v, x);
       }
-      R.xc[ic] = x;
-      R.v0[ic] = v;
-      R.xcw[ic] = wrapb(x, R.box[c], R.invbox[c]);
+      xcg[ic] = x;
+      v0g[ic] = v;
+      xcw[ic] = wrapb(x, Rp->box[c], Rp->invbox[c]);
       sQ[t * P] = 0.f;
     }
     __syncthreads();
     for (int task = threadIdx.x; task < len; task += blockDim.x) {
-      const int j = task % P;
-      const float *qq = sQ + (task / P) * P;
+      const int jj = lg >= 0 ? (task & (P - 1)) : task % P;
+      const int row = lg >= 0 ? (task >> lg) : task / P;
+      const float *qq = sQ + row * P;
+      const float *mrow = Mf + jj;
       float xa = 0.f, xb = 0.f;
       int k = 1;
+#pragma unroll 4
       for (; k + 1 < P; k += 2) {
-        xa = fmaf(__ldg(R.Mf + k * P + j), qq[k], xa);
-        xb = fmaf(__ldg(R.Mf + (k + 1) * P + j), qq[k + 1], xb);
+        xa = fmaf(__ldg(mrow + k * P), qq[k], xa);
+        xb = fmaf(__ldg(mrow + (k + 1) * P), qq[k + 1], xb);
       }
-      if (k < P) xa = fmaf(__ldg(R.Mf + k * P + j), qq[k], xa);
+      if (k < P) xa = fmaf(__ldg(mrow + k * P), qq[k], xa);
       const float dn = xa + xb;
-      R.d[base + task] = dn;
+      dg[base + task] = dn;
       sD[task] = dn;
     }
+    }  // generic P
     __syncthreads();
-    double vdisp = 0.0, vdev = 0.0;
+    double vdisp = 0.0;
+    float vdevf = 0.f;
+    const double *__restrict__ cref = Rp->cref;
+    double *__restrict__ ccur = Rp->ccur;
     for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
-      const int al = t / P, k = t % P;
+      const int al = lg >= 0 ? (t >> lg) : t / P;
+      const int k = lg >= 0 ? (t & (P - 1)) : t % P;
       const int i = tile0 + al;
       if (i % 3) continue;
       const float *ds = sD + al * 3 * P;
       const float e0 = ds[k], e1 = ds[P + k], e2 = ds[2 * P + k];
-      vdev = fmax(vdev, (double)(e0 * e0 + e1 * e1 + e2 * e2));
+      vdevf = fmaxf(vdevf, e0 * e0 + e1 * e1 + e2 * e2);
       if (k == 0) {
         const int m = i / 3;
-        const double c0 = R.xc[3 * (size_t)i], c1 = R.xc[3 * (size_t)i + 1], c2 = R.xc[3 * (size_t)i + 2];
-        const double g0 = c0 - R.cref[3 * m], g1 = c1 - R.cref[3 * m + 1], g2 = c2 - R.cref[3 * m + 2];
+        const double c0 = xcg[3 * (size_t)i], c1 = xcg[3 * (size_t)i + 1], c2 = xcg[3 * (size_t)i + 2];
+        const double g0 = c0 - cref[3 * m], g1 = c1 - cref[3 * m + 1], g2 = c2 - cref[3 * m + 2];
         vdisp = fmax(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
-        R.ccur[3 * m] = c0;
-        R.ccur[3 * m + 1] = c1;
-        R.ccur[3 * m + 2] = c2;
+        ccur[3 * m] = c0;
+        ccur[3 * m + 1] = c1;
+        ccur[3 * m + 2] = c2;
       }
     }
+    float vdispf = (float)vdisp;   // squared drifts: FP32 is ample for a rebuild criterion
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      vdisp = fmax(vdisp, __shfl_down_sync(0xffffffffu, vdisp, o));
-      vdev = fmax(vdev, __shfl_down_sync(0xffffffffu, vdev, o));
+      vdispf = fmaxf(vdispf, __shfl_down_sync(0xffffffffu, vdispf, o));
+      vdevf = fmaxf(vdevf, __shfl_down_sync(0xffffffffu, vdevf, o));
     }
     if ((threadIdx.x & 31) == 0) {
-      sred[0][threadIdx.x >> 5] = vdisp;
-      sred[1][threadIdx.x >> 5] = vdev;
+      sred[0][threadIdx.x >> 5] = vdispf;
+      sred[1][threadIdx.x >> 5] = vdevf;
     }
     __syncthreads();
     if (threadIdx.x < 2) {
       double mx = 0.0;
       for (int ww = 0; ww < (int)((blockDim.x + 31) / 32); ++ww) mx = fmax(mx, sred[threadIdx.x][ww]);
-      R.blkmax[2 * w.y + threadIdx.x] = (mx == mx) ? sqrt(mx) + 1e-4 : 1e300;
+      // margins for FP32 rounding of the deviations and squared drifts; NaN forces a rebuild
+      Rp->blkmax[2 * w.y + threadIdx.x] = (mx == mx) ? sqrt(mx) * (1.0 + 1e-6) + 1e-4 : 1e300;
     }
     __syncthreads();
   }
@@ -287,7 +501,7 @@ __global__ void __launch_bounds__(256) k_bstep(const RepDesc *reps, const int2 *
 
 // Closing B(h/2) (O(h/2) for OBABO) of the replicas that stepped since their
 // last closing kick, over step items.
-__global__ void __launch_bounds__(256) k_bclose(const RepDesc *reps, const int2 *items, const int *count) {
+__global__ void __launch_bounds__(128) k_bclose(const RepDesc *reps, const int2 *items, const int *count) {
   __shared__ float sF[kTileMax];
   const int n = *count;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
@@ -362,220 +576,191 @@ __global__ void k_bnbr(const RepDesc *reps, const int2 *items, const int *count,
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) s_go = force_all || (2.0 * sd[0] + 2.0 * se[0] > R.skin);
+    if (threadIdx.x == 0) {
+      s_go = force_all || (2.0 * sd[0] + 2.0 * se[0] > R.skin);
+      if (s_go && w.y == 0) R.ctl[kCtlRebuilds] += 1;
+    }
     __syncthreads();
-    const int m = w.y * 128 + threadIdx.x;
-    if (s_go && m < R.nmol) {
+    if (s_go) {
+      // the replica's oxygen centroids (wrapped, FP32) into shared memory
+      extern __shared__ float s_cw[];
+      for (int t = threadIdx.x; t < 3 * R.nmol; t += blockDim.x) s_cw[t] = R.xcw[9 * (t / 3) + t % 3];
+      __syncthreads();
+      // One warp per molecule of this item's 32: the warp walks the buckets
+      // b = 0..NS-1 (neighbours j = b mod NS, increasing j), 32 candidates per
+      // ballot, and compacts the hits in order.  Candidates are tested in FP32
+      // on the wrapped centroids within rc + skin + 1e-3 A (FP32 rounding of
+      // the centroids is ~1e-5 A); extra far candidates add nothing to any
+      // force.
       const int NS = kLJWarps * R.G;
-      const double c0 = R.ccur[3 * m], c1 = R.ccur[3 * m + 1], c2 = R.ccur[3 * m + 2];
-      const double rl2 = R.rlist * R.rlist;
-      int cnt[kMaxBuckets];
-      for (int b = 0; b < NS; ++b) cnt[b] = 0;
-      int nn = 0;
-      for (int j = 0; j < R.nmol; ++j) {
-        if (j == m) continue;
-        const double d0 = mic(R.ccur[3 * j] - c0, R.box[0], R.invbox[0]);
-        const double d1 = mic(R.ccur[3 * j + 1] - c1, R.box[1], R.invbox[1]);
-        const double d2 = mic(R.ccur[3 * j + 2] - c2, R.box[2], R.invbox[2]);
-        if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
-          ++cnt[j % NS];
-          ++nn;
-        }
-      }
-      int *off = R.nbr_off + (size_t)m * (NS + 1);
-      if (nn > kMaxNeighbours) {
-        R.ctl[kCtlWords - 1] |= kErrNbrOverflow;
-        for (int b = 0; b <= NS; ++b) off[b] = 0;
-      } else {
-        int acc = 0;
-        for (int b = 0; b < NS; ++b) {
-          off[b] = acc;
-          acc += cnt[b];
-          cnt[b] = 0;
-        }
-        off[NS] = acc;
+      const float *cw = s_cw;
+      const float L0 = (float)R.box[0], L1 = (float)R.box[1], L2 = (float)R.box[2];
+      const float i0 = (float)R.invbox[0], i1 = (float)R.invbox[1], i2 = (float)R.invbox[2];
+      const float rl = (float)(R.rlist + 1e-3);
+      const float rl2 = rl * rl;
+      const int lane = threadIdx.x & 31;
+      const int nmol = R.nmol;
+      for (int mm = threadIdx.x >> 5; mm < kNbrMolPerItem; mm += blockDim.x >> 5) {
+        const int m = w.y * kNbrMolPerItem + mm;
+        if (m >= nmol) break;
+        const float c0 = cw[3 * m], c1 = cw[3 * m + 1], c2 = cw[3 * m + 2];
+        int *off = R.nbr_off + (size_t)m * (NS + 1);
         int *nl = R.nbr + (size_t)m * kMaxNeighbours;
-        for (int j = 0; j < R.nmol; ++j) {
-          if (j == m) continue;
-          const double d0 = mic(R.ccur[3 * j] - c0, R.box[0], R.invbox[0]);
-          const double d1 = mic(R.ccur[3 * j + 1] - c1, R.box[1], R.invbox[1]);
-          const double d2 = mic(R.ccur[3 * j + 2] - c2, R.box[2], R.invbox[2]);
-          if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
-            const int b = j % NS;
-            nl[off[b] + cnt[b]++] = j;
+        int total = 0;
+        for (int b = 0; b < NS; ++b) {
+          if (lane == 0) off[b] = total;
+          for (int j0 = b; j0 < nmol; j0 += 32 * NS) {
+            const int j = j0 + lane * NS;
+            bool hit = false;
+            if (j < nmol && j != m) {
+              const float d0 = micb(cw[3 * j] - c0, L0, i0);
+              const float d1 = micb(cw[3 * j + 1] - c1, L1, i1);
+              const float d2 = micb(cw[3 * j + 2] - c2, L2, i2);
+              hit = d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, hit);
+            const int pos = total + __popc(mask & ((1u << lane) - 1u));
+            if (hit && pos < kMaxNeighbours) nl[pos] = j;
+            total += __popc(mask);
           }
         }
-        R.cref[3 * m] = c0;
-        R.cref[3 * m + 1] = c1;
-        R.cref[3 * m + 2] = c2;
+        if (lane == 0) {
+          if (total > kMaxNeighbours) {
+            // leave an empty list and report: the forces are incomplete
+            atomicOr((unsigned long long *)&R.ctl[kCtlWords - 1], (unsigned long long)kErrNbrOverflow);
+            for (int b = 0; b <= NS; ++b) off[b] = 0;
+          } else {
+            off[NS] = total;
+            R.cref[3 * m] = R.ccur[3 * m];
+            R.cref[3 * m + 1] = R.ccur[3 * m + 1];
+            R.cref[3 * m + 2] = R.ccur[3 * m + 2];
+          }
+        }
       }
     }
     __syncthreads();
   }
 }
 
-// Water-like forces in FP32 over cluster work items (replica, molecule,
-// bead chunk): the decomposition of the single-system split kernel.
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128)
-    k_bforce(const RepDesc *reps, const int4 *items, const int *count, int force_all) {
-  __shared__ float sacc[9][128];
-  __shared__ double saccd[2][128];
-  __shared__ float red[9][32];
-  __shared__ double redd[2][32];
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
+// Water-like forces in FP32, one warp per work item (replica, first
+// molecule, bead chunk): lane = (group u, bead kl) with Bk = min(P, 32) beads
+// per group and G = 32 / Bk molecules per warp (m = first + u), so every
+// lane is busy whatever P is.  Each lane evaluates its molecule-bead's two
+// bonds, the angle and the O-O Lennard-Jones sum over the whole neighbour
+// list, and writes the three atoms' forces and its U / Tr Xi row entries:
+// no cross-lane reduction.  The list is grouped by j mod NS and index-ordered
+// within a group, so the summation order depends only on the interacting
+// pairs (far candidates add nothing): alone-vs-mix and rebuild invariant.
+__global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps, const int4 *__restrict__ items,
+                                                const int *__restrict__ count, int force_all) {
   const int n = *count;
-  const int ncl = gridDim.x >> 2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = rank * 4 + warp;
-  for (int it = blockIdx.x >> 2; it < n; it += ncl) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int it = gw; it < n; it += nw) {
     const int4 w = items[it];
-    const RepDesc &R = reps[w.x];
-    if (!force_all && !R.ctl[kCtlActive]) continue;
-    const int P = R.P, m = w.y, chunk = w.z;
+    const RepDesc *__restrict__ Rp = reps + w.x;
+    if (!force_all && !Rp->ctl[kCtlActive]) continue;
+    const RepDesc &R = *Rp;
+    const int P = R.P;
+    const float *__restrict__ dg = R.d;
+    const float *__restrict__ xcw = R.xcw;
     const int Bk = P < 32 ? P : 32;
-    const int G = R.G;
-    const int NS = kLJWarps * G;
+    const int G = 32 / Bk;
     const int u = lane / Bk, kl = lane % Bk;
-    const int k = chunk * Bk + kl;
-    float acc[9];
+    const int m = w.y + u;
+    const int k = w.z * Bk + kl;
+    if (u >= G || m >= R.nmol || k >= P) continue;
+    const int o = 3 * m;
+    const float L0 = (float)R.box[0], L1 = (float)R.box[1], L2 = (float)R.box[2];
+    const float i0 = (float)R.invbox[0], i1 = (float)R.invbox[1], i2 = (float)R.invbox[2];
+    const size_t so = (size_t)o * 3 * P + k;
+    const float co0 = R.xcw[3 * o], co1 = R.xcw[3 * o + 1], co2 = R.xcw[3 * o + 2];
+    const float do0 = R.d[so], do1 = R.d[so + P], do2 = R.d[so + 2 * P];
+    float fO[3] = {0.f, 0.f, 0.f}, fH[2][3];
+    float dv[2][3], r[2], ir[2];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0.f;
-    double ue = 0.0, we = 0.0;
-    if (u < G && k < P) {
-      const int o = 3 * m;
-      const float L0 = (float)R.box[0], L1 = (float)R.box[1], L2 = (float)R.box[2];
-      const float i0 = (float)R.invbox[0], i1 = (float)R.invbox[1], i2 = (float)R.invbox[2];
-      const size_t so = (size_t)o * 3 * P + k;
-      const float co0 = R.xcw[3 * o], co1 = R.xcw[3 * o + 1], co2 = R.xcw[3 * o + 2];
-      const float do0 = R.d[so], do1 = R.d[so + P], do2 = R.d[so + 2 * P];
-      if (s >= kLJWarps) {
-        if (u == 0) {
-          float dv[2][3], r[2], ir[2];
+    for (int h = 0; h < 2; ++h) {
+      const int hh = o + 1 + h;
+      const size_t sh = (size_t)hh * 3 * P + k;
+      dv[h][0] = micb(R.xcw[3 * hh] - co0, L0, i0) + (R.d[sh] - do0);
+      dv[h][1] = micb(R.xcw[3 * hh + 1] - co1, L1, i1) + (R.d[sh + P] - do1);
+      dv[h][2] = micb(R.xcw[3 * hh + 2] - co2, L2, i2) + (R.d[sh + 2 * P] - do2);
+      r[h] = sqrtf(dv[h][0] * dv[h][0] + dv[h][1] * dv[h][1] + dv[h][2] * dv[h][2]);
+      ir[h] = 1.f / r[h];
+    }
+    // bonds: U = 1/2 kb (r - r0)^2
+    float ub = 0.f, wb = 0.f;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int hh = o + 1 + h;
-            const size_t sh = (size_t)hh * 3 * P + k;
-            dv[h][0] = micb(R.xcw[3 * hh] - co0, L0, i0) + (R.d[sh] - do0);
-            dv[h][1] = micb(R.xcw[3 * hh + 1] - co1, L1, i1) + (R.d[sh + P] - do1);
-            dv[h][2] = micb(R.xcw[3 * hh + 2] - co2, L2, i2) + (R.d[sh + 2 * P] - do2);
-            r[h] = sqrtf(dv[h][0] * dv[h][0] + dv[h][1] * dv[h][1] + dv[h][2] * dv[h][2]);
-            ir[h] = 1.f / r[h];
-          }
-          float uu = 0.f, ww = 0.f;
-          if (s == kLJWarps) {
+    for (int h = 0; h < 2; ++h) {
+      const float dr = r[h] - (float)R.r0;
+      ub = fmaf(0.5f * (float)R.kb * dr, dr, ub);
+      const float g = -(float)R.kb * dr * ir[h];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float dr = r[h] - (float)R.r0;
-              uu = fmaf(0.5f * (float)R.kb * dr, dr, uu);
-              const float g = -(float)R.kb * dr * ir[h];
+      for (int c = 0; c < 3; ++c) {
+        fH[h][c] = g * dv[h][c];
+        wb = fmaf(dv[h][c], fH[h][c], wb);
+      }
+    }
+    // angle: U = 1/2 kth (theta - th0)^2
+    {
+      const float ir01 = ir[0] * ir[1];
+      const float dot = dv[0][0] * dv[1][0] + dv[0][1] * dv[1][1] + dv[0][2] * dv[1][2];
+      const float cth = fminf(1.f, fmaxf(-1.f, dot * ir01));
+      const float th = acosf(cth);
+      const float dth = th - (float)R.th0;
+      const float pref = (float)R.kth * dth / sinf(th);
 #pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const float fc = g * dv[h][c];
-                acc[3 + 3 * h + c] = fc;
-                acc[c] -= fc;
-                ww = fmaf(dv[h][c], fc, ww);
-              }
-            }
-          } else {
-            const float ir01 = ir[0] * ir[1];
-            const float dot = dv[0][0] * dv[1][0] + dv[0][1] * dv[1][1] + dv[0][2] * dv[1][2];
-            const float cth = fminf(1.f, fmaxf(-1.f, dot * ir01));
-            const float th = acosf(cth);
-            const float dth = th - (float)R.th0;
-            const float pref = (float)R.kth * dth / sinf(th);
+      for (int h = 0; h < 2; ++h) {
+        const int g = 1 - h;
+        const float ch = cth * ir[h] * ir[h];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int g = 1 - h;
-              const float ch = cth * ir[h] * ir[h];
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const float fa = pref * fmaf(dv[g][c], ir01, -ch * dv[h][c]);
-                acc[3 + 3 * h + c] = fa;
-                acc[c] -= fa;
-                ww = fmaf(dv[h][c], fa, ww);
-              }
-            }
-            uu = 0.5f * (float)R.kth * dth * dth;
-          }
-          ue = uu;
-          we = ww;
+        for (int c = 0; c < 3; ++c) {
+          const float fa = pref * fmaf(dv[g][c], ir01, -ch * dv[h][c]);
+          fH[h][c] += fa;
+          wb = fmaf(dv[h][c], fa, wb);
         }
-      } else {
-        const int b = s * G + u;
-        const int *off = R.nbr_off + (size_t)m * (NS + 1);
-        const int q0 = __ldg(off + b), q1 = __ldg(off + b + 1);
-        const int *nl = R.nbr + (size_t)m * kMaxNeighbours;
-        const float rc2 = (float)(R.rc * R.rc);
-        const float sig2 = (float)(R.sig * R.sig);
-        const float e4 = (float)(4.0 * R.eps), e24 = (float)(24.0 * R.eps);
-        float f0 = 0.f, f1 = 0.f, f2 = 0.f, ulj = 0.f, wlj = 0.f;
-        for (int q = q0; q < q1; ++q) {
-          const int j = __ldg(nl + q);
-          const size_t sj = (size_t)(3 * j) * 3 * P + k;
-          const float d0 = micb(__ldg(R.xcw + 9 * j) - co0, L0, i0) + (__ldg(R.d + sj) - do0);
-          const float d1 = micb(__ldg(R.xcw + 9 * j + 1) - co1, L1, i1) + (__ldg(R.d + sj + P) - do1);
-          const float d2 = micb(__ldg(R.xcw + 9 * j + 2) - co2, L2, i2) + (__ldg(R.d + sj + 2 * P) - do2);
-          const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-          if (r2 < rc2) {
-            const float inv = 1.f / r2;
-            const float s2 = sig2 * inv;
-            const float s6 = s2 * s2 * s2;
-            ulj = fmaf(e4, fmaf(s6, s6, -s6), ulj);
-            const float fr = e24 * fmaf(2.f * s6, s6, -s6) * inv;
-            f0 = fmaf(-fr, d0, f0);
-            f1 = fmaf(-fr, d1, f1);
-            f2 = fmaf(-fr, d2, f2);
-            wlj = fmaf(fr, r2, wlj);
-          }
-        }
-        acc[0] = f0;
-        acc[1] = f1;
-        acc[2] = f2;
-        ue = 0.5 * (double)ulj;
-        we = 0.5 * (double)wlj;
+      }
+      ub = fmaf(0.5f * (float)R.kth * dth, dth, ub);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) fO[c] = -(fH[0][c] + fH[1][c]);
+    // O-O Lennard-Jones over the whole list
+    const int NS = kLJWarps * R.G;
+    const int *off = R.nbr_off + (size_t)m * (NS + 1);
+    const int q1 = __ldg(off + NS);
+    const int *__restrict__ nl = R.nbr + (size_t)m * kMaxNeighbours;
+    const float rc2 = (float)(R.rc * R.rc);
+    const float sig2 = (float)(R.sig * R.sig);
+    const float e4 = (float)(4.0 * R.eps), e24 = (float)(24.0 * R.eps);
+    float ulj = 0.f, wlj = 0.f;
+    for (int q = __ldg(off); q < q1; ++q) {
+      const int j = __ldg(nl + q);
+      const size_t sj = (size_t)(3 * j) * 3 * P + k;
+      const float d0 = micb(__ldg(xcw + 9 * j) - co0, L0, i0) + (__ldg(dg + sj) - do0);
+      const float d1 = micb(__ldg(xcw + 9 * j + 1) - co1, L1, i1) + (__ldg(dg + sj + P) - do1);
+      const float d2 = micb(__ldg(xcw + 9 * j + 2) - co2, L2, i2) + (__ldg(dg + sj + 2 * P) - do2);
+      const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      if (r2 < rc2) {
+        const float inv = 1.f / r2;
+        const float s2 = sig2 * inv;
+        const float s6 = s2 * s2 * s2;
+        ulj = fmaf(e4, fmaf(s6, s6, -s6), ulj);
+        const float fr = e24 * fmaf(2.f * s6, s6, -s6) * inv;
+        fO[0] = fmaf(-fr, d0, fO[0]);
+        fO[1] = fmaf(-fr, d1, fO[1]);
+        fO[2] = fmaf(-fr, d2, fO[2]);
+        wlj = fmaf(fr, r2, wlj);
       }
     }
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sacc[c][threadIdx.x] = acc[c];
-    saccd[0][threadIdx.x] = ue;
-    saccd[1][threadIdx.x] = we;
-    __syncthreads();
-    for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
-      const int comp = t / Bk, kk = t % Bk;
-      if (comp < 9) {
-        float sum = 0.f;
-        for (int ww = 0; ww < 4; ++ww)
-          for (int g = 0; g < G; ++g) sum += sacc[comp][ww * 32 + g * Bk + kk];
-        red[comp][kk] = sum;
-      } else {
-        double sum = 0.0;
-        for (int ww = 0; ww < 4; ++ww)
-          for (int g = 0; g < G; ++g) sum += saccd[comp - 9][ww * 32 + g * Bk + kk];
-        redd[comp - 9][kk] = sum;
-      }
+    for (int c = 0; c < 3; ++c) {
+      R.F[so + c * P] = fO[c];
+      R.F[so + 3 * P + c * P] = fH[0][c];
+      R.F[so + 6 * P + c * P] = fH[1][c];
     }
-    cluster.sync();
-    if (rank == 0) {
-      for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
-        const int comp = t / Bk, kk = t % Bk;
-        const int k2 = chunk * Bk + kk;
-        if (k2 >= P) continue;
-        if (comp < 9) {
-          float sum = 0.f;
-          for (int rr = 0; rr < 4; ++rr) sum += cluster.map_shared_rank(&red[0][0], rr)[comp * 32 + kk];
-          R.F[(size_t)(3 * m + comp / 3) * 3 * P + (comp % 3) * P + k2] = sum;
-        } else {
-          double sum = 0.0;
-          for (int rr = 0; rr < 4; ++rr) sum += cluster.map_shared_rank(&redd[0][0], rr)[(comp - 9) * 32 + kk];
-          if (comp == 9)
-            R.Upart[(size_t)m * P + k2] = sum;
-          else
-            R.Wpart[(size_t)m * P + k2] = sum;
-        }
-      }
-    }
-    cluster.sync();
+    R.Upart[(size_t)m * P + k] = (double)ub + 0.5 * (double)ulj;
+    R.Wpart[(size_t)m * P + k] = (double)wb + 0.5 * (double)wlj;
   }
 }
 
@@ -589,10 +774,12 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = items[it];
     const RepDesc &R = reps[w.x];
-    const int P = R.P, A = R.A, N = R.N;
+    const int P = R.P, N = R.N;
+    const int A = P >= 128 ? 1 : 128 / P;       // estimator tile: A P <= 128 tasks
+    const int ntiles = (N + A - 1) / A;
     const int ntask = A * P;
     double kk = 0.0, ss = 0.0, rF = 0.0, rcF = 0.0, mv0 = 0.0;
-    for (int tile = w.y; tile < R.nstep_items; tile += R.ne) {
+    for (int tile = w.y; tile < ntiles; tile += R.ne) {
       const int tile0 = tile * A;
       for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
         const int k = task % P, al = task / P;
@@ -622,8 +809,8 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
         if (k == 0) mv0 += mm * v2;
       }
     }
-    // per-mode sums: tile tasks never exceed the 128 threads (A P <= 85), so
-    // thread t always held task t, i.e. mode t mod P; sum over atoms in order
+    // per-mode sums: tile tasks never exceed the 128 threads, so thread t
+    // always held task t, i.e. mode t mod P; sum over atoms in order
     double *out = R.epart + (size_t)w.y * (2 * P + 4);
     sK[threadIdx.x] = kk;
     sS[threadIdx.x] = ss;
@@ -771,8 +958,6 @@ size_t layout_replica(Replica &r, char *base) {
   d.inv_mm = carve_ptr<double>(base, off, N);
   d.sigv = carve_ptr<double>(base, off, N);
   d.mass_mm = carve_ptr<double>(base, off, N);
-  d.Mf = carve_ptr<float>(base, off, P * P);
-  d.Mtf = carve_ptr<float>(base, off, P * P);
   d.cAf = carve_ptr<float>(base, off, P);
   d.sAf = carve_ptr<float>(base, off, P);
   d.wsAf = carve_ptr<float>(base, off, P);
@@ -789,13 +974,15 @@ size_t layout_replica(Replica &r, char *base) {
   d.Wpart = carve_ptr<double>(base, off, nmol * P);
   d.epart = carve_ptr<double>(base, off, 8 * (2 * P + 4));
   r.d_items_step = carve_ptr<int2>(base, off, N);
-  r.d_items_nbr = carve_ptr<int2>(base, off, (nmol + 127) / 128);
+  r.d_items_nbr = carve_ptr<int2>(base, off, (nmol + kNbrMolPerItem - 1) / kNbrMolPerItem);
   r.d_items_clu = carve_ptr<int4>(base, off, nmol * ((P + 31) / 32));
   r.d_counts = carve_ptr<int>(base, off, 4);
   return off + 256;
 }
 
-int default_tile(int P) { return std::max(1, 256 / (3 * P)); }
+// step tile (atoms per item): A P <= 512 for the register-blocked path (P a
+// multiple of 4), A 3 P <= 256 otherwise
+int default_tile(int P) { return (P % 4 == 0) ? std::max(1, 512 / P) : std::max(1, 256 / (3 * P)); }
 
 }  // namespace
 }  // namespace pimd
@@ -823,6 +1010,9 @@ struct pimd_batch {
   bool dirty = true;
   int64_t launches = 0;
   int tileA[PIMD_MAX_BEADS + 1] = {0};     // autotuned step tile per P (0 = default)
+  // one FP32 copy of M and M^T per bead count, shared by all replicas with
+  // that P (the normal-mode matrix depends on P only): small, L1-resident
+  float *ptab[PIMD_MAX_BEADS + 1] = {nullptr};
   std::vector<int2> h_step, h_nbr, h_est;
   std::vector<int4> h_clu;
   int h_counts[4] = {0, 0, 0, 0};
@@ -861,12 +1051,16 @@ void replica_items(pimd_batch *b, int slot, Replica &r) {
   r.items_step.clear();
   for (int t = 0; t < r.ntiles; ++t) r.items_step.push_back(make_int2(slot, t));
   r.items_nbr.clear();
-  for (int mb = 0; mb < (r.nmol + 127) / 128; ++mb) r.items_nbr.push_back(make_int2(slot, mb));
+  for (int mb = 0; mb < (r.nmol + kNbrMolPerItem - 1) / kNbrMolPerItem; ++mb)
+    r.items_nbr.push_back(make_int2(slot, mb));
   r.items_clu.clear();
   const int nchunk = (r.P + 31) / 32;
-  for (int m = 0; m < r.nmol; ++m)
+  const int per = r.P < 32 ? 32 / r.P : 1;   // molecules per warp
+  for (int m = 0; m < r.nmol; m += per)
     for (int c = 0; c < nchunk; ++c) r.items_clu.push_back(make_int4(slot, m, c, 0));
   r.items_est.clear();
+  const int Ae = r.P >= 128 ? 1 : 128 / r.P;
+  r.ne = std::min((r.N + Ae - 1) / Ae, 8);
   for (int e = 0; e < r.ne; ++e) r.items_est.push_back(make_int2(slot, e));
   r.desc.A = r.A;
   r.desc.nstep_items = r.ntiles;
@@ -922,10 +1116,10 @@ pimd_status upload(pimd_batch *b) {
 cudaError_t launch_one_step(pimd_batch *b, cudaEvent_t e0, cudaEvent_t e1) {
   k_bctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, 0);
   if (e0) cudaEventRecord(e0, b->stream);
-  k_bstep<<<b->grid_step, 256, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+  k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
   if (e1) cudaEventRecord(e1, b->stream);
-  k_bnbr<<<b->grid_nbr, 128, 0, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, 0);
-  k_bforce<<<4 * b->grid_clu, 128, 0, b->stream>>>(b->d_reps, b->d_clu, b->d_counts + 1, 0);
+  k_bnbr<<<b->grid_nbr, 128, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, 0);
+  k_bforce<<<b->grid_clu, 128, 0, b->stream>>>(b->d_reps, b->d_clu, b->d_counts + 1, 0);
   return cudaGetLastError();
 }
 
@@ -1020,11 +1214,23 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // persistent grids sized to the SM count (resident blocks per SM)
-  b->grid_step = nsm * 4;
-  b->grid_clu = nsm * 4;
-  b->grid_nbr = nsm * 2;
-  b->grid_est = nsm * 2;
+  // the rebuild stages up to kBatchMaxMol centroids in dynamic shared memory
+  if (cudaFuncSetAttribute((const void *)k_bnbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNbrSmem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    pimd_batch_destroy(b);
+    return fail(PIMD_ECUDA, "cannot enable %zu bytes of shared memory for the neighbour kernel", kNbrSmem);
+  }
+  // persistent grids: every SM filled to the kernel's occupancy limit
+  auto occ = [&](const void *fn, size_t smem = 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, smem) != cudaSuccess || n < 1) n = 2;
+    return nsm * n;
+  };
+  b->grid_step = occ((const void *)k_bstep);
+  b->grid_clu = occ((const void *)k_bforce);
+  b->grid_nbr = occ((const void *)k_bnbr, kNbrSmem);
+  b->grid_est = 2 * nsm;
   auto fail_free = [&](pimd_status st) {
     pimd_batch_destroy(b);
     return st;
@@ -1059,6 +1265,7 @@ extern "C" void pimd_batch_destroy(pimd_batch *b) {
   dev_free(b->alloc, b->d_nbr, b->stream);
   dev_free(b->alloc, b->d_est, b->stream);
   dev_free(b->alloc, b->stg_x, b->stream);
+  for (auto p : b->ptab) dev_free(b->alloc, p, b->stream);
   if (b->h_eout) cudaFreeHost(b->h_eout);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -1074,6 +1281,8 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   if (st != PIMD_OK) return st;
   if (sys->potential != PIMD_POT_WATERLIKE)
     return fail(PIMD_EINVAL, "the batch engine runs water-like systems");
+  if (sys->n_atoms / 3 > kBatchMaxMol)
+    return fail(PIMD_EINVAL, "batch replicas hold at most %d molecules", kBatchMaxMol);
   if (nsteps < 0) return fail(PIMD_EINVAL, "nsteps must be >= 0");
   // no batch kernel may be in flight while a new descriptor goes live
   BK(cudaStreamSynchronize(b->stream));
@@ -1140,6 +1349,19 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
     sigv[i] = std::sqrt(P * kBoltzmann * T / mm);
   }
   std::vector<float> Mf(tb.M.begin(), tb.M.end()), Mtf(tb.Mt.begin(), tb.Mt.end());
+  if (!b->ptab[P]) {
+    float *t = (float *)dev_alloc(b->alloc, 2 * (size_t)P * P * sizeof(float), b->stream);
+    if (!t) return cleanup(fail(PIMD_ENOMEM, "mode-table allocation failed"));
+    if (cudaMemcpy(t, Mf.data(), Mf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t + (size_t)P * P, Mtf.data(), Mtf.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      dev_free(b->alloc, t, b->stream);
+      return cleanup(fail(PIMD_ECUDA, "mode-table upload failed"));
+    }
+    b->ptab[P] = t;
+  }
+  d.Mf = b->ptab[P];
+  d.Mtf = b->ptab[P] + (size_t)P * P;
   std::vector<float> cAf(tb.cA.begin(), tb.cA.end()), sAf(tb.sA.begin(), tb.sA.end());
   std::vector<float> wsAf(tb.wsA.begin(), tb.wsA.end()), c1f(tb.c1.begin(), tb.c1.end());
   std::vector<float> c2f(tb.c2.begin(), tb.c2.end());
@@ -1155,8 +1377,6 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
       {(void *)d.inv_mm, inv_mm.data(), N * sizeof(double)},
       {(void *)d.sigv, sigv.data(), N * sizeof(double)},
       {(void *)d.mass_mm, mass_mm.data(), N * sizeof(double)},
-      {(void *)d.Mf, Mf.data(), Mf.size() * sizeof(float)},
-      {(void *)d.Mtf, Mtf.data(), Mtf.size() * sizeof(float)},
       {(void *)d.cAf, cAf.data(), P * sizeof(float)},
       {(void *)d.sAf, sAf.data(), P * sizeof(float)},
       {(void *)d.wsAf, wsAf.data(), P * sizeof(float)},
@@ -1196,10 +1416,10 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   }
   // initial neighbour list and forces of this replica only
   if (e == cudaSuccess) {
-    k_bnbr<<<std::max(1, (int)r.items_nbr.size()), 128, 0, b->stream>>>(b->d_reps, r.d_items_nbr,
+    k_bnbr<<<std::max(1, (int)r.items_nbr.size()), 128, kNbrSmem, b->stream>>>(b->d_reps, r.d_items_nbr,
                                                                         r.d_counts + 2, 1);
-    k_bforce<<<4 * std::max(1, (int)std::min<size_t>(r.items_clu.size(), b->grid_clu)), 128, 0, b->stream>>>(
-        b->d_reps, r.d_items_clu, r.d_counts + 1, 1);
+    k_bforce<<<std::max(1, (int)std::min<size_t>((r.items_clu.size() + 3) / 4, b->grid_clu)), 128, 0,
+               b->stream>>>(b->d_reps, r.d_items_clu, r.d_counts + 1, 1);
     b->launches += 2;
     e = cudaGetLastError();
   }
@@ -1253,7 +1473,7 @@ extern "C" pimd_status pimd_batch_run(pimd_batch *b, int64_t nsteps) {
   }
   const int cg = (b->capacity + 127) / 128;
   k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1);
-  k_bclose<<<b->grid_step, 256, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+  k_bclose<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
   k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2);
   b->launches += 3;
   BK(cudaGetLastError());
@@ -1266,9 +1486,7 @@ extern "C" pimd_status pimd_batch_sync(pimd_batch *b) {
   return PIMD_OK;
 }
 
-// Per-slot step counter and steps left (-1 for empty slots); arrays of
-// max_replicas entries, either may be NULL.  Synchronises.
-extern "C" pimd_status pimd_batch_status(pimd_batch *b, int64_t *step, int64_t *steps_left) {
+extern "C" pimd_status pimd_batch_status(pimd_batch *b, int64_t *step, int64_t *steps_left, int64_t *rebuilds) {
   if (!b) return fail(PIMD_EINVAL, "batch is NULL");
   pimd_status st;
   if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
@@ -1281,6 +1499,7 @@ extern "C" pimd_status pimd_batch_status(pimd_batch *b, int64_t *step, int64_t *
     const long long *c = b->h_ctl + (size_t)s * kCtlWords;
     if (step) step[s] = b->reps[s].live ? c[kCtlStep] : -1;
     if (steps_left) steps_left[s] = b->reps[s].live ? c[kCtlLeft] : -1;
+    if (rebuilds) rebuilds[s] = b->reps[s].live ? c[kCtlRebuilds] : -1;
     if (b->reps[s].live && (c[kCtlWords - 1] & kErrNbrOverflow))
       return fail(PIMD_EOVERFLOW, "replica %d: neighbour list overflow", s);
   }
@@ -1297,7 +1516,7 @@ extern "C" pimd_status pimd_batch_estimators(pimd_batch *b, pimd_estimates *out)
     b->launches += 2;
     BK(cudaGetLastError());
   }
-  if ((st = pimd_batch_status(b, nullptr, nullptr)) != PIMD_OK) return st;
+  if ((st = pimd_batch_status(b, nullptr, nullptr, nullptr)) != PIMD_OK) return st;
   BK(cudaMemcpyAsync(b->h_eout, b->d_eout, sizeof(double) * kOutStride * b->capacity, cudaMemcpyDeviceToHost,
                      b->stream));
   BK(cudaStreamSynchronize(b->stream));
@@ -1342,6 +1561,39 @@ extern "C" pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double 
 }
 
 extern "C" int64_t pimd_batch_kernel_launches(const pimd_batch *b) { return b ? b->launches : -1; }
+
+// nsteps steps launched one kernel at a time with CUDA events around each of
+// the four kernels of a step; ms[4] receives the summed device milliseconds
+// of control, step, neighbour and force kernels.  The steps are real steps.
+extern "C" pimd_status pimd_batch_time_kernels(pimd_batch *b, int32_t nsteps, double *ms) {
+  if (!b || !ms || nsteps < 1) return fail(PIMD_EINVAL, "invalid argument");
+  pimd_status st;
+  if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
+  cudaEvent_t ev[5];
+  for (auto &e : ev) BK(cudaEventCreate(&e));
+  double acc[4] = {0, 0, 0, 0};
+  for (int s = 0; s < nsteps; ++s) {
+    cudaEventRecord(ev[0], b->stream);
+    k_bctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, 0);
+    cudaEventRecord(ev[1], b->stream);
+    k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+    cudaEventRecord(ev[2], b->stream);
+    k_bnbr<<<b->grid_nbr, 128, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, 0);
+    cudaEventRecord(ev[3], b->stream);
+    k_bforce<<<b->grid_clu, 128, 0, b->stream>>>(b->d_reps, b->d_clu, b->d_counts + 1, 0);
+    cudaEventRecord(ev[4], b->stream);
+    BK(cudaEventSynchronize(ev[4]));
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.f;
+      BK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      acc[k] += t;
+    }
+    b->launches += 4;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  for (int k = 0; k < 4; ++k) ms[k] = acc[k];
+  return pimd_batch_run(b, 0) == PIMD_OK ? PIMD_OK : fail(PIMD_ECUDA, "timing close failed");
+}
 
 // Autotuner of the step-kernel tile: for each bead count present, try tiles
 // A = Amax, Amax/2, ..., 1 (A atoms x 3 components x P modes per block) while
@@ -1401,7 +1653,7 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
   if (st == PIMD_OK) {
     const int cg = (b->capacity + 127) / 128;
     k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1);
-    k_bclose<<<b->grid_step, 256, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+    k_bclose<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
     k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2);
     b->launches += 3;
     if (cudaGetLastError() != cudaSuccess) st = fail(PIMD_ECUDA, "autotune close failed");
@@ -1518,7 +1770,7 @@ void server_loop(pimd_server *s) {
     lk.unlock();
     const double t_run = now_s(s);
     pimd_status st = pimd_batch_run(s->batch, s->chunk);
-    if (st == PIMD_OK) st = pimd_batch_status(s->batch, s->st_step.data(), s->st_left.data());
+    if (st == PIMD_OK) st = pimd_batch_status(s->batch, s->st_step.data(), s->st_left.data(), nullptr);
     bool any_done = false;
     if (st == PIMD_OK)
       for (int k = 0; k < (int)s->st_left.size(); ++k) any_done |= (s->st_left[k] == 0);
