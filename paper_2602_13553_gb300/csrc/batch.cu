@@ -48,6 +48,9 @@ cudaError_t launch_centroids(const NbrArgs &a, double *ccur, cudaStream_t s);
 int water_lane_groups(int P);
 
 constexpr int kTileMax = 3 * 512;   // largest A * 3 * P of a step tile (A P <= 512)
+constexpr int kMmaRowsMax = 192;    // padded rows 8 NT of the tensor-core path (A P <= 512)
+constexpr int kMmaTile = 2304;      // max padded rows x (P + 4) over P % 8 == 0
+constexpr int kStepSmem = 3 * kMmaTile;   // floats; >= 4 * kTileMax
 constexpr int kBatchMaxMol = 4096;   // molecules per replica (centroids staged in shared memory)
 constexpr int kNbrMolPerItem = 32;   // molecules per neighbour-list work item
 constexpr size_t kNbrSmem = 3 * kBatchMaxMol * sizeof(float);
@@ -59,14 +62,19 @@ struct RepDesc {
   int nstep_items, ne, pad0, pad1;
   uint64_t seed;
   double dt, tA, c1_0, c2_0, kT, volume, wn2;
+  double dr0;                 // tA / sqrt(P): centroid drift per unit v~_0
   double box[3], invbox[3];
   double kb, r0, kth, th0, eps, sig, rc, rlist, skin;
   long long *ctl;
   double *xc, *v0;
   float *d, *vk, *F, *xcw;
   const double *inv_mm, *sigv, *mass_mm;
+  const float *inv_mmf, *sigvf;   // FP32 copies for the FP32 mode updates
   const float *Mf, *Mtf, *cAf, *sAf, *wsAf, *c1f, *c2f;
   const double *Mt64, *lam;
+  // tensor-core path (P % 8 == 0): M (forward) and M^T (inverse) as TF32
+  // hi/lo halves in m16n8k8 A-fragment order [mode tile][k step][lane][4]
+  const float4 *mfa_hi, *mfa_lo, *mia_hi, *mia_lo;
   double *cref, *ccur, *blkmax;
   int *nbr, *nbr_off;
   double *Upart, *Wpart, *epart;
@@ -145,17 +153,113 @@ __device__ __forceinline__ void gauss3f_b(uint64_t seed, uint32_t atom, uint32_t
   e2 = r1 * cospif(2.0f * (((float)(w.w >> 8) + 0.5f) * s));
 }
 
-// Register-blocked inner part of the batched step for P divisible by 4:
-// thread task (atom al, mode group g) forms F~ and q~ of modes 4g..4g+3 for
-// all three components -- one float4 of M^T feeds 24 FMAs -- then updates
-// those modes with one Philox draw per (atom, mode); mode 0 goes to the FP64
-// centroid update in place.  The inverse runs per (atom, bead group).
-__device__ __forceinline__ void bstep_blocked(const RepDesc *__restrict__ Rp, int P, int tile0, int na,
-                                              size_t base, float *sD, float *sV, float *sF, float *sQ,
-                                              uint64_t step, int first) {
+// ---- tensor-core mode transforms (P % 8 == 0) -------------------------------
+// The forward transforms F~ = M F and q~ = M d and the inverse d' = M^T q~' of
+// a tile are GEMMs with K = P: A = the P x P matrix (rows padded to 16),
+// B = the tile's rows (one column per atom-component row, padded to 8).
+// mma.sync m16n8k8 in TF32 with the 3xTF32 split (a = a_hi + a_lo in TF32;
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) keeps FP32-level accuracy.
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kMmaPairsMax = 6;   // (mode tile, row tile) pairs per warp
+
+// acc[p][0..3] = (A B1) tile, acc[p][4..7] = (A B2) tile for the warp's pairs
+// p = warp, warp + 4, ...; B1, B2 are [row][k] arrays with row stride PS.
+__device__ __forceinline__ void mma_gemm2(const float4 *__restrict__ ahi, const float4 *__restrict__ alo, int KS,
+                                          int MT, int NT, const float *B1, const float *B2, int PS,
+                                          float (&acc)[kMmaPairsMax][8]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int p = 0; p < kMmaPairsMax; ++p) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[p][q] = 0.f;
+    const int pair = warp + 4 * p;
+    if (pair >= MT * NT) continue;
+    const int mt = pair / NT, nt = pair - mt * NT;
+    const float *b1 = B1 + (8 * nt + g) * PS + t;
+    const float *b2 = B2 ? B2 + (8 * nt + g) * PS + t : nullptr;
+    for (int ks = 0; ks < KS; ++ks) {
+      const float4 h = __ldg(ahi + ((size_t)mt * KS + ks) * 32 + lane);
+      const float4 l = __ldg(alo + ((size_t)mt * KS + ks) * 32 + lane);
+      const uint32_t ah[4] = {__float_as_uint(h.x), __float_as_uint(h.y), __float_as_uint(h.z), __float_as_uint(h.w)};
+      const uint32_t al[4] = {__float_as_uint(l.x), __float_as_uint(l.y), __float_as_uint(l.z), __float_as_uint(l.w)};
+      {
+        const float x0 = b1[8 * ks], x1 = b1[8 * ks + 4];
+        const uint32_t h0 = tf32_rna(x0), h1 = tf32_rna(x1);
+        const uint32_t l0 = tf32_rna(x0 - __uint_as_float(h0)), l1 = tf32_rna(x1 - __uint_as_float(h1));
+        float (&c)[4] = *reinterpret_cast<float(*)[4]>(&acc[p][0]);
+        mma_tf32(c, al, h0, h1);
+        mma_tf32(c, ah, l0, l1);
+        mma_tf32(c, ah, h0, h1);
+      }
+      if (b2) {
+        const float x0 = b2[8 * ks], x1 = b2[8 * ks + 4];
+        const uint32_t h0 = tf32_rna(x0), h1 = tf32_rna(x1);
+        const uint32_t l0 = tf32_rna(x0 - __uint_as_float(h0)), l1 = tf32_rna(x1 - __uint_as_float(h1));
+        float (&c)[4] = *reinterpret_cast<float(*)[4]>(&acc[p][4]);
+        mma_tf32(c, al, h0, h1);
+        mma_tf32(c, ah, l0, l1);
+        mma_tf32(c, ah, h0, h1);
+      }
+    }
+  }
+}
+
+// Writes a GEMM result tile pair back as [row][col] with row stride PS:
+// D[col = 16 mt + g (+8)][row = 8 nt + 2 t (+1)] from the C fragment.
+__device__ __forceinline__ void mma_store(const float (&acc)[kMmaPairsMax][8], int half, int MT, int NT, int P,
+                                          int rows, float *dst, int PS) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int p = 0; p < kMmaPairsMax; ++p) {
+    const int pair = warp + 4 * p;
+    if (pair >= MT * NT) continue;
+    const int mt = pair / NT, nt = pair - mt * NT;
+    const int c0 = 16 * mt + g, r0 = 8 * nt + 2 * t;
+    const float *c = &acc[p][4 * half];
+    if (c0 < P) {
+      if (r0 < rows) dst[r0 * PS + c0] = c[0];
+      if (r0 + 1 < rows) dst[(r0 + 1) * PS + c0] = c[1];
+    }
+    if (c0 + 8 < P) {
+      if (r0 < rows) dst[r0 * PS + c0 + 8] = c[2];
+      if (r0 + 1 < rows) dst[(r0 + 1) * PS + c0 + 8] = c[3];
+    }
+  }
+}
+
+// The batched step of one tile on tensor cores.  sF, sX, sV: [row][P] tiles
+// with row stride PS = P + 4 (bank-conflict-free B fragments).
+__device__ __forceinline__ void bstep_mma(const RepDesc *__restrict__ Rp, int P, int tile0, int na, size_t base,
+                                          float *sF, float *sX, float *sV, uint64_t step, int first) {
+  const int PS = P + 4;
+  const int rows = na * 3;
+  const int NT = (rows + 7) >> 3;
+  const int MT = (P + 15) >> 4;
+  const int KS = P >> 3;
+  float acc[kMmaPairsMax][8];
+  mma_gemm2(Rp->mfa_hi, Rp->mfa_lo, KS, MT, NT, sF, sX, PS, acc);
+  __syncthreads();
+  mma_store(acc, 0, MT, NT, P, rows, sF, PS);   // F~ [row][mode]
+  mma_store(acc, 1, MT, NT, P, rows, sX, PS);   // q~ [row][mode]
+  __syncthreads();
+  // per-mode update: thread (atom al, modes 4 g4 .. 4 g4 + 3), all components
   const int NG = P >> 2;
-  const float4 *__restrict__ Mt4 = reinterpret_cast<const float4 *>(Rp->Mtf);
-  const float4 *__restrict__ M4 = reinterpret_cast<const float4 *>(Rp->Mf);
   const float *__restrict__ cAf = Rp->cAf;
   const float *__restrict__ sAf = Rp->sAf;
   const float *__restrict__ wsAf = Rp->wsAf;
@@ -172,72 +276,17 @@ __device__ __forceinline__ void bstep_blocked(const RepDesc *__restrict__ Rp, in
   const double dt = Rp->dt;
   const float hd = (float)dt, half = 0.5f * hd;
   const float kick = first ? half : hd;
+  const float *__restrict__ inv_mmf = Rp->inv_mmf;
+  const float *__restrict__ sigvf = Rp->sigvf;
   for (int task = threadIdx.x; task < na * NG; task += blockDim.x) {
-    const int al = task / NG, g = task - al * NG;
+    const int al = task / NG, g4 = task - al * NG;
     const int i = tile0 + al;
-    const float *fr = sF + al * 3 * P;
-    const float *xr = sD + al * 3 * P;
-    float f[3][4], q[3][4];
+    const float im = __ldg(inv_mmf + i);
+    const float sg = __ldg(sigvf + i);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) f[c][t] = q[c][t] = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < P; ++j) {
-      const float4 m = __ldg(Mt4 + j * NG + g);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float fj = fr[c * P + j], xj = xr[c * P + j];
-        f[c][0] = fmaf(m.x, fj, f[c][0]);
-        f[c][1] = fmaf(m.y, fj, f[c][1]);
-        f[c][2] = fmaf(m.z, fj, f[c][2]);
-        f[c][3] = fmaf(m.w, fj, f[c][3]);
-        q[c][0] = fmaf(m.x, xj, q[c][0]);
-        q[c][1] = fmaf(m.y, xj, q[c][1]);
-        q[c][2] = fmaf(m.z, xj, q[c][2]);
-        q[c][3] = fmaf(m.w, xj, q[c][3]);
-      }
-    }
-    const float im = (float)__ldg(inv_mm + i);
-    const float sg = (float)__ldg(sigv + i);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int k = 4 * g + t;
-      if (k == 0) {
-        // centroid, FP64: q~_0 = sqrt(P) xc
-        const double dr = Rp->tA * rsqrt((double)P);
-        const double imd = __ldg(inv_mm + i), c2s = Rp->c2_0 * __ldg(sigv + i);
-        float e[3] = {0.f, 0.f, 0.f}, e2[3] = {0.f, 0.f, 0.f};
-        if (thermo) gauss3f_b(seed, (uint32_t)i, 0u, kStreamO1, step, e[0], e[1], e[2]);
-        if (thermo && integ == 1 && !first)
-          gauss3f_b(seed, (uint32_t)i, 0u, kStreamO2, step - 1, e2[0], e2[1], e2[2]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const size_t ic = (size_t)i * 3 + c;
-          double x = xcg[ic], v = v0g[ic];
-          const double f0 = (double)f[c][0];
-          if (integ == 0) {
-            v = fma((first ? 0.5 : 1.0) * dt * imd, f0, v);
-            x = fma(dr, v, x);
-            if (thermo) v = fma(Rp->c1_0, v, c2s * (double)e[c]);
-            x = fma(dr, v, x);
-          } else {
-            const double kb = 0.5 * dt * imd;
-            if (!first) {
-              v = fma(kb, f0, v);
-              if (thermo) v = fma(Rp->c1_0, v, c2s * (double)e2[c]);
-            }
-            if (thermo) v = fma(Rp->c1_0, v, c2s * (double)e[c]);
-            v = fma(kb, f0, v);
-            x = fma(dr, v, x);
-          }
-          xcg[ic] = x;
-          v0g[ic] = v;
-          xcw[ic] = wrapb(x, Rp->box[c], Rp->invbox[c]);
-          sQ[(al * 3 + c) * P] = 0.f;
-        }
-        continue;
-      }
+    for (int tt = 0; tt < 4; ++tt) {
+      const int k = 4 * g4 + tt;
+      if (k == 0) continue;   // the centroid mode: packed FP64 phase below
       const float cA = __ldg(cAf + k), sA = __ldg(sAf + k), wsA = __ldg(wsAf + k);
       const float c1 = __ldg(c1f + k), c2s = __ldg(c2f + k) * sg;
       float e[3] = {0.f, 0.f, 0.f}, e2[3] = {0.f, 0.f, 0.f};
@@ -246,10 +295,10 @@ __device__ __forceinline__ void bstep_blocked(const RepDesc *__restrict__ Rp, in
         gauss3f_b(seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, e2[0], e2[1], e2[2]);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const int sidx = (al * 3 + c) * P + k;
+        const int sidx = (al * 3 + c) * PS + k;
         float v = sV[sidx];
-        float qq = q[c][t];
-        const float ff = f[c][t];
+        float qq = sX[sidx];
+        const float ff = sF[sidx];
         if (integ == 0) {
           v = fmaf(kick * im, ff, v);
           rotb(qq, v, cA, sA, wsA);
@@ -265,43 +314,62 @@ __device__ __forceinline__ void bstep_blocked(const RepDesc *__restrict__ Rp, in
           v = fmaf(kb, ff, v);
           rotb(qq, v, cA, sA, wsA);
         }
-        sQ[sidx] = qq;
-        vkg[base + sidx] = v;
+        sX[sidx] = qq;
+        vkg[base + (size_t)(al * 3 + c) * P + k] = v;
       }
+    }
+  }
+  // centroid mode, FP64, one (atom, component) per lane: q~_0 = sqrt(P) xc
+  {
+    const double dr = Rp->dr0, c1_0 = Rp->c1_0;
+    const double kfac = (integ == 0 ? (first ? 0.5 : 1.0) : 0.5) * dt;
+    for (int t = threadIdx.x; t < na * 3; t += blockDim.x) {
+      const int al = t / 3, c = t - 3 * al;
+      const int i = tile0 + al;
+      const size_t ic = (size_t)i * 3 + c;
+      // one Philox draw serves the three components; components are lanes here
+      float e = 0.f, e2 = 0.f;
+      if (thermo) {
+        float a0, a1, a2;
+        gauss3f_b(seed, (uint32_t)i, 0u, kStreamO1, step, a0, a1, a2);
+        e = c == 0 ? a0 : (c == 1 ? a1 : a2);
+        if (integ == 1 && !first) {
+          gauss3f_b(seed, (uint32_t)i, 0u, kStreamO2, step - 1, a0, a1, a2);
+          e2 = c == 0 ? a0 : (c == 1 ? a1 : a2);
+        }
+      }
+      const double kb = kfac * __ldg(inv_mm + i);
+      const double c2s = Rp->c2_0 * __ldg(sigv + i);
+      const double f0 = (double)sF[t * PS];
+      double x = xcg[ic], v = v0g[ic];
+      if (integ == 0) {
+        v = fma(kb, f0, v);
+        x = fma(dr, v, x);
+        if (thermo) v = fma(c1_0, v, c2s * (double)e);
+        x = fma(dr, v, x);
+      } else {
+        if (!first) {
+          v = fma(kb, f0, v);
+          if (thermo) v = fma(c1_0, v, c2s * (double)e2);
+        }
+        if (thermo) v = fma(c1_0, v, c2s * (double)e);
+        v = fma(kb, f0, v);
+        x = fma(dr, v, x);
+      }
+      xcg[ic] = x;
+      v0g[ic] = v;
+      xcw[ic] = wrapb(x, Rp->box[c], Rp->invbox[c]);
+      sX[t * PS] = 0.f;   // the deviations carry no centroid mode
     }
   }
   __syncthreads();
-  float *__restrict__ dg = Rp->d;
-  for (int task = threadIdx.x; task < na * NG; task += blockDim.x) {
-    const int al = task / NG, g = task - al * NG;
-    const float *qr = sQ + al * 3 * P;
-    float x[3][4];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) x[c][t] = 0.f;
-#pragma unroll 4
-    for (int k = 1; k < P; ++k) {
-      const float4 m = __ldg(M4 + k * NG + g);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float qk = qr[c * P + k];
-        x[c][0] = fmaf(m.x, qk, x[c][0]);
-        x[c][1] = fmaf(m.y, qk, x[c][1]);
-        x[c][2] = fmaf(m.z, qk, x[c][2]);
-        x[c][3] = fmaf(m.w, qk, x[c][3]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const int o = (al * 3 + c) * P + 4 * g;
-      *reinterpret_cast<float4 *>(dg + base + o) = make_float4(x[c][0], x[c][1], x[c][2], x[c][3]);
-      sD[o] = x[c][0];
-      sD[o + 1] = x[c][1];
-      sD[o + 2] = x[c][2];
-      sD[o + 3] = x[c][3];
-    }
-  }
+  // inverse: d' = M^T q~' (mode 0 zeroed above)
+  mma_gemm2(Rp->mia_hi, Rp->mia_lo, KS, MT, NT, sX, nullptr, PS, acc);
+  mma_store(acc, 0, MT, NT, P, rows, sF, PS);   // new deviations [row][bead] into sF
+  __syncthreads();
+  float *__restrict__ dg = Rp->d + base;
+  for (int r = threadIdx.x >> 5; r < rows; r += blockDim.x >> 5)
+    for (int j = threadIdx.x & 31; j < P; j += 32) dg[r * P + j] = sF[r * PS + j];
 }
 
 // The split-precision fused step (same arithmetic as the single-system split
@@ -310,7 +378,8 @@ __device__ __forceinline__ void bstep_blocked(const RepDesc *__restrict__ Rp, in
 // split (mode, row) uses shifts when P is a power of two.
 __global__ void __launch_bounds__(128, 4) k_bstep(const RepDesc *__restrict__ reps, const int2 *__restrict__ items,
                                                const int *__restrict__ count) {
-  __shared__ float sD[kTileMax], sV[kTileMax], sF[kTileMax], sQ[kTileMax];
+  __shared__ __align__(16) float sbuf[kStepSmem];
+  float *sD = sbuf, *sV = sbuf + kTileMax, *sF = sbuf + 2 * kTileMax, *sQ = sbuf + 3 * kTileMax;
   __shared__ double sred[2][4];
   const int n = *count;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
@@ -318,6 +387,69 @@ __global__ void __launch_bounds__(128, 4) k_bstep(const RepDesc *__restrict__ re
     const RepDesc *__restrict__ Rp = reps + w.x;
     long long *__restrict__ ctl = Rp->ctl;
     if (!ctl[kCtlActive]) continue;
+    if ((Rp->P & 7) == 0) {
+      // tensor-core path: tiles with padded rows in sF (forces), sX
+      // (deviations), sV (velocities)
+      const int P = Rp->P, A = Rp->A, N = Rp->N, PS = P + 4;
+      const int tile0 = w.y * A;
+      const int na = min(A, N - tile0);
+      const int len = na * 3 * P;
+      const size_t base = (size_t)tile0 * 3 * P;
+      float *mF = sbuf, *mX = sbuf + kMmaTile, *mV = sbuf + 2 * kMmaTile;
+      {
+        // rows over warps, beads over lanes (coalesced, no division)
+        const float *__restrict__ gF = Rp->F + base;
+        const float *__restrict__ gX = Rp->d + base;
+        const float *__restrict__ gV = Rp->vk + base;
+        const int rows = na * 3;
+        for (int r = threadIdx.x >> 5; r < rows; r += blockDim.x >> 5)
+          for (int j = threadIdx.x & 31; j < P; j += 32) {
+            mF[r * PS + j] = __ldg(gF + r * P + j);
+            mX[r * PS + j] = __ldg(gX + r * P + j);
+            mV[r * PS + j] = __ldg(gV + r * P + j);
+          }
+      }
+      __syncthreads();
+      bstep_mma(Rp, P, tile0, na, base, mF, mX, mV, (uint64_t)ctl[kCtlStep], (int)ctl[kCtlFirst]);
+      // skin check on the new deviations (mF) and the new centroids
+      double vdisp = 0.0;
+      float vdevf = 0.f;
+      // oxygens only: atoms i = 3 m of the tile, warps over atoms, lanes over beads
+      for (int al = (3 - tile0 % 3) % 3 + (threadIdx.x >> 5) * 3; al < na; al += 3 * (blockDim.x >> 5))
+        for (int k = threadIdx.x & 31; k < P; k += 32) {
+        const int i = tile0 + al;
+        const float *ds = mF + al * 3 * PS;
+        const float e0 = ds[k], e1 = ds[PS + k], e2 = ds[2 * PS + k];
+        vdevf = fmaxf(vdevf, e0 * e0 + e1 * e1 + e2 * e2);
+        if (k == 0) {
+          const int m = i / 3;
+          const double c0 = Rp->xc[3 * (size_t)i], c1 = Rp->xc[3 * (size_t)i + 1], c2 = Rp->xc[3 * (size_t)i + 2];
+          const double g0 = c0 - Rp->cref[3 * m], g1 = c1 - Rp->cref[3 * m + 1], g2 = c2 - Rp->cref[3 * m + 2];
+          vdisp = fmax(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
+          Rp->ccur[3 * m] = c0;
+          Rp->ccur[3 * m + 1] = c1;
+          Rp->ccur[3 * m + 2] = c2;
+        }
+      }
+      float vdispf = (float)vdisp;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        vdispf = fmaxf(vdispf, __shfl_down_sync(0xffffffffu, vdispf, o));
+        vdevf = fmaxf(vdevf, __shfl_down_sync(0xffffffffu, vdevf, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        sred[0][threadIdx.x >> 5] = vdispf;
+        sred[1][threadIdx.x >> 5] = vdevf;
+      }
+      __syncthreads();
+      if (threadIdx.x < 2) {
+        double mx = 0.0;
+        for (int ww = 0; ww < (int)((blockDim.x + 31) / 32); ++ww) mx = fmax(mx, sred[threadIdx.x][ww]);
+        Rp->blkmax[2 * w.y + threadIdx.x] = (mx == mx) ? sqrt(mx) * (1.0 + 1e-6) + 1e-4 : 1e300;
+      }
+      __syncthreads();
+      continue;
+    }
     const int P = Rp->P, A = Rp->A, N = Rp->N, integ = Rp->integrator, thermo = Rp->thermo;
     const int lg = (P & (P - 1)) == 0 ? __ffs(P) - 1 : -1;
     const uint64_t seed = Rp->seed;
@@ -351,9 +483,7 @@ __global__ void __launch_bounds__(128, 4) k_bstep(const RepDesc *__restrict__ re
     const int first = (int)ctl[kCtlFirst];
     const float hd = (float)dt, half = 0.5f * hd;
     const float kick = first ? half : hd;
-    if ((P & 3) == 0) {
-      bstep_blocked(Rp, P, tile0, na, base, sD, sV, sF, sQ, step, first);
-    } else {
+    {
     for (int task = threadIdx.x; task < len; task += blockDim.x) {
       const int k = lg >= 0 ? (task & (P - 1)) : task % P;
       const int r = lg >= 0 ? (task >> lg) : task / P;
@@ -958,6 +1088,8 @@ size_t layout_replica(Replica &r, char *base) {
   d.inv_mm = carve_ptr<double>(base, off, N);
   d.sigv = carve_ptr<double>(base, off, N);
   d.mass_mm = carve_ptr<double>(base, off, N);
+  d.inv_mmf = carve_ptr<float>(base, off, N);
+  d.sigvf = carve_ptr<float>(base, off, N);
   d.cAf = carve_ptr<float>(base, off, P);
   d.sAf = carve_ptr<float>(base, off, P);
   d.wsAf = carve_ptr<float>(base, off, P);
@@ -980,9 +1112,9 @@ size_t layout_replica(Replica &r, char *base) {
   return off + 256;
 }
 
-// step tile (atoms per item): A P <= 512 for the register-blocked path (P a
-// multiple of 4), A 3 P <= 256 otherwise
-int default_tile(int P) { return (P % 4 == 0) ? std::max(1, 512 / P) : std::max(1, 256 / (3 * P)); }
+// step tile (atoms per item): A P <= 512 for the tensor-core path (P a
+// multiple of 8), A 3 P <= 256 otherwise
+int default_tile(int P) { return (P % 8 == 0) ? std::max(1, 512 / P) : std::max(1, 256 / (3 * P)); }
 
 }  // namespace
 }  // namespace pimd
@@ -1013,6 +1145,9 @@ struct pimd_batch {
   // one FP32 copy of M and M^T per bead count, shared by all replicas with
   // that P (the normal-mode matrix depends on P only): small, L1-resident
   float *ptab[PIMD_MAX_BEADS + 1] = {nullptr};
+  // tensor-core fragment tables per bead count (P % 8 == 0): forward hi, lo,
+  // inverse hi, lo, each [mode tile][k step][lane] float4
+  float4 *mtab[PIMD_MAX_BEADS + 1] = {nullptr};
   std::vector<int2> h_step, h_nbr, h_est;
   std::vector<int4> h_clu;
   int h_counts[4] = {0, 0, 0, 0};
@@ -1158,6 +1293,43 @@ pimd_status ensure_staging(pimd_batch *b, size_t len) {
   return PIMD_OK;
 }
 
+// TF32 rounding as cvt.rna (to nearest, ties away from zero): 10 mantissa bits.
+float tf32_round(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x1000u;
+    u &= 0xffffe000u;
+  }
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+// m16n8k8 A fragments of a P x P matrix A (row-major, rows padded to 16 with
+// zeros) as [mode tile mt][k step ks][lane] float4 = (a0, a1, a2, a3):
+// a0 = A[16 mt + g][8 ks + t], a1 = A[16 mt + g + 8][8 ks + t],
+// a2 = A[16 mt + g][8 ks + t + 4], a3 = A[16 mt + g + 8][8 ks + t + 4],
+// g = lane / 4, t = lane % 4; hi = tf32(a), lo = tf32(a - hi).
+void fragment_tables(const std::vector<double> &A, int P, std::vector<float> &hi, std::vector<float> &lo) {
+  const int MT = (P + 15) / 16, KS = P / 8;
+  hi.assign((size_t)MT * KS * 32 * 4, 0.f);
+  lo.assign(hi.size(), 0.f);
+  auto at = [&](int r, int c) -> float { return r < P ? (float)A[(size_t)r * P + c] : 0.f; };
+  for (int mt = 0; mt < MT; ++mt)
+    for (int ks = 0; ks < KS; ++ks)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane / 4, t = lane % 4;
+        const float v[4] = {at(16 * mt + g, 8 * ks + t), at(16 * mt + g + 8, 8 * ks + t),
+                            at(16 * mt + g, 8 * ks + t + 4), at(16 * mt + g + 8, 8 * ks + t + 4)};
+        for (int q = 0; q < 4; ++q) {
+          const size_t o = (((size_t)mt * KS + ks) * 32 + lane) * 4 + q;
+          hi[o] = tf32_round(v[q]);
+          lo[o] = tf32_round(v[q] - hi[o]);
+        }
+      }
+}
+
 SplitStepArgs replica_split_args(const Replica &r) {
   SplitStepArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -1266,6 +1438,7 @@ extern "C" void pimd_batch_destroy(pimd_batch *b) {
   dev_free(b->alloc, b->d_est, b->stream);
   dev_free(b->alloc, b->stg_x, b->stream);
   for (auto p : b->ptab) dev_free(b->alloc, p, b->stream);
+  for (auto p : b->mtab) dev_free(b->alloc, p, b->stream);
   if (b->h_eout) cudaFreeHost(b->h_eout);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -1316,6 +1489,7 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   d.seed = prm.seed;
   d.dt = dt;
   d.tA = tb.tA;
+  d.dr0 = tb.tA / std::sqrt((double)P);
   d.c1_0 = tb.c1[0];
   d.c2_0 = tb.c2[0];
   d.kT = kBoltzmann * T;
@@ -1342,11 +1516,14 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   // tables and per-atom constants
   const int N = r.N;
   std::vector<double> inv_mm(N), sigv(N), mass_mm(N);
+  std::vector<float> inv_mmf(N), sigvf(N);
   for (int i = 0; i < N; ++i) {
     const double mm = sys->mass[i] * kMvv2e;
     mass_mm[i] = mm;
     inv_mm[i] = 1.0 / mm;
     sigv[i] = std::sqrt(P * kBoltzmann * T / mm);
+    inv_mmf[i] = (float)inv_mm[i];
+    sigvf[i] = (float)sigv[i];
   }
   std::vector<float> Mf(tb.M.begin(), tb.M.end()), Mtf(tb.Mt.begin(), tb.Mt.end());
   if (!b->ptab[P]) {
@@ -1362,6 +1539,29 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   }
   d.Mf = b->ptab[P];
   d.Mtf = b->ptab[P] + (size_t)P * P;
+  d.mfa_hi = d.mfa_lo = d.mia_hi = d.mia_lo = nullptr;
+  if (P % 8 == 0) {
+    const size_t one = (size_t)((P + 15) / 16) * (P / 8) * 32;   // float4 per table
+    if (!b->mtab[P]) {
+      std::vector<float> fh, fl, ih, il;
+      fragment_tables(tb.M, P, fh, fl);
+      fragment_tables(tb.Mt, P, ih, il);
+      float4 *t = (float4 *)dev_alloc(b->alloc, 4 * one * sizeof(float4), b->stream);
+      if (!t) return cleanup(fail(PIMD_ENOMEM, "mode-table allocation failed"));
+      const std::vector<float> *parts[4] = {&fh, &fl, &ih, &il};
+      for (int q = 0; q < 4; ++q)
+        if (cudaMemcpy(t + q * one, parts[q]->data(), one * sizeof(float4), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+          dev_free(b->alloc, t, b->stream);
+          return cleanup(fail(PIMD_ECUDA, "mode-table upload failed"));
+        }
+      b->mtab[P] = t;
+    }
+    d.mfa_hi = b->mtab[P];
+    d.mfa_lo = b->mtab[P] + one;
+    d.mia_hi = b->mtab[P] + 2 * one;
+    d.mia_lo = b->mtab[P] + 3 * one;
+  }
   std::vector<float> cAf(tb.cA.begin(), tb.cA.end()), sAf(tb.sA.begin(), tb.sA.end());
   std::vector<float> wsAf(tb.wsA.begin(), tb.wsA.end()), c1f(tb.c1.begin(), tb.c1.end());
   std::vector<float> c2f(tb.c2.begin(), tb.c2.end());
@@ -1377,6 +1577,8 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
       {(void *)d.inv_mm, inv_mm.data(), N * sizeof(double)},
       {(void *)d.sigv, sigv.data(), N * sizeof(double)},
       {(void *)d.mass_mm, mass_mm.data(), N * sizeof(double)},
+      {(void *)d.inv_mmf, inv_mmf.data(), N * sizeof(float)},
+      {(void *)d.sigvf, sigvf.data(), N * sizeof(float)},
       {(void *)d.cAf, cAf.data(), P * sizeof(float)},
       {(void *)d.sAf, sAf.data(), P * sizeof(float)},
       {(void *)d.wsAf, wsAf.data(), P * sizeof(float)},
