@@ -62,6 +62,30 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def barrier(world):
+    """Host barrier across the replica ranks (gloo; no data-path collective)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    """The slowest rank's elapsed time: every rank's value, maximum taken."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank holds its own replica)."""
+    return world * units_per_rank / seconds
+
+
 def system(seed):
     from paper_2602_13553_gb300 import inputs
     w = WORKLOAD
@@ -387,15 +411,10 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.fill_(rank & 0xff)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     for _ in range(max(3, args.warmup)):
         flush_l2()
         bench_step()
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
@@ -408,17 +427,12 @@ def run_ours(args):
         bench_step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    barrier()
+    barrier(world)
     launches = sim.kernel_launches() - launches0
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
     units_per_rank = 3 * w["nmol"] * w["P"] * w["md_per_step"] * args.steps
-    value = world * units_per_rank / (total_ms / 1e3)
+    value = job_throughput(world, units_per_rank, total_ms / 1e3)
 
     # --- per-kernel device durations (CUDA events around every launch) -----
     ksteps = min(args.steps, 10)
@@ -437,20 +451,15 @@ def run_ours(args):
     xh.numpy()[:] = xa
     vh.numpy()[:] = va
     e2e_steps = max(3, args.steps // 2)
-    barrier()
+    barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         sim.set_state(xh.numpy(), vh.numpy(), st0)
         bench_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * 3 * w["nmol"] * w["P"] * w["md_per_step"] * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = job_throughput(world, 3 * w["nmol"] * w["P"] * w["md_per_step"] * e2e_steps, e2e_s)
     P, N = w["P"], 3 * w["nmol"]
     h2d = 2 * P * N * 3 * 8
     d2h = nchunks * ((3 * P + 12) * 8 + 4)
