@@ -65,6 +65,9 @@ struct RepDesc {
   double dr0;                 // tA / sqrt(P): centroid drift per unit v~_0
   double box[3], invbox[3];
   double kb, r0, kth, th0, eps, sig, rc, rlist, skin;
+  // FP32 copies for the force kernel: box, 1/box, kb, r0, kth, th0, rc^2,
+  // sigma^2, 4 eps, 24 eps
+  float boxf[3], invboxf[3], kbf, r0f, kthf, th0f, rc2f, sig2f, e4f, e24f;
   long long *ctl;
   double *xc, *v0;
   float *d, *vk, *F, *xcw;
@@ -90,8 +93,10 @@ struct RepDesc {
 //   mode 1 (finalize):   apply the last advance; a replica that stepped since
 //                        its last closing kick needs one now
 //   mode 2 (after close): the closed replicas are at integer time again
-__global__ void k_bctl(const RepDesc *reps, int nslots, int mode) {
+// Mode 0 also resets the item counter of the warp-item step kernel.
+__global__ void k_bctl(const RepDesc *reps, int nslots, int mode, int *wnext) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mode == 0 && r == 0 && wnext) *wnext = 0;
   if (r >= nslots || !reps[r].live) return;
   long long *c = reps[r].ctl;
   if (mode < 2 && c[kCtlActive]) {
@@ -108,19 +113,28 @@ __global__ void k_bctl(const RepDesc *reps, int nslots, int mode) {
   }
 }
 
+// FP32 Box-Muller on the 24 high bits of Philox words: u = (w >> 8 + 1/2) 2^-24
+// in (0, 1), radius sqrt(-2 ln u) and angle 2 pi u' from hardware
+// approximations (errors near 1e-6 of the deviate).  sin and cos of 2 pi u'
+// are taken as -sin, -cos of pi (2 u' - 1), whose argument lies in (-pi, pi).
+__device__ __forceinline__ float bm_radius(uint32_t w) {
+  const float u = fmaf((float)(w >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f);
+  const float x = fmaxf(-2.0f * __logf(u), 1e-30f);
+  return x * rsqrtf(x);
+}
+__device__ __forceinline__ float bm_angle(uint32_t w) {   // pi (2 u - 1)
+  const float u = fmaf((float)(w >> 8), 5.9604644775390625e-8f, 2.98023223876953125e-8f);
+  return 3.14159265358979f * fmaf(2.0f, u, -1.0f);
+}
+
 __device__ __forceinline__ float gauss1f_b(uint64_t seed, uint32_t atom, uint32_t mode, uint32_t stream,
                                            uint64_t step, int d) {
   const uint4 w = philox4x32_10(
       make_uint4(atom, (mode & 0xffffu) | (stream << 16), (uint32_t)step, (uint32_t)(step >> 32)),
       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-  const uint32_t wa = d < 2 ? w.x : w.z;
-  const uint32_t wb = d < 2 ? w.y : w.w;
-  const float s = 5.9604644775390625e-8f;  // 2^-24
-  const float r = sqrtf(-2.0f * __logf(((float)(wa >> 8) + 0.5f) * s));
-  const float ang = 2.0f * (((float)(wb >> 8) + 0.5f) * s);
-  float sn, cs;
-  sincospif(ang, &sn, &cs);
-  return r * (d == 1 ? sn : cs);
+  const float r = bm_radius(d < 2 ? w.x : w.z);
+  const float b = bm_angle(d < 2 ? w.y : w.w);
+  return -r * (d == 1 ? __sinf(b) : __cosf(b));
 }
 
 __device__ __forceinline__ void rotb(float &q, float &v, float c, float s_over_w, float w_s) {
@@ -143,14 +157,12 @@ __device__ __forceinline__ void gauss3f_b(uint64_t seed, uint32_t atom, uint32_t
   const uint4 w = philox4x32_10(
       make_uint4(atom, (mode & 0xffffu) | (stream << 16), (uint32_t)step, (uint32_t)(step >> 32)),
       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-  const float s = 5.9604644775390625e-8f;  // 2^-24
-  const float r0 = sqrtf(-2.0f * __logf(((float)(w.x >> 8) + 0.5f) * s));
-  const float r1 = sqrtf(-2.0f * __logf(((float)(w.z >> 8) + 0.5f) * s));
+  const float r0 = bm_radius(w.x), r1 = bm_radius(w.z);
   float sn, cs;
-  sincospif(2.0f * (((float)(w.y >> 8) + 0.5f) * s), &sn, &cs);
-  e0 = r0 * cs;
-  e1 = r0 * sn;
-  e2 = r1 * cospif(2.0f * (((float)(w.w >> 8) + 0.5f) * s));
+  __sincosf(bm_angle(w.y), &sn, &cs);
+  e0 = -r0 * cs;
+  e1 = -r0 * sn;
+  e2 = -r1 * __cosf(bm_angle(w.w));
 }
 
 // ---- tensor-core mode transforms (P % 8 == 0) -------------------------------
@@ -372,17 +384,411 @@ __device__ __forceinline__ void bstep_mma(const RepDesc *__restrict__ Rp, int P,
     for (int j = threadIdx.x & 31; j < P; j += 32) dg[r * P + j] = sF[r * PS + j];
 }
 
+// ---- warp-item step on tensor cores: P in {8, 16, 32, 64} --------------------
+// One warp advances a tile of 8 atoms x 3 components x P beads with no block
+// barrier, so the warps of an SM overlap one another's memory waits.  Per
+// component c the forward transforms are GEMMs C[mode][atom] = M[mode][bead]
+// X_c[bead][atom] whose B operand (8 atoms = one n-tile) is the staged tile;
+// the C fragment of lane (g, t) then holds modes {16 mt + g, 16 mt + g + 8} of
+// atoms {2t, 2t + 1} for all three components, so one Philox draw per
+// (atom, mode) serves the three components in registers, and the mode update
+// runs on the accumulators.  The inverse d'_c[bead][atom] = M^T q~'_c reads
+// q~' back from shared memory as its B operand.  3xTF32 throughout.
+constexpr int kWAtoms = 8;      // atoms per warp item
+constexpr int kWWarps = 4;      // warps per block
+constexpr int kWMaxP = 64;
+__host__ __device__ constexpr int wslot_floats(int P) { return 48 * (P + 4) + 128; }
+__host__ __device__ constexpr bool warp_class(int P) { return P == 8 || P == 16 || P == 32 || P == 64; }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &h, uint32_t &l) {
+  h = tf32_rna(x);
+  l = tf32_rna(x - __uint_as_float(h));
+}
+
+// c += A B with the 3xTF32 split, small terms first
+__device__ __forceinline__ void mma3(float (&c)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                     uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+  mma_tf32(c, al, bh0, bh1);
+  mma_tf32(c, ah, bl0, bl1);
+  mma_tf32(c, ah, bh0, bh1);
+}
+
+// A fragment of a mode-matrix table, kept in L1 in preference to streamed data
+__device__ __forceinline__ float4 ld_frag(const float4 *p) {
+  float4 v;
+  asm("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void frag_u32(const float4 &v, uint32_t (&a)[4]) {
+  a[0] = __float_as_uint(v.x);
+  a[1] = __float_as_uint(v.y);
+  a[2] = __float_as_uint(v.z);
+  a[3] = __float_as_uint(v.w);
+}
+
+// C_c[mode][atom] = M[mode][bead] S_c[bead][atom] for the three components of
+// a staged tile S ([c*8 + atom][bead], row stride P + 4), all mode tiles.
+template <int P>
+__device__ __forceinline__ void fwd_tile(const float4 *__restrict__ thi, const float4 *__restrict__ tlo,
+                                         const float *__restrict__ S, float (&C)[(P + 15) / 16][3][4]) {
+  constexpr int PS = P + 4, MT = (P + 15) / 16, KS = P / 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) C[mt][c][q] = 0.f;
+#pragma unroll 1
+  for (int ks = 0; ks < KS; ++ks) {
+    uint32_t bh[3][2], bl[3][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int so = (c * 8 + g) * PS + 8 * ks + t;
+      split_tf32(S[so], bh[c][0], bl[c][0]);
+      split_tf32(S[so + 4], bh[c][1], bl[c][1]);
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+      uint32_t ah[4], al[4];
+      const int o = (mt * KS + ks) * 32 + lane;
+      frag_u32(ld_frag(thi + o), ah);
+      frag_u32(ld_frag(tlo + o), al);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mma3(C[mt][c], ah, al, bh[c][0], bh[c][1], bl[c][0], bl[c][1]);
+    }
+  }
+}
+
+// Shared-memory slot of one warp (floats): staged forces [c*8 + atom][bead]
+// and deviations (the latter reused as q~' [c][mode][atom]), row stride P + 4
+// (conflict-free B fragments); then F~_0, the centroid-mode noise of both
+// streams per (atom, component) and the new FP64 centroids.
+template <int P>
+__device__ void bstep_warp(const RepDesc *__restrict__ Rp, int tile, float *__restrict__ slot, uint64_t step,
+                           int first) {
+  constexpr int PS = P + 4, MT = (P + 15) / 16, KS = P / 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int tile0 = tile * kWAtoms;
+  const int na = min(kWAtoms, Rp->N - tile0);
+  const size_t base = (size_t)tile0 * 3 * P;
+  float *sF = slot;
+  float *sX = slot + 24 * PS;
+  float *__restrict__ sf0 = slot + 48 * PS;
+  float *__restrict__ se = sf0 + 24;
+  float *__restrict__ se2 = se + 24;
+  double *__restrict__ sxc = reinterpret_cast<double *>(se2 + 24);
+  {
+    constexpr int CPR = P / 4;   // 16-byte chunks per (atom, component) row
+    const float *__restrict__ gF = Rp->F + base;
+    const float *__restrict__ gX = Rp->d + base;
+    const int nchunk = na * 3 * CPR;
+    for (int q = lane; q < nchunk; q += 32) {
+      const int row = q / CPR, col = (q - row * CPR) * 4;
+      const int a = row / 3, c = row - 3 * a;
+      const int so = (c * 8 + a) * PS + col;
+      cp_async16(sF + so, gF + (size_t)row * P + col);
+      cp_async16(sX + so, gX + (size_t)row * P + col);
+    }
+    cp_async_commit();
+    for (int q = lane; q < (kWAtoms - na) * 3 * P; q += 32) {   // rows of missing atoms
+      const int r = q / P, j = q - r * P;
+      const int a = na + r / 3, c = r - 3 * (r / 3);
+      sF[(c * 8 + a) * PS + j] = 0.f;
+      sX[(c * 8 + a) * PS + j] = 0.f;
+    }
+  }
+  const int integ = Rp->integrator, thermo = Rp->thermo;
+  const uint64_t seed = Rp->seed;
+  const double dt = Rp->dt;
+  const float hd = (float)dt, half = 0.5f * hd;
+  const float kick = first ? half : hd;
+  const float *__restrict__ cAf = Rp->cAf;
+  const float *__restrict__ sAf = Rp->sAf;
+  const float *__restrict__ wsAf = Rp->wsAf;
+  const float *__restrict__ c1f = Rp->c1f;
+  const float *__restrict__ c2f = Rp->c2f;
+  float *__restrict__ vkg = Rp->vk + base;
+  // per-lane atom constants (atoms 2t, 2t + 1) and the centroid prefetch
+  float imv[2], sgv[2];
+#pragma unroll
+  for (int aa = 0; aa < 2; ++aa) {
+    const int a = min(2 * t + aa, na - 1);
+    imv[aa] = __ldg(Rp->inv_mmf + tile0 + a);
+    sgv[aa] = __ldg(Rp->sigvf + tile0 + a);
+  }
+  double xpre = 0.0, vpre = 0.0;
+  if (lane < 3 * na) {
+    xpre = Rp->xc[(size_t)tile0 * 3 + lane];
+    vpre = Rp->v0[(size_t)tile0 * 3 + lane];
+  }
+  cp_async_wait_all();
+  __syncwarp();
+
+  const float4 *__restrict__ fhi = Rp->mfa_hi;
+  const float4 *__restrict__ flo = Rp->mfa_lo;
+  float *sQ = sX;   // q~ [c][mode][atom] once the deviations are transformed
+  float C[MT][3][4];
+  // forward transform of the deviations: q~_c = M d_c
+  fwd_tile<P>(fhi, flo, sX, C);
+  __syncwarp();   // every lane is done with the staged deviations
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int k = 16 * mt + g;
+      *reinterpret_cast<float2 *>(sQ + (c * P + k) * 8 + 2 * t) = make_float2(C[mt][c][0], C[mt][c][1]);
+      if (k + 8 < P)
+        *reinterpret_cast<float2 *>(sQ + (c * P + k + 8) * 8 + 2 * t) = make_float2(C[mt][c][2], C[mt][c][3]);
+    }
+  // forward transform of the forces: F~_c = M F_c, then F~ [c][mode][atom]
+  // over the staged forces
+  fwd_tile<P>(fhi, flo, sF, C);
+  __syncwarp();   // every lane is done with the staged forces
+  float *sG = sF;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int k = 16 * mt + g;
+      *reinterpret_cast<float2 *>(sG + (c * P + k) * 8 + 2 * t) = make_float2(C[mt][c][0], C[mt][c][1]);
+      if (k + 8 < P)
+        *reinterpret_cast<float2 *>(sG + (c * P + k + 8) * 8 + 2 * t) = make_float2(C[mt][c][2], C[mt][c][3]);
+    }
+  // mode update: lane (g, t) owns modes {16 mt + g, 16 mt + g + 8} of atoms
+  // {2t, 2t + 1}, the same (mode, atom) slots it wrote; q~' replaces q~
+#pragma unroll 1
+  for (int j = 0; j < 2 * MT; ++j) {
+    const int k = 16 * (j >> 1) + g + 8 * (j & 1);
+    if (k >= P) continue;
+    const float cA = __ldg(cAf + k), sA = __ldg(sAf + k), wsA = __ldg(wsAf + k);
+    const float c1 = __ldg(c1f + k), c2 = __ldg(c2f + k);
+    float2 qv[3], fv[3];
+    float vv[2][3], e[2][3], e2[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qv[c] = *reinterpret_cast<const float2 *>(sQ + (c * P + k) * 8 + 2 * t);
+      fv[c] = *reinterpret_cast<const float2 *>(sG + (c * P + k) * 8 + 2 * t);
+    }
+#pragma unroll
+    for (int aa = 0; aa < 2; ++aa) {
+      const int a = min(2 * t + aa, na - 1);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        vv[aa][c] = k != 0 ? __ldcs(vkg + (a * 3 + c) * P + k) : 0.f;
+        e[aa][c] = e2[aa][c] = 0.f;
+      }
+      if (thermo) gauss3f_b(seed, (uint32_t)(tile0 + a), (uint32_t)k, kStreamO1, step, e[aa][0], e[aa][1], e[aa][2]);
+      if (thermo && integ == 1 && !first)
+        gauss3f_b(seed, (uint32_t)(tile0 + a), (uint32_t)k, kStreamO2, step - 1, e2[aa][0], e2[aa][1], e2[aa][2]);
+    }
+    if (k == 0) {   // the centroid mode: FP64 phase below
+#pragma unroll
+      for (int aa = 0; aa < 2; ++aa) {
+        const int a = 2 * t + aa;
+        if (a >= na) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          sf0[a * 3 + c] = aa == 0 ? fv[c].x : fv[c].y;
+          se[a * 3 + c] = e[aa][c];
+          se2[a * 3 + c] = e2[aa][c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) qv[c] = make_float2(0.f, 0.f);   // the deviations carry no centroid mode
+    } else {
+#pragma unroll
+      for (int aa = 0; aa < 2; ++aa) {
+        const int a = 2 * t + aa;
+        if (a >= na) continue;
+        const float im = imv[aa], c2s = c2 * sgv[aa];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float v = vv[aa][c], qq = aa == 0 ? qv[c].x : qv[c].y;
+          const float ff = aa == 0 ? fv[c].x : fv[c].y;
+          if (integ == 0) {
+            v = fmaf(kick * im, ff, v);
+            rotb(qq, v, cA, sA, wsA);
+            if (thermo) v = fmaf(c1, v, c2s * e[aa][c]);
+            rotb(qq, v, cA, sA, wsA);
+          } else {
+            const float kb = half * im;
+            if (!first) {
+              v = fmaf(kb, ff, v);
+              if (thermo) v = fmaf(c1, v, c2s * e2[aa][c]);
+            }
+            if (thermo) v = fmaf(c1, v, c2s * e[aa][c]);
+            v = fmaf(kb, ff, v);
+            rotb(qq, v, cA, sA, wsA);
+          }
+          if (aa == 0) qv[c].x = qq; else qv[c].y = qq;
+          __stcs(vkg + (a * 3 + c) * P + k, v);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) *reinterpret_cast<float2 *>(sQ + (c * P + k) * 8 + 2 * t) = qv[c];
+  }
+  __syncwarp();
+  // centroid mode in FP64, one (atom, component) per lane: q~_0 = sqrt(P) xc
+  if (lane < 3 * na) {
+    const int a = lane / 3, c = lane - 3 * a;
+    const int i = tile0 + a;
+    const size_t ic = (size_t)tile0 * 3 + lane;
+    const double dr = Rp->dr0, c1_0 = Rp->c1_0;
+    const double kfac = (integ == 0 ? (first ? 0.5 : 1.0) : 0.5) * dt;
+    const double kb = kfac * __ldg(Rp->inv_mm + i);
+    const double c2s = Rp->c2_0 * __ldg(Rp->sigv + i);
+    const double f0 = (double)sf0[lane];
+    const float e = se[lane], e2 = se2[lane];
+    double x = xpre, v = vpre;
+    if (integ == 0) {
+      v = fma(kb, f0, v);
+      x = fma(dr, v, x);
+      if (thermo) v = fma(c1_0, v, c2s * (double)e);
+      x = fma(dr, v, x);
+    } else {
+      if (!first) {
+        v = fma(kb, f0, v);
+        if (thermo) v = fma(c1_0, v, c2s * (double)e2);
+      }
+      if (thermo) v = fma(c1_0, v, c2s * (double)e);
+      v = fma(kb, f0, v);
+      x = fma(dr, v, x);
+    }
+    Rp->xc[ic] = x;
+    Rp->v0[ic] = v;
+    Rp->xcw[ic] = wrapb(x, Rp->box[c], Rp->invbox[c]);
+    sxc[lane] = x;
+  }
+  // inverse: d'_c = M^T q~'_c, bead tiles of 16 as the M dimension
+  const float4 *__restrict__ ihi = Rp->mia_hi;
+  const float4 *__restrict__ ilo = Rp->mia_lo;
+  float D[MT][3][4];
+#pragma unroll
+  for (int bt = 0; bt < MT; ++bt)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) D[bt][c][q] = 0.f;
+#pragma unroll 1
+  for (int ks = 0; ks < KS; ++ks) {
+    uint32_t bh[3][2], bl[3][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float *qp = sQ + (c * P + 8 * ks + t) * 8 + g;
+      split_tf32(qp[0], bh[c][0], bl[c][0]);
+      split_tf32(qp[32], bh[c][1], bl[c][1]);
+    }
+#pragma unroll
+    for (int bt = 0; bt < MT; ++bt) {
+      uint32_t ah[4], al[4];
+      const int o = (bt * KS + ks) * 32 + lane;
+      frag_u32(ld_frag(ihi + o), ah);
+      frag_u32(ld_frag(ilo + o), al);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) mma3(D[bt][c], ah, al, bh[c][0], bh[c][1], bl[c][0], bl[c][1]);
+    }
+  }
+  __syncwarp();   // the centroids in sxc are visible to every lane
+  // new deviations, and the skin criterion: bead spread of the oxygens
+  float *__restrict__ dg = Rp->d + base;
+  float vdev = 0.f;
+#pragma unroll
+  for (int bt = 0; bt < MT; ++bt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int bead = 16 * bt + g + 8 * (q >> 1);
+      const int a = 2 * t + (q & 1);
+      if (bead < P && a < na) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) __stcs(dg + (a * 3 + c) * P + bead, D[bt][c][q]);
+        if ((tile0 + a) % 3 == 0)
+          vdev = fmaxf(vdev, D[bt][0][q] * D[bt][0][q] + D[bt][1][q] * D[bt][1][q] + D[bt][2][q] * D[bt][2][q]);
+      }
+    }
+  // centroid drift of the oxygens since the last rebuild
+  float vdisp = 0.f;
+  if (lane < na && (tile0 + lane) % 3 == 0) {
+    const int m = (tile0 + lane) / 3;
+    double s2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double x = sxc[lane * 3 + c];
+      const double gd = x - Rp->cref[3 * m + c];
+      s2 = fma(gd, gd, s2);
+      Rp->ccur[3 * m + c] = x;
+    }
+    vdisp = (float)s2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vdisp = fmaxf(vdisp, __shfl_xor_sync(0xffffffffu, vdisp, o));
+    vdev = fmaxf(vdev, __shfl_xor_sync(0xffffffffu, vdev, o));
+  }
+  if (lane < 2) {
+    const double mx = lane == 0 ? (double)vdisp : (double)vdev;
+    // margins for FP32 rounding of the deviations and squared drifts; NaN forces a rebuild
+    Rp->blkmax[2 * tile + lane] = (mx == mx) ? sqrt(mx) * (1.0 + 1e-6) + 1e-4 : 1e300;
+  }
+  __syncwarp();   // the slot is free for the next item
+}
+
+// Warp items (replica, 8-atom tile) of the bead counts in {8, 16, 32, 64},
+// the prefix counts[4] of the step list, taken dynamically: lane 0 of each
+// warp claims the next item from the counter *next (reset by k_bctl).
+__global__ void __launch_bounds__(kWWarps * 32, 4) k_bstep_w(const RepDesc *__restrict__ reps,
+                                                            const int2 *__restrict__ items,
+                                                            const int *__restrict__ counts, int *next,
+                                                            int slot_floats) {
+  extern __shared__ __align__(16) float wsm[];
+  float *slot = wsm + (threadIdx.x >> 5) * slot_floats;
+  const int n = counts[4];
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(next, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n) break;
+    const int2 w = items[it];
+    const RepDesc *__restrict__ Rp = reps + w.x;
+    const long long *ctl = Rp->ctl;
+    if (!ctl[kCtlActive]) continue;
+    const uint64_t step = (uint64_t)ctl[kCtlStep];
+    const int first = (int)ctl[kCtlFirst];
+    switch (Rp->P) {
+      case 8: bstep_warp<8>(Rp, w.y, slot, step, first); break;
+      case 16: bstep_warp<16>(Rp, w.y, slot, step, first); break;
+      case 32: bstep_warp<32>(Rp, w.y, slot, step, first); break;
+      case 64: bstep_warp<64>(Rp, w.y, slot, step, first); break;
+      default: break;
+    }
+  }
+}
+
 // The split-precision fused step (same arithmetic as the single-system split
-// kernel) over work items (replica, tile).  Every descriptor field an item
+// kernel) over the block items (replica, tile) of the bead counts outside the
+// warp-item classes: the suffix [counts[4], counts[0]) of the step list.
+// Every descriptor field an item
 // needs is read once into registers (restrict-qualified), and the task index
 // split (mode, row) uses shifts when P is a power of two.
 __global__ void __launch_bounds__(128, 4) k_bstep(const RepDesc *__restrict__ reps, const int2 *__restrict__ items,
-                                               const int *__restrict__ count) {
+                                               const int *__restrict__ counts) {
   __shared__ __align__(16) float sbuf[kStepSmem];
   float *sD = sbuf, *sV = sbuf + kTileMax, *sF = sbuf + 2 * kTileMax, *sQ = sbuf + 3 * kTileMax;
   __shared__ double sred[2][4];
-  const int n = *count;
-  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+  const int n = counts[0];
+  for (int it = counts[4] + blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = items[it];
     const RepDesc *__restrict__ Rp = reps + w.x;
     long long *__restrict__ ctl = Rp->ctl;
@@ -802,8 +1208,8 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
     const int k = w.z * Bk + kl;
     if (u >= G || m >= R.nmol || k >= P) continue;
     const int o = 3 * m;
-    const float L0 = (float)R.box[0], L1 = (float)R.box[1], L2 = (float)R.box[2];
-    const float i0 = (float)R.invbox[0], i1 = (float)R.invbox[1], i2 = (float)R.invbox[2];
+    const float L0 = R.boxf[0], L1 = R.boxf[1], L2 = R.boxf[2];
+    const float i0 = R.invboxf[0], i1 = R.invboxf[1], i2 = R.invboxf[2];
     const size_t so = (size_t)o * 3 * P + k;
     const float co0 = R.xcw[3 * o], co1 = R.xcw[3 * o + 1], co2 = R.xcw[3 * o + 2];
     const float do0 = R.d[so], do1 = R.d[so + P], do2 = R.d[so + 2 * P];
@@ -823,9 +1229,9 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
     float ub = 0.f, wb = 0.f;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const float dr = r[h] - (float)R.r0;
-      ub = fmaf(0.5f * (float)R.kb * dr, dr, ub);
-      const float g = -(float)R.kb * dr * ir[h];
+      const float dr = r[h] - R.r0f;
+      ub = fmaf(0.5f * R.kbf * dr, dr, ub);
+      const float g = -R.kbf * dr * ir[h];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         fH[h][c] = g * dv[h][c];
@@ -838,8 +1244,8 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
       const float dot = dv[0][0] * dv[1][0] + dv[0][1] * dv[1][1] + dv[0][2] * dv[1][2];
       const float cth = fminf(1.f, fmaxf(-1.f, dot * ir01));
       const float th = acosf(cth);
-      const float dth = th - (float)R.th0;
-      const float pref = (float)R.kth * dth / sinf(th);
+      const float dth = th - R.th0f;
+      const float pref = R.kthf * dth / sinf(th);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int g = 1 - h;
@@ -851,7 +1257,7 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
           wb = fmaf(dv[h][c], fa, wb);
         }
       }
-      ub = fmaf(0.5f * (float)R.kth * dth, dth, ub);
+      ub = fmaf(0.5f * R.kthf * dth, dth, ub);
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) fO[c] = -(fH[0][c] + fH[1][c]);
@@ -860,10 +1266,9 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
     const int *off = R.nbr_off + (size_t)m * (NS + 1);
     const int q1 = __ldg(off + NS);
     const int *__restrict__ nl = R.nbr + (size_t)m * kMaxNeighbours;
-    const float rc2 = (float)(R.rc * R.rc);
-    const float sig2 = (float)(R.sig * R.sig);
-    const float e4 = (float)(4.0 * R.eps), e24 = (float)(24.0 * R.eps);
+    const float rc2 = R.rc2f, sig2 = R.sig2f, e4 = R.e4f, e24 = R.e24f;
     float ulj = 0.f, wlj = 0.f;
+#pragma unroll 4
     for (int q = __ldg(off); q < q1; ++q) {
       const int j = __ldg(nl + q);
       const size_t sj = (size_t)(3 * j) * 3 * P + k;
@@ -872,7 +1277,7 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
       const float d2 = micb(__ldg(xcw + 9 * j + 2) - co2, L2, i2) + (__ldg(dg + sj + 2 * P) - do2);
       const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
       if (r2 < rc2) {
-        const float inv = 1.f / r2;
+        const float inv = __frcp_rn(r2);
         const float s2 = sig2 * inv;
         const float s6 = s2 * s2 * s2;
         ulj = fmaf(e4, fmaf(s6, s6, -s6), ulj);
@@ -889,8 +1294,8 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
       R.F[so + 3 * P + c * P] = fH[0][c];
       R.F[so + 6 * P + c * P] = fH[1][c];
     }
-    R.Upart[(size_t)m * P + k] = (double)ub + 0.5 * (double)ulj;
-    R.Wpart[(size_t)m * P + k] = (double)wb + 0.5 * (double)wlj;
+    R.Upart[(size_t)m * P + k] = (double)fmaf(0.5f, ulj, ub);
+    R.Wpart[(size_t)m * P + k] = (double)fmaf(0.5f, wlj, wb);
   }
 }
 
@@ -1128,7 +1533,9 @@ struct pimd_batch {
   DevAllocator alloc;
   std::vector<Replica> reps;
   RepDesc *d_reps = nullptr;
-  int *d_counts = nullptr;                 // [4]: step, cluster, nbr, est items (all replicas)
+  // [8]: step, cluster, nbr, est items (all replicas); [4] warp-item prefix
+  // of the step list; [5] the warp-item counter
+  int *d_counts = nullptr;
   int2 *d_step = nullptr, *d_nbr = nullptr, *d_est = nullptr;
   int4 *d_clu = nullptr;
   size_t cap_step = 0, cap_clu = 0, cap_nbr = 0, cap_est = 0;
@@ -1150,7 +1557,12 @@ struct pimd_batch {
   float4 *mtab[PIMD_MAX_BEADS + 1] = {nullptr};
   std::vector<int2> h_step, h_nbr, h_est;
   std::vector<int4> h_clu;
-  int h_counts[4] = {0, 0, 0, 0};
+  int h_counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int wslot = 0;          // floats of shared memory per warp of the warp-item step kernel
+  int grid_w = 0;         // its blocks (persistent grid)
+  int wblocks_sm = 0;     // blocks per SM in use
+  int wtuned = 0;         // blocks per SM chosen by the autotuner (0: the occupancy limit)
+  int nsm = 152;
 };
 
 namespace hostside {
@@ -1180,7 +1592,7 @@ pimd_status grow(pimd_batch *b, T **ptr, size_t *cap, size_t need) {
 }
 
 void replica_items(pimd_batch *b, int slot, Replica &r) {
-  r.A = b->tileA[r.P] > 0 ? b->tileA[r.P] : default_tile(r.P);
+  r.A = warp_class(r.P) ? kWAtoms : (b->tileA[r.P] > 0 ? b->tileA[r.P] : default_tile(r.P));
   r.ntiles = (r.N + r.A - 1) / r.A;
   r.ne = std::min(r.ntiles, 8);
   r.items_step.clear();
@@ -1210,10 +1622,25 @@ pimd_status upload(pimd_batch *b) {
   b->h_nbr.clear();
   b->h_est.clear();
   std::vector<RepDesc> descs(b->capacity);
+  // warp items first, largest bead count first (the costliest items are
+  // claimed first), then the block items of the other bead counts
+  int pmax_w = 0;
+  for (int P : {64, 32, 16, 8})
+    for (int s = 0; s < b->capacity; ++s) {
+      Replica &r = b->reps[s];
+      if (r.live && r.P == P) {
+        b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
+        pmax_w = std::max(pmax_w, P);
+      }
+    }
+  const int nw = (int)b->h_step.size();
+  for (int s = 0; s < b->capacity; ++s) {
+    Replica &r = b->reps[s];
+    if (r.live && !warp_class(r.P)) b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
+  }
   for (int s = 0; s < b->capacity; ++s) {
     Replica &r = b->reps[s];
     if (r.live) {
-      b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
       b->h_clu.insert(b->h_clu.end(), r.items_clu.begin(), r.items_clu.end());
       b->h_nbr.insert(b->h_nbr.end(), r.items_nbr.begin(), r.items_nbr.end());
       b->h_est.insert(b->h_est.end(), r.items_est.begin(), r.items_est.end());
@@ -1232,6 +1659,23 @@ pimd_status upload(pimd_batch *b) {
   b->h_counts[1] = (int)b->h_clu.size();
   b->h_counts[2] = (int)b->h_nbr.size();
   b->h_counts[3] = (int)b->h_est.size();
+  b->h_counts[4] = nw;
+  b->h_counts[5] = 0;
+  const int slot = pmax_w ? wslot_floats(pmax_w) : wslot_floats(8);
+  if (slot != b->wslot) {
+    b->wslot = slot;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k_bstep_w, kWWarps * 32,
+                                                      (size_t)kWWarps * slot * sizeof(float)) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    b->wblocks_sm = b->wtuned > 0 ? std::min(b->wtuned, nb) : nb;
+    b->grid_w = b->nsm * b->wblocks_sm;
+    if (b->graph) {   // the captured launch has the old shared-memory size
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
   if (!b->h_step.empty())
     BK(cudaMemcpyAsync(b->d_step, b->h_step.data(), b->h_step.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream));
   if (!b->h_clu.empty())
@@ -1247,11 +1691,18 @@ pimd_status upload(pimd_batch *b) {
   return PIMD_OK;
 }
 
+// The two step kernels: warp items, then block items.
+void launch_step_kernels(pimd_batch *b) {
+  k_bstep_w<<<b->grid_w, kWWarps * 32, (size_t)kWWarps * b->wslot * sizeof(float), b->stream>>>(
+      b->d_reps, b->d_step, b->d_counts, b->d_counts + 5, b->wslot);
+  k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts);
+}
+
 // One MD step of every active replica.
 cudaError_t launch_one_step(pimd_batch *b, cudaEvent_t e0, cudaEvent_t e1) {
-  k_bctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, 0);
+  k_bctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, 0, b->d_counts + 5);
   if (e0) cudaEventRecord(e0, b->stream);
-  k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+  launch_step_kernels(b);
   if (e1) cudaEventRecord(e1, b->stream);
   k_bnbr<<<b->grid_nbr, 128, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, 0);
   k_bforce<<<b->grid_clu, 128, 0, b->stream>>>(b->d_reps, b->d_clu, b->d_counts + 1, 0);
@@ -1393,6 +1844,14 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
     pimd_batch_destroy(b);
     return fail(PIMD_ECUDA, "cannot enable %zu bytes of shared memory for the neighbour kernel", kNbrSmem);
   }
+  const int wsmem = (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float));
+  if (cudaFuncSetAttribute((const void *)k_bstep_w, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    pimd_batch_destroy(b);
+    return fail(PIMD_ECUDA, "cannot enable %d bytes of shared memory for the step kernel", wsmem);
+  }
+  b->nsm = nsm;
   // persistent grids: every SM filled to the kernel's occupancy limit
   auto occ = [&](const void *fn, size_t smem = 0) {
     int n = 0;
@@ -1408,7 +1867,7 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
     return st;
   };
   b->d_reps = (RepDesc *)dev_alloc(b->alloc, sizeof(RepDesc) * max_replicas, b->stream);
-  b->d_counts = (int *)dev_alloc(b->alloc, 4 * sizeof(int), b->stream);
+  b->d_counts = (int *)dev_alloc(b->alloc, 8 * sizeof(int), b->stream);
   b->d_eout = (double *)dev_alloc(b->alloc, sizeof(double) * kOutStride * max_replicas, b->stream);
   b->d_ctl = (long long *)dev_alloc(b->alloc, sizeof(long long) * kCtlWords * max_replicas, b->stream);
   if (!b->d_reps || !b->d_counts || !b->d_eout || !b->d_ctl)
@@ -1508,6 +1967,18 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   d.rc = sys->ff[6];
   d.skin = 1.5;
   d.rlist = d.rc + d.skin;
+  for (int c = 0; c < 3; ++c) {
+    d.boxf[c] = (float)d.box[c];
+    d.invboxf[c] = (float)d.invbox[c];
+  }
+  d.kbf = (float)d.kb;
+  d.r0f = (float)d.r0;
+  d.kthf = (float)d.kth;
+  d.th0f = (float)d.th0;
+  d.rc2f = (float)(d.rc * d.rc);
+  d.sig2f = (float)(d.sig * d.sig);
+  d.e4f = (float)(4.0 * d.eps);
+  d.e24f = (float)(24.0 * d.eps);
   auto cleanup = [&](pimd_status s2) {
     cudaStreamSynchronize(b->stream);
     dev_free(b->alloc, r.arena, b->stream);
@@ -1665,18 +2136,18 @@ extern "C" pimd_status pimd_batch_run(pimd_batch *b, int64_t nsteps) {
     if (!b->graph && (st = capture(b)) != PIMD_OK) return st;
     while (left >= b->graph_steps) {
       BK(cudaGraphLaunch(b->graph, b->stream));
-      b->launches += 4 * b->graph_steps;
+      b->launches += 5 * b->graph_steps;
       left -= b->graph_steps;
     }
   }
   for (; left > 0; --left) {
     BK(launch_one_step(b, nullptr, nullptr));
-    b->launches += 4;
+    b->launches += 5;
   }
   const int cg = (b->capacity + 127) / 128;
-  k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1);
+  k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1, nullptr);
   k_bclose<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
-  k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2);
+  k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2, nullptr);
   b->launches += 3;
   BK(cudaGetLastError());
   return PIMD_OK;
@@ -1776,9 +2247,9 @@ extern "C" pimd_status pimd_batch_time_kernels(pimd_batch *b, int32_t nsteps, do
   double acc[4] = {0, 0, 0, 0};
   for (int s = 0; s < nsteps; ++s) {
     cudaEventRecord(ev[0], b->stream);
-    k_bctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, 0);
+    k_bctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, 0, b->d_counts + 5);
     cudaEventRecord(ev[1], b->stream);
-    k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
+    launch_step_kernels(b);
     cudaEventRecord(ev[2], b->stream);
     k_bnbr<<<b->grid_nbr, 128, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, 0);
     cudaEventRecord(ev[3], b->stream);
@@ -1790,18 +2261,20 @@ extern "C" pimd_status pimd_batch_time_kernels(pimd_batch *b, int32_t nsteps, do
       BK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
       acc[k] += t;
     }
-    b->launches += 4;
+    b->launches += 5;
   }
   for (auto &e : ev) cudaEventDestroy(e);
   for (int k = 0; k < 4; ++k) ms[k] = acc[k];
   return pimd_batch_run(b, 0) == PIMD_OK ? PIMD_OK : fail(PIMD_ECUDA, "timing close failed");
 }
 
-// Autotuner of the step-kernel tile: for each bead count present, try tiles
-// A = Amax, Amax/2, ..., 1 (A atoms x 3 components x P modes per block) while
-// the replicas keep stepping, time the step kernel with CUDA events, keep the
-// fastest.  A replica's arithmetic does not depend on A, so tuning changes no
-// trajectory; the tuning steps count toward the replicas' step budgets.
+// Autotuner of the step kernels, timed with CUDA events while the replicas
+// keep stepping: for the warp-item kernel (P in {8, 16, 32, 64}, 8-atom
+// tiles) the number of resident blocks per SM, which trades warps in flight
+// against L1 left for the mode-matrix fragments; for every other bead count
+// present the block tile A = Amax, Amax/2, ..., 1 (A atoms x 3 components x P
+// modes per block).  Neither changes a replica's arithmetic, so tuning
+// changes no trajectory; the tuning steps count toward the step budgets.
 extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t *tiles_out) {
   if (!b) return fail(PIMD_EINVAL, "batch is NULL");
   if (steps_per_trial < 1) steps_per_trial = 2;
@@ -1823,12 +2296,44 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
       BK(cudaEventElapsedTime(&ms, e0, e1));
       total += ms;
     }
-    b->launches += 4 * steps_per_trial;
+    b->launches += 5 * steps_per_trial;
     *ms_out = total;
     return PIMD_OK;
   };
   pimd_status st = PIMD_OK;
+  if (std::any_of(classes.begin(), classes.end(), [](int P) { return warp_class(P); })) {
+    if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
+    int nbmax = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbmax, (const void *)k_bstep_w, kWWarps * 32,
+                                                      (size_t)kWWarps * b->wslot * sizeof(float)) != cudaSuccess ||
+        nbmax < 1)
+      nbmax = 1;
+    int best = nbmax;
+    float best_ms = 1e30f;
+    for (int nb = nbmax; nb >= 1 && st == PIMD_OK; --nb) {
+      b->wblocks_sm = nb;
+      b->grid_w = b->nsm * nb;
+      float ms = 0.f;
+      st = time_step(&ms);
+      if (st == PIMD_OK && ms < best_ms) {
+        best_ms = ms;
+        best = nb;
+      }
+    }
+    b->wblocks_sm = best;
+    b->wtuned = best;
+    b->grid_w = b->nsm * best;
+    if (b->graph) {   // captured with another grid
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
   for (int P : classes) {
+    if (st != PIMD_OK) break;
+    if (warp_class(P)) {
+      b->tileA[P] = kWAtoms;
+      continue;
+    }
     const int amax = default_tile(P);
     int best = amax;
     float best_ms = 1e30f;
@@ -1854,9 +2359,9 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
   if (st == PIMD_OK) st = pimd_batch_run(b, 0);
   if (st == PIMD_OK) {
     const int cg = (b->capacity + 127) / 128;
-    k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1);
+    k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1, nullptr);
     k_bclose<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts + 0);
-    k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2);
+    k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 2, nullptr);
     b->launches += 3;
     if (cudaGetLastError() != cudaSuccess) st = fail(PIMD_ECUDA, "autotune close failed");
   }
