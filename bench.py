@@ -235,7 +235,7 @@ def batched_bench(stream, steps, warmup):
         # centroids, 16 B per molecule-bead of energy/virial rows
         step_bytes += 60.0 * N * r.P + 124.0 * N
         force_bytes += 24.0 * N * r.P + 12.0 * N + 16.0 * r.nmol * r.P
-    tiles = b.autotune(1)
+    tiles = b.autotune(3)
     for _ in range(warmup):
         b.run(100)
         b.estimators()
@@ -270,10 +270,11 @@ def batched_bench(stream, steps, warmup):
         "autotuned_tiles": {str(k): v for k, v in tiles.items()},
         "nbr_rebuilds_per_replica_step": rebuild_rate,
         "vs_plain_fp64": None,
-        "roofline": {"bound": "hbm", "kernel": "k_bstep" if dom == "step" else "k_bforce",
+        "roofline": {"bound": "hbm", "kernel": "k_bstep_w" if dom == "step" else "k_bforce",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": src, "algorithmic_bytes_per_launch": bytes_,
-                     "avg_launch_ms": per_ms, "traffic": traffic_for("k_bstep" if dom == "step" else "k_bforce"),
+                     "avg_launch_ms": per_ms,
+                     "traffic": traffic_for("k_bstep_w" if dom == "step" else "k_bforce"),
                      "kernel_time_share": {k: round(v / tot, 4) for k, v in kt.items()}},
     }
 
