@@ -34,6 +34,10 @@ POT_HARMONIC = 0
 POT_WATERLIKE = 1
 BAOAB = 0
 OBABO = 1
+NMPIMD = 0
+PIMD = 1          # Cartesian method
+FM_PHYSICAL = 0
+FM_NORMAL = 1
 
 
 def build(force: bool = False) -> str:
@@ -53,7 +57,7 @@ class _Sim(ctypes.Structure):
     _fields_ = [
         ("N", ctypes.c_int32), ("P", ctypes.c_int32),
         ("potential", ctypes.c_int32), ("thermostat", ctypes.c_int32),
-        ("integrator", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("integrator", ctypes.c_int32), ("method", ctypes.c_int32),
         ("T", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
         ("scale", ctypes.c_double), ("sp", ctypes.c_double),
         ("seed", ctypes.c_uint64),
@@ -66,6 +70,8 @@ class _Sim(ctypes.Structure):
         ("U", ctypes.POINTER(ctypes.c_double)),
         ("vir", ctypes.POINTER(ctypes.c_double)),
         ("step", ctypes.c_int64),
+        ("fmmode", ctypes.c_int32), ("fixcom", ctypes.c_int32),
+        ("fmass", ctypes.c_double),
     ]
 
 
@@ -217,14 +223,18 @@ def max_threads() -> int:
 class Sim:
     """One ring-polymer system advanced by the oracle.
 
-    x0: [P][N][3] bead positions (A, unwrapped); v0: [P][N][3] normal-mode
-    velocities (A/ps) at integer time, or None to draw them thermally (noise
-    stream 2).  potential 0 = harmonic (ff[0] = omega in 1/ps), 1 = water-like
-    (ff = kb, r0, kth, th0, eps, sig, rc).  thermostat 0 = NVE, 1 = PILE_L.
+    x0: [P][N][3] bead positions (A, unwrapped); v0: [P][N][3] velocities
+    (A/ps) at integer time -- normal-mode velocities (method NMPIMD) or bead
+    velocities (method PIMD, Cartesian) -- or None to draw them thermally
+    (noise stream 2).  potential 0 = harmonic (ff[0] = omega in 1/ps), 1 =
+    water-like (ff = kb, r0, kth, th0, eps, sig, rc).  thermostat 0 = NVE,
+    1 = PILE_L.  fmmode 0 = physical, 1 = normal; fmass scales the fictitious
+    masses; fixcom removes the centre-of-mass velocity every step.
     """
 
     def __init__(self, x0, mass, *, T, dt, potential=POT_HARMONIC, ff=(0.0,), box=(0.0, 0.0, 0.0),
-                 v0=None, thermostat=1, integrator=BAOAB, seed=1, tau=1.0, scale=1.0, sp=1.0):
+                 v0=None, thermostat=1, integrator=BAOAB, seed=1, tau=1.0, scale=1.0, sp=1.0,
+                 method=NMPIMD, fmmode=FM_PHYSICAL, fmass=1.0, fixcom=0):
         x0 = np.ascontiguousarray(x0, dtype=np.float64)
         P, N, three = x0.shape
         assert three == 3 and 1 <= P <= 128
@@ -239,6 +249,7 @@ class Sim:
         s = _Sim()
         s.N, s.P = N, P
         s.potential, s.thermostat, s.integrator = potential, thermostat, integrator
+        s.method, s.fmmode, s.fixcom, s.fmass = method, fmmode, int(fixcom), float(fmass)
         s.T, s.dt, s.tau, s.scale, s.sp = T, dt, tau, scale, sp
         s.seed = seed
         for a in range(3):

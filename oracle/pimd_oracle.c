@@ -319,16 +319,31 @@ typedef struct {
   int32_t potential;   /* 0 harmonic, 1 water-like */
   int32_t thermostat;  /* 0 none (NVE), 1 PILE_L */
   int32_t integrator;  /* 0 BAOAB, 1 OBABO */
-  int32_t pad0;
+  int32_t method;      /* 0 nmpimd (normal modes), 1 pimd (Cartesian), Sec. III.C */
   double T, dt, tau, scale, sp;
   uint64_t seed;
   double box[3];
   double ff[8];
-  const double *mass;        /* [N] */
-  double *x, *v, *F;         /* [P][N][3]; v in normal modes at integer time */
+  const double *mass;        /* [N] physical masses */
+  double *x, *v, *F;         /* [P][N][3]; v: normal-mode (nmpimd) or bead (pimd) velocities */
   double *U, *vir;           /* [P] */
   int64_t step;
+  int32_t fmmode;      /* 0 physical, 1 normal (Sec. III.C) */
+  int32_t fixcom;      /* remove the centre-of-mass velocity every step */
+  double fmass;        /* factor on the fictitious masses (Sec. III.C) */
 } or_sim;
+
+/* Fictitious-mass factor of mode k (nmpimd), Sec. III.C keywords fmmode and
+ * fmass: m^(k) = fmass * mu_k * m with mu_k = 1 (physical) or lambda_k
+ * (normal, k >= 1); the centroid keeps mu_0 = 1 since lambda_0 = 0.  The
+ * Cartesian method uses fmass * m for every bead. */
+static double or_mode_mu(const or_sim *s, int k) {
+  if (s->method == 0 && s->fmmode == 1 && k > 0) {
+    double sn = sin(OR_PI * k / s->P);
+    return s->fmass * 4.0 * sn * sn;
+  }
+  return s->fmass;
+}
 
 /* Forces on every bead k from its own coordinates (Eq. (1): U(r^(k))). */
 void or_compute_forces(or_sim *s) {
@@ -373,16 +388,19 @@ void or_from_nm(int P, int N, const double *M, const double *q, double *x) {
 static void or_B(or_sim *s, const double *M, double *Ft, double tau) {
   int N = s->N, P = s->P;
   or_to_nm(P, N, M, s->F, Ft);
-  for (int k = 0; k < P; ++k)
+  for (int k = 0; k < P; ++k) {
+    double mu = or_mode_mu(s, k);
     for (int n = 0; n < N; ++n)
       for (int a = 0; a < 3; ++a) {
         size_t id = ((size_t)k * N + n) * 3 + a;
-        s->v[id] += tau * Ft[id] / (s->mass[n] * OR_MVV2E);
+        s->v[id] += tau * Ft[id] / (s->mass[n] * mu * OR_MVV2E);
       }
+  }
 }
 
-/* A: exact flow of the free ring polymer H_k = 1/2 m v~^2 + 1/2 m w_k^2 q~^2
- * for time tau, mode by mode (i-PI's equations of motion, Sec. IV.A).
+/* A: exact flow of the free ring polymer H_k = 1/2 m^(k) v~^2 + 1/2 m w_k^2 q~^2
+ * for time tau, mode by mode (i-PI's equations of motion, Sec. IV.A): the
+ * mode oscillates at omega[k] = w_k / sqrt(m^(k) / m) (the caller's table).
  * The centroid (w_0 = 0) drifts. */
 static void or_A(or_sim *s, const double *omega, double *q, double tau) {
   int N = s->N, P = s->P;
@@ -403,17 +421,19 @@ static void or_A(or_sim *s, const double *omega, double *q, double tau) {
   }
 }
 
-/* O: PILE_L, App. D:  v~ <- c1 v~ + c2 sqrt(P kB T / (m mvv2e)) eta. */
+/* O: PILE_L, App. D:  v~ <- c1 v~ + c2 sqrt(P kB T / (m^(k) mvv2e)) eta, with
+ * tau_k = scale / (2 omega_k) for the mode's own frequency omega[k]. */
 static void or_O(or_sim *s, const double *omega, double dtO, uint32_t stream) {
   int N = s->N, P = s->P;
   for (int k = 0; k < P; ++k) {
     double tauk = (k == 0) ? s->tau : s->scale / (2.0 * omega[k]);
     double c1 = exp(-dtO / tauk);
     double c2 = sqrt(1.0 - c1 * c1);
+    double mu = or_mode_mu(s, k);
     for (int n = 0; n < N; ++n) {
       double eta[3];
       or_gauss3(s->seed, (uint32_t)n, (uint32_t)k, stream, (uint64_t)s->step, eta);
-      double sig = sqrt(P * OR_KB * s->T / (s->mass[n] * OR_MVV2E));
+      double sig = sqrt(P * OR_KB * s->T / (s->mass[n] * mu * OR_MVV2E));
       for (int a = 0; a < 3; ++a) {
         size_t id = ((size_t)k * N + n) * 3 + a;
         s->v[id] = c1 * s->v[id] + c2 * sig * eta[a];
@@ -422,23 +442,87 @@ static void or_O(or_sim *s, const double *omega, double dtO, uint32_t stream) {
   }
 }
 
-/* Draw v~ for every mode from N(0, P kB T / (m mvv2e)) with noise stream 2
- * at step 0 (the ring polymer is thermostatted at P T, Sec. IV.A). */
+/* Draw v~ for every mode (or v for every bead, Cartesian) from
+ * N(0, P kB T / (m^(k) mvv2e)) with noise stream 2 at step 0 (the ring
+ * polymer is thermostatted at P T, Sec. IV.A). */
 void or_thermal_velocities(or_sim *s) {
   int N = s->N, P = s->P;
   for (int k = 0; k < P; ++k)
     for (int n = 0; n < N; ++n) {
       double eta[3];
       or_gauss3(s->seed, (uint32_t)n, (uint32_t)k, 2u, 0u, eta);
-      double sig = sqrt(P * OR_KB * s->T / (s->mass[n] * OR_MVV2E));
+      double sig = sqrt(P * OR_KB * s->T / (s->mass[n] * or_mode_mu(s, k) * OR_MVV2E));
       for (int a = 0; a < 3; ++a) s->v[((size_t)k * N + n) * 3 + a] = sig * eta[a];
+    }
+}
+
+/* fixcom (Sec. III.C): subtract the mass-weighted mean velocity of the
+ * centroid mode (nmpimd) or of every bead separately (pimd), once per step at
+ * its end (after the closing B, and after the closing O of OBABO). */
+static void or_fixcom(or_sim *s) {
+  int N = s->N, P = s->P;
+  int nb = s->method == 0 ? 1 : P;
+  double mt = 0.0;
+  for (int n = 0; n < N; ++n) mt += s->mass[n];
+  for (int k = 0; k < nb; ++k) {
+    double pc[3] = {0.0, 0.0, 0.0};
+    for (int n = 0; n < N; ++n)
+      for (int a = 0; a < 3; ++a) pc[a] += s->mass[n] * s->v[((size_t)k * N + n) * 3 + a];
+    for (int n = 0; n < N; ++n)
+      for (int a = 0; a < 3; ++a) s->v[((size_t)k * N + n) * 3 + a] -= pc[a] / mt;
+  }
+}
+
+/* Cartesian method (Sec. III.C "method pimd"): bead velocities v, the ring
+ * springs of Eq. (1) as forces, F_s^(k) = -m omega_n^2 (2 r^k - r^(k-1) -
+ * r^(k+1)) (cyclic), and the bead masses fmass * m. */
+static void or_B_cart(or_sim *s, double wn, double tau) {
+  int N = s->N, P = s->P;
+  for (int k = 0; k < P; ++k) {
+    int km = (k + P - 1) % P, kp = (k + 1) % P;
+    for (int n = 0; n < N; ++n) {
+      double mm = s->mass[n] * OR_MVV2E;
+      for (int a = 0; a < 3; ++a) {
+        size_t id = ((size_t)k * N + n) * 3 + a;
+        double xk = s->x[id];
+        double fs = -mm * wn * wn *
+                    (2.0 * xk - s->x[((size_t)km * N + n) * 3 + a] - s->x[((size_t)kp * N + n) * 3 + a]);
+        s->v[id] += tau * (s->F[id] + fs) / (mm * s->fmass);
+      }
+    }
+  }
+}
+
+/* Cartesian A: free drift r += tau v. */
+static void or_A_cart(or_sim *s, double tau) {
+  size_t len = (size_t)s->P * s->N * 3;
+  for (size_t id = 0; id < len; ++id) s->x[id] += tau * s->v[id];
+}
+
+/* Cartesian O (App. D): every bead with tau = scale / (2 omega_n),
+ * v <- c1 v + c2 sqrt(P kB T / (fmass m mvv2e)) eta; the noise of bead k is
+ * keyed like mode k of the normal-mode method. */
+static void or_O_cart(or_sim *s, double wn, double dtO, uint32_t stream) {
+  int N = s->N, P = s->P;
+  double c1 = exp(-dtO / (s->scale / (2.0 * wn)));
+  double c2 = sqrt(1.0 - c1 * c1);
+  for (int k = 0; k < P; ++k)
+    for (int n = 0; n < N; ++n) {
+      double eta[3];
+      or_gauss3(s->seed, (uint32_t)n, (uint32_t)k, stream, (uint64_t)s->step, eta);
+      double sig = sqrt(P * OR_KB * s->T / (s->mass[n] * s->fmass * OR_MVV2E));
+      for (int a = 0; a < 3; ++a) {
+        size_t id = ((size_t)k * N + n) * 3 + a;
+        s->v[id] = c1 * s->v[id] + c2 * sig * eta[a];
+      }
     }
 }
 
 /* n steps.  BAOAB: B(h/2) A(h/2) O(h) A(h/2) [forces] B(h/2).
  *           OBABO: O(h/2) B(h/2) A(h) [forces] B(h/2) O(h/2).
- * The O sub-steps are skipped when thermostat == 0 (NVE).  Requires F, U,
- * vir to hold the forces at x on entry (call or_compute_forces once first). */
+ * The O sub-steps are skipped when thermostat == 0 (NVE); with fixcom the
+ * centre-of-mass velocity is removed at the end of every step.  Requires F, U, vir to
+ * hold the forces at x on entry (call or_compute_forces once first). */
 void or_run(or_sim *s, int64_t nsteps) {
   int N = s->N, P = s->P;
   size_t len = (size_t)P * N * 3;
@@ -448,9 +532,27 @@ void or_run(or_sim *s, int64_t nsteps) {
   double *Ft = (double *)malloc(sizeof(double) * len);
   or_nm_matrix(P, M);
   or_mode_omega(P, s->T, s->sp, omega);
+  for (int k = 0; k < P; ++k) omega[k] /= sqrt(or_mode_mu(s, k));   /* the mode's own frequency */
+  double wn = or_omega_n(P, s->T, s->sp);
   double h = s->dt;
   for (int64_t it = 0; it < nsteps; ++it) {
-    if (s->integrator == 0) {
+    if (s->method == 1) {
+      if (s->integrator == 0) {
+        or_B_cart(s, wn, 0.5 * h);
+        or_A_cart(s, 0.5 * h);
+        if (s->thermostat) or_O_cart(s, wn, h, 0u);
+        or_A_cart(s, 0.5 * h);
+        or_compute_forces(s);
+        or_B_cart(s, wn, 0.5 * h);
+      } else {
+        if (s->thermostat) or_O_cart(s, wn, 0.5 * h, 0u);
+        or_B_cart(s, wn, 0.5 * h);
+        or_A_cart(s, h);
+        or_compute_forces(s);
+        or_B_cart(s, wn, 0.5 * h);
+        if (s->thermostat) or_O_cart(s, wn, 0.5 * h, 1u);
+      }
+    } else if (s->integrator == 0) {
       or_B(s, M, Ft, 0.5 * h);
       or_to_nm(P, N, M, s->x, q);
       or_A(s, omega, q, 0.5 * h);
@@ -469,6 +571,7 @@ void or_run(or_sim *s, int64_t nsteps) {
       or_B(s, M, Ft, 0.5 * h);
       if (s->thermostat) or_O(s, omega, 0.5 * h, 1u);
     }
+    if (s->fixcom) or_fixcom(s);
     s->step += 1;
   }
   free(M); free(omega); free(q); free(Ft);
@@ -505,12 +608,20 @@ void or_estimators(const or_sim *s, or_estimates *e) {
   double Ktot = 0.0, Stot = 0.0, Utot = 0.0, virtot = 0.0;
   for (int k = 0; k < P; ++k) {
     double K = 0.0, S = 0.0;
+    double mu = or_mode_mu(s, k);
+    int km = (k + P - 1) % P, kp = (k + 1) % P;
     for (int n = 0; n < N; ++n) {
       double mm = s->mass[n] * OR_MVV2E;
       for (int a = 0; a < 3; ++a) {
         size_t id = ((size_t)k * N + n) * 3 + a;
-        K += 0.5 * mm * s->v[id] * s->v[id];                   /* output 1 */
-        S += 0.5 * mm * wn * wn * lam[k] * q[id] * q[id];      /* output 2 */
+        K += 0.5 * mm * mu * s->v[id] * s->v[id];              /* output 1 */
+        if (s->method == 0) {
+          S += 0.5 * mm * wn * wn * lam[k] * q[id] * q[id];    /* output 2 */
+        } else {                                                /* output 2, Cartesian form */
+          double dm = s->x[id] - s->x[((size_t)km * N + n) * 3 + a];
+          double dp = s->x[id] - s->x[((size_t)kp * N + n) * 3 + a];
+          S += 0.25 * mm * wn * wn * (dm * dm + dp * dp);
+        }
       }
     }
     e->K_mode[k] = K;
@@ -545,11 +656,20 @@ void or_estimators(const or_sim *s, or_estimates *e) {
         rcF += (s->x[id] - rc) * s->F[id];
       }
     }
+  /* m^(0) |v~^(0)|^2; Cartesian: v~^(0) = (1/sqrt(P)) sum_k v^(k) */
   double mv0 = 0.0, mvall = 0.0;
+  double mu0 = or_mode_mu(s, 0);
   for (int n = 0; n < N; ++n) {
-    double mm = s->mass[n] * OR_MVV2E;
+    double mm = s->mass[n] * OR_MVV2E * mu0;
     for (int a = 0; a < 3; ++a) {
-      mv0 += mm * s->v[(size_t)n * 3 + a] * s->v[(size_t)n * 3 + a];
+      double v0 = 0.0;
+      if (s->method == 0) {
+        v0 = s->v[(size_t)n * 3 + a];
+      } else {
+        for (int k = 0; k < P; ++k) v0 += s->v[((size_t)k * N + n) * 3 + a];
+        v0 /= sqrt((double)P);
+      }
+      mv0 += mm * v0 * v0;
     }
   }
   mvall = 2.0 * Ktot;
