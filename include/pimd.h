@@ -61,8 +61,15 @@ enum { PIMD_POT_HARMONIC = 0, PIMD_POT_WATERLIKE = 1 };
 enum { PIMD_THERMO_NONE = 0, PIMD_THERMO_PILE_L = 1 };
 /* Sec. III.C keyword "integrator" */
 enum { PIMD_BAOAB = 0, PIMD_OBABO = 1 };
-/* Sec. III.C keyword "method": only nmpimd (normal modes) is implemented */
-enum { PIMD_METHOD_NMPIMD = 0 };
+/* Sec. III.C keyword "method": nmpimd integrates in normal modes (App. B);
+ * pimd integrates bead by bead in Cartesian coordinates with the ring
+ * springs of Eq. (1) as forces (velocity-Verlet B and A, PILE_L O on every
+ * bead with tau = scale / (2 omega_n), App. D) */
+enum { PIMD_METHOD_NMPIMD = 0, PIMD_METHOD_PIMD = 1 };
+/* Sec. III.C keyword "fmmode": fictitious masses of the normal modes,
+ * m^(k) = m (physical) or lambda_k m (normal, k >= 1; the centroid keeps m
+ * because lambda_0 = 0).  Every internal mode then oscillates at omega_n. */
+enum { PIMD_FMMODE_PHYSICAL = 0, PIMD_FMMODE_NORMAL = 1 };
 /* arithmetic of the step and force kernels:
  *   FP64   every quantity in FP64.
  *   SPLIT  the ring-polymer centroid (position and centroid-mode velocity) in
@@ -75,12 +82,14 @@ enum { PIMD_PREC_FP64 = 0, PIMD_PREC_SPLIT = 1 };
 typedef struct pimd_handle pimd_handle;
 
 /* The physical system.  Copied at pimd_create; the pointers are host memory.
- *   mass      [n_atoms] physical masses (amu); fmmode physical (Sec. III.C).
+ *   mass      [n_atoms] physical masses (amu).
  *   pos       [P][n_atoms][3] bead positions (A), unwrapped.
- *   vel       [P][n_atoms][3] normal-mode velocities (A/ps) at integer time,
- *             or NULL: every mode is then drawn from N(0, P kB T/(m mvv2e))
- *             (the ring polymer is thermostatted at P T, Sec. IV.A) with
- *             noise stream 2 of the Philox keying described at pimd_create.
+ *   vel       [P][n_atoms][3] velocities (A/ps) at integer time: normal-mode
+ *             velocities (method nmpimd) or bead velocities (method pimd),
+ *             or NULL: every mode (bead) k is then drawn from
+ *             N(0, P kB T/(m^(k) mvv2e)) (the ring polymer is thermostatted
+ *             at P T, Sec. IV.A) with noise stream 2 of the Philox keying
+ *             described at pimd_create.
  *   potential PIMD_POT_HARMONIC: U = 1/2 m omega^2 |r|^2 per atom,
  *               ff[0] = omega (1/ps); box ignored (no pressure estimators).
  *             PIMD_POT_WATERLIKE: atoms 3m, 3m+1, 3m+2 are the O, H, H of
@@ -104,12 +113,18 @@ typedef struct {
  * thermostat PILE_L, integrator BAOAB, method nmpimd, seed 1, tau 1 ps,
  * scale 1, sp 1, fixcom 0 (the paper's default is "yes"; it couples
  * otherwise independent systems, so this library defaults to "no", as the
- * paper's own example input does), precision FP64.
+ * paper's own example input does), fmmode physical, fmass 1, precision FP64.
  *   tau     damping time of the centroid mode (ps), App. D.
- *   scale   tau_k = scale / (2 omega_k) for k >= 1, App. D.
+ *   scale   tau_k = scale / (2 Omega_k) for k >= 1 with Omega_k the mode's own
+ *           frequency omega_k / sqrt(m^(k) / m) (App. D); Cartesian method:
+ *           tau = scale / (2 omega_n) for every bead.
  *   sp      hbar -> sp * hbar; only omega_n changes (Eq. 2).  Must be > 0.
- *   fixcom  must be 0 (removal of the centroid centre-of-mass velocity is not
- *           implemented). */
+ *   fixcom  1: subtract the mass-weighted mean velocity of the centroid mode
+ *           (nmpimd) or of every bead (pimd) at the end of every step.
+ *   fmmode  PIMD_FMMODE_PHYSICAL or PIMD_FMMODE_NORMAL (nmpimd only).
+ *   fmass   > 0, multiplies every fictitious mass (m^(k) = fmass mu_k m).
+ * method pimd, fmmode normal, fmass != 1 and fixcom run in FP64 on a single
+ * handle (EINVAL with PIMD_PREC_SPLIT and in the batch engine and server). */
 typedef struct {
   int32_t thermostat;
   int32_t integrator;
@@ -120,13 +135,17 @@ typedef struct {
   double scale;
   double sp;
   int32_t fixcom;
-  int32_t reserved;
+  int32_t fmmode;
+  double fmass;
 } pimd_params;
 
 /* App. A outputs 1-10 at integer time, plus bookkeeping.
- *   K_mode[k]  output 1: 1/2 sum_i m_i |v~_i^(k)|^2 (eV), k < P
+ *   K_mode[k]  output 1: 1/2 sum_i m^(k)_i |v~_i^(k)|^2 (eV), k < P (method
+ *              pimd: 1/2 sum_i fmass m_i |v_i^(k)|^2 of bead k)
  *   S_mode[k]  output 2: 1/2 sum_i m_i omega_n^2 lambda_k |q~_i^(k)|^2 (eV),
- *              reading the printed "m omega_n" as m omega_n^2
+ *              reading the printed "m omega_n" as m omega_n^2 (method pimd:
+ *              the bead form 1/4 sum_i m_i omega_n^2 (|r^k - r^(k-1)|^2 +
+ *              |r^k - r^(k+1)|^2))
  *   U_bead[k]  output 3: potential energy of bead k (eV)
  *   H          output 4: sum_k (K + S + U)
  *   K_PR       output 5: 3 P N kB T / 2 - (1/P) sum 1/2 m omega_n^2 |r^k - r^(k+1)|^2
@@ -134,7 +153,8 @@ typedef struct {
  *   K_CV       output 7: 3 N kB T / 2 - (1/2P) sum (r - r_c).F
  *   P_PR       output 8: [3 P N kB T - (1/P) sum m omega_n^2 |dr|^2 + (1/P) sum_k Tr Xi^(k)] / 3V
  *   P_MD       output 9: sum_k [sum_i m |v~^(k)|^2 + Tr Xi^(k)] / 3V
- *   P_CV       output 10: [sum_i m |v~^(0)|^2 - sum (r - r_c).F + sum_k Tr Xi^(k)] / 3PV
+ *   P_CV       output 10: [sum_i m^(0) |v~^(0)|^2 - sum (r - r_c).F + sum_k Tr Xi^(k)] / 3PV
+ *              (method pimd: v~^(0) = sum_k v^(k) / sqrt(P))
  *   T_ring     2 sum_k K^(k) / (3 N P kB): equals P T in equilibrium (Sec. IV.A)
  * Pressures are eV/A^3 (NaN without a periodic box); volume in A^3;
  * vir_sum = sum_k Tr Xi^(k) (eV). */
@@ -179,8 +199,10 @@ const char *pimd_last_error(void);
  * 1 = second O of OBABO, 2 = initial velocities.
  * Validation (EINVAL): P outside 1..128, T <= 0, dt <= 0, n_atoms <= 0, NULL
  * mass/pos, non-positive mass, unknown potential/thermostat/integrator/
- * method/precision, tau <= 0 or scale <= 0 with PILE_L, sp <= 0,
- * fixcom != 0, water-like n_atoms not a multiple of 3 or a box edge <= 2 rc.
+ * method/precision/fmmode, tau <= 0 or scale <= 0 with PILE_L, sp <= 0,
+ * fmass <= 0, fixcom not 0 or 1, fmmode normal with method pimd, method pimd /
+ * fmmode normal / fmass != 1 / fixcom with PIMD_PREC_SPLIT, water-like
+ * n_atoms not a multiple of 3 or a box edge <= 2 rc.
  * Computes the forces of the initial positions before returning. */
 pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, double dt, double gamma0,
                         const pimd_params *params, void *stream, pimd_handle **out);
@@ -190,8 +212,10 @@ pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, double dt, 
  * [forces] B(h/2); OBABO = O(h/2) B(h/2) A(h) [forces] B(h/2) O(h/2), where
  * B kicks v~ with the normal-mode forces M F (Sec. IV.A), A is the exact
  * harmonic flow of each free-ring-polymer mode (i-PI's equations of motion)
- * and O is PILE_L (App. D).  On return of the queued work the state is at
- * integer time. */
+ * and O is PILE_L (App. D); method pimd: B kicks the bead velocities with the
+ * forces plus the ring springs, A is the free drift.  With fixcom the
+ * centre-of-mass velocity is removed at the end of every step.  On return of
+ * the queued work the state is at integer time. */
 pimd_status pimd_step(pimd_handle *h, int64_t n);
 
 /* Wait for the handle's queued work; returns any latched error. */
@@ -203,7 +227,8 @@ pimd_status pimd_sync(pimd_handle *h);
 pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out);
 
 /* Copy the state to host arrays: x [P][N][3] Cartesian positions (A), v_nm
- * [P][N][3] normal-mode velocities (A/ps), *step the step counter.  Any of
+ * [P][N][3] normal-mode velocities (A/ps; bead velocities with method pimd),
+ * *step the step counter.  Any of
  * the three pointers may be NULL.  Synchronises the handle's stream. */
 pimd_status pimd_get_state(pimd_handle *h, double *x, double *v_nm, int64_t *step);
 

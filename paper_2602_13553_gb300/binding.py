@@ -23,6 +23,9 @@ THERMO_PILE_L = 1
 BAOAB = 0
 OBABO = 1
 METHOD_NMPIMD = 0
+METHOD_PIMD = 1
+FMMODE_PHYSICAL = 0
+FMMODE_NORMAL = 1
 PREC_FP64 = 0
 PREC_SPLIT = 1
 MAX_BEADS = 128
@@ -55,7 +58,8 @@ class Params(ctypes.Structure):
         ("method", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("tau", ctypes.c_double), ("scale", ctypes.c_double), ("sp", ctypes.c_double),
-        ("fixcom", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("fixcom", ctypes.c_int32), ("fmmode", ctypes.c_int32),
+        ("fmass", ctypes.c_double),
     ]
 
 
@@ -195,8 +199,10 @@ def reset_allocator() -> None:
 class Simulation:
     """One ring-polymer system on the GPU (a pimd_handle).
 
-    x0: [P][N][3] positions (A); v0: [P][N][3] normal-mode velocities or None
-    (thermal draw).  Keyword arguments map onto pimd_params fields.
+    x0: [P][N][3] positions (A); v0: [P][N][3] velocities -- normal-mode
+    (method nmpimd) or bead (method pimd) -- or None (thermal draw).  Keyword
+    arguments map onto pimd_params fields (thermostat, integrator, method,
+    precision, seed, tau, scale, sp, fixcom, fmmode, fmass).
     """
 
     def __init__(self, x0, mass, *, T, dt, potential=POT_HARMONIC, ff=(0.0,), box=(0.0, 0.0, 0.0),

@@ -40,7 +40,8 @@ namespace pimd {
 
 cudaError_t launch_pna_to_nap(const double *src, double *dst, int N, int P, cudaStream_t s);
 cudaError_t launch_nap_to_pna(const double *src, double *dst, int N, int P, cudaStream_t s);
-cudaError_t launch_thermal_v(double *v, const double *sigv, uint64_t seed, int N, int P, cudaStream_t s);
+cudaError_t launch_thermal_v(double *v, const double *sigv, const double *imu, uint64_t seed, int N, int P,
+                             cudaStream_t s);
 cudaError_t launch_compress_split(const SplitStepArgs &a, const double *x, const double *v, cudaStream_t s);
 cudaError_t launch_expand_split(const SplitStepArgs &a, const float *F, double *x, double *v, double *Fd,
                                 cudaStream_t s);
@@ -2014,6 +2015,7 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   pimd_params prm;
   pimd_status st = validate_create(sys, P, T, dt, gamma0, params, &prm);
   if (st != PIMD_OK) return st;
+  if ((st = require_default_keywords(prm, "the batch engine")) != PIMD_OK) return st;
   if (sys->potential != PIMD_POT_WATERLIKE)
     return fail(PIMD_EINVAL, "the batch engine runs water-like systems");
   if (sys->n_atoms / 3 > kBatchMaxMol)
@@ -2178,7 +2180,7 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
       e = cudaMemcpyAsync(b->stg_t, sys->vel, len * sizeof(double), cudaMemcpyHostToDevice, b->stream);
       if (e == cudaSuccess) e = launch_pna_to_nap(b->stg_t, b->stg_v, N, P, b->stream);
     } else {
-      e = launch_thermal_v(b->stg_v, d.sigv, d.seed, N, P, b->stream);
+      e = launch_thermal_v(b->stg_v, d.sigv, nullptr, d.seed, N, P, b->stream);
     }
   }
   if (e == cudaSuccess) e = launch_compress_split(replica_split_args(r), b->stg_x, b->stg_v, b->stream);
@@ -2667,6 +2669,7 @@ extern "C" pimd_status pimd_batch_submit(pimd_server *s, const pimd_system *sys,
   pimd_params prm;
   pimd_status st = validate_create(sys, P, T, dt, gamma0, params, &prm);
   if (st != PIMD_OK) return st;
+  if ((st = require_default_keywords(prm, "the server")) != PIMD_OK) return st;
   if (sys->potential != PIMD_POT_WATERLIKE) return fail(PIMD_EINVAL, "the server runs water-like systems");
   if (nsteps < 0) return fail(PIMD_EINVAL, "nsteps must be >= 0");
   const size_t bytes = pimd_batch_replica_bytes(sys->n_atoms, P);

@@ -25,8 +25,9 @@ cudaError_t launch_step(const StepArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_close(const StepArgs &a, int threads, cudaStream_t s);
 cudaError_t launch_advance(int64_t *step, int n, cudaStream_t s);
 cudaError_t launch_to_f32(const double *src, float *dst, size_t n, cudaStream_t s);
-cudaError_t launch_thermal_v(double *v, const double *sigv, uint64_t seed, int N, int P,
+cudaError_t launch_thermal_v(double *v, const double *sigv, const double *imu, uint64_t seed, int N, int P,
                              cudaStream_t s);
+cudaError_t launch_fixcom(const FixcomArgs &a, cudaStream_t s);
 cudaError_t launch_pna_to_nap(const double *src, double *dst, int N, int P, cudaStream_t s);
 cudaError_t launch_nap_to_pna(const double *src, double *dst, int N, int P, cudaStream_t s);
 cudaError_t launch_force_harmonic(const ForceArgs &a, cudaStream_t s);
@@ -125,6 +126,8 @@ extern "C" void pimd_params_default(pimd_params *p) {
   p->scale = 1.0;
   p->sp = 1.0;
   p->fixcom = 0;
+  p->fmmode = PIMD_FMMODE_PHYSICAL;
+  p->fmass = 1.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -132,7 +135,8 @@ extern "C" void pimd_params_default(pimd_params *p) {
 // ---------------------------------------------------------------------------
 struct pimd_handle {
   int N = 0, P = 0, potential = 0, nmol = 0, integrator = 0, thermostat = 0, precision = 0;
-  double T = 0, dt = 0, tau = 0, scale = 0, sp = 0;
+  int method = 0, fixcom = 0;
+  double T = 0, dt = 0, tau = 0, scale = 0, sp = 0, fmass = 1.0;
   uint64_t seed = 0;
   double box[3] = {0, 0, 0};
   double ff[8] = {0};
@@ -153,7 +157,7 @@ struct pimd_handle {
   double tA = 0.0, c1_0 = 0.0, c2_0 = 0.0;
   double *inv_mm = nullptr, *sigv = nullptr, *mass_mm = nullptr, *kspring = nullptr;
   double *M = nullptr, *Mt = nullptr, *cA = nullptr, *sA = nullptr, *wsA = nullptr;
-  double *c1 = nullptr, *c2 = nullptr, *lam = nullptr;
+  double *c1 = nullptr, *c2 = nullptr, *lam = nullptr, *mu = nullptr, *imu = nullptr;
   double *Upart = nullptr, *Wpart = nullptr;
   int nblk_force = 0;
   double *cref = nullptr, *ccur = nullptr, *blkmax = nullptr;
@@ -291,12 +295,16 @@ static StepArgs step_args(pimd_handle *h) {
   a.N = h->N;
   a.P = h->P;
   a.A = h->A_step;
-  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam};
+  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam, h->mu, h->imu};
   a.inv_mm = h->inv_mm;
   a.sigv = h->sigv;
   a.x = h->x;
   a.v = h->v;
   a.F = h->F;
+  a.method = h->method;
+  a.ifmass = 1.0 / h->fmass;
+  a.wn2 = h->wn * h->wn;
+  a.mass_mm = h->mass_mm;
   a.step = h->d_step;
   a.step_off = 0;
   const bool water = h->potential == PIMD_POT_WATERLIKE;
@@ -507,7 +515,28 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
   a.kick = first ? 0.5 * h->dt : h->dt;
   pimd_status st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a, h->threads_step, h->stream); });
   if (st != PIMD_OK) return st;
-  return enqueue_forces(h, false, true);
+  st = enqueue_forces(h, false, true);
+  if (st != PIMD_OK || !h->fixcom) return st;
+  // fixcom at the end of this step: the next kernel (step or close) applies
+  // this step's closing B(h/2) (and O(h/2)); remove the momentum it will leave
+  FixcomArgs f;
+  f.N = h->N;
+  f.P = h->P;
+  f.method = h->method;
+  f.mass_mm = h->mass_mm;
+  f.x = h->x;
+  f.F = h->F;
+  f.v = h->v;
+  f.half = 0.5 * h->dt;
+  f.imu0 = 1.0 / h->fmass;   // mu_0 = fmass in both methods
+  f.wn2 = h->wn * h->wn;
+  f.obabo_thermo = h->integrator == PIMD_OBABO && h->thermostat == PIMD_THERMO_PILE_L;
+  f.seed = h->seed;
+  f.step = h->d_step;
+  f.c1 = h->c1;
+  f.c2 = h->c2;
+  f.sigv = h->sigv;
+  return enqueue(h, PIMD_KIND_OTHER, 1, [&] { return launch_fixcom(f, h->stream); });
 }
 
 static pimd_status enqueue_close(pimd_handle *h) {
@@ -612,6 +641,8 @@ static void carve(pimd_handle *h, Carver &c) {
   h->c1 = c.take<double>(P);
   h->c2 = c.take<double>(P);
   h->lam = c.take<double>(P);
+  h->mu = c.take<double>(P);
+  h->imu = c.take<double>(P);
   // rows of per-bead U / Tr Xi sums: one per molecule (water) or per block
   h->nblk_force = h->potential == PIMD_POT_WATERLIKE ? h->nmol : force_blocks(h->N, P);
   h->Upart = c.take<double>((size_t)h->nblk_force * P);
@@ -654,7 +685,7 @@ static pimd_status upload_state(pimd_handle *h, const double *x, const double *v
     CK(cudaMemcpyAsync(h->tmp, v, bytes, cudaMemcpyHostToDevice, h->stream));
     CK(launch_pna_to_nap(h->tmp, h->v, h->N, h->P, h->stream));
   } else {
-    CK(launch_thermal_v(h->v, h->sigv, h->seed, h->N, h->P, h->stream));
+    CK(launch_thermal_v(h->v, h->sigv, h->imu, h->seed, h->N, h->P, h->stream));
   }
   if (h->precision == PIMD_PREC_SPLIT) CK(launch_compress_split(split_args(h), h->x, h->v, h->stream));
   return PIMD_OK;
@@ -680,11 +711,21 @@ pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double 
     return fail(PIMD_EINVAL, "unknown thermostat %d", prm.thermostat);
   if (prm.integrator != PIMD_BAOAB && prm.integrator != PIMD_OBABO)
     return fail(PIMD_EINVAL, "unknown integrator %d", prm.integrator);
-  if (prm.method != PIMD_METHOD_NMPIMD) return fail(PIMD_EINVAL, "only method nmpimd is implemented");
+  if (prm.method != PIMD_METHOD_NMPIMD && prm.method != PIMD_METHOD_PIMD)
+    return fail(PIMD_EINVAL, "unknown method %d", prm.method);
   if (prm.precision != PIMD_PREC_FP64 && prm.precision != PIMD_PREC_SPLIT)
     return fail(PIMD_EINVAL, "unknown precision %d", prm.precision);
-  if (prm.fixcom != 0) return fail(PIMD_EINVAL, "fixcom is not implemented");
+  if (prm.fixcom != 0 && prm.fixcom != 1) return fail(PIMD_EINVAL, "fixcom must be 0 or 1");
+  if (prm.fmmode != PIMD_FMMODE_PHYSICAL && prm.fmmode != PIMD_FMMODE_NORMAL)
+    return fail(PIMD_EINVAL, "unknown fmmode %d", prm.fmmode);
+  if (prm.fmmode == PIMD_FMMODE_NORMAL && prm.method == PIMD_METHOD_PIMD)
+    return fail(PIMD_EINVAL, "fmmode normal applies to normal modes (method nmpimd)");
+  if (!(prm.fmass > 0.0) || !std::isfinite(prm.fmass)) return fail(PIMD_EINVAL, "fmass must be > 0");
   if (!(prm.sp > 0.0)) return fail(PIMD_EINVAL, "sp must be > 0");
+  if (prm.precision == PIMD_PREC_SPLIT) {
+    pimd_status ks = require_default_keywords(prm, "split precision");
+    if (ks != PIMD_OK) return ks;
+  }
   if (gamma0 > 0.0) {
     const double tau = 1.0 / gamma0;
     if (params && std::fabs(params->tau - tau) > 1e-12 * tau)
@@ -713,6 +754,13 @@ pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double 
   return PIMD_OK;
 }
 
+pimd_status require_default_keywords(const pimd_params &prm, const char *where) {
+  if (prm.method != PIMD_METHOD_NMPIMD || prm.fmmode != PIMD_FMMODE_PHYSICAL || prm.fmass != 1.0 ||
+      prm.fixcom != 0)
+    return fail(PIMD_EINVAL, "%s implements method nmpimd, fmmode physical, fmass 1 and fixcom 0", where);
+  return PIMD_OK;
+}
+
 void build_tables(int P, double T, double dt, const pimd_params &prm, HostTables &t) {
   build_nm_matrix(P, t.M);
   t.Mt.assign((size_t)P * P, 0.0);
@@ -728,10 +776,18 @@ void build_tables(int P, double T, double dt, const pimd_params &prm, HostTables
   t.c1.resize(P);
   t.c2.resize(P);
   t.lam.resize(P);
+  t.mu.resize(P);
+  t.imu.resize(P);
+  const bool cart = prm.method == PIMD_METHOD_PIMD;
   for (int k = 0; k < P; ++k) {
     const double s = std::sin(kPi * k / P);
     t.lam[k] = 4.0 * s * s;                               // Eq. (A2)
-    const double wk = 2.0 * t.wn * std::fabs(s);          // w_k = sqrt(lam_k) w_n
+    // fictitious mass m^(k) = mu_k m (Sec. III.C fmmode, fmass; lambda_0 = 0
+    // leaves the centroid at fmass m)
+    t.mu[k] = (!cart && prm.fmmode == PIMD_FMMODE_NORMAL && k > 0) ? prm.fmass * t.lam[k] : prm.fmass;
+    t.imu[k] = 1.0 / t.mu[k];
+    // the mode's own frequency in the free ring polymer: w_k / sqrt(mu_k)
+    const double wk = 2.0 * t.wn * std::fabs(s) / std::sqrt(t.mu[k]);
     if (k == 0 || wk == 0.0) {
       t.cA[k] = 1.0;
       t.sA[k] = t.tA;
@@ -741,9 +797,10 @@ void build_tables(int P, double T, double dt, const pimd_params &prm, HostTables
       t.sA[k] = std::sin(wk * t.tA) / wk;
       t.wsA[k] = wk * std::sin(wk * t.tA);
     }
-    const double tauk = (k == 0) ? prm.tau : prm.scale / (2.0 * wk);
+    // App. D: tau_0 = tau, tau_k = scale / (2 w_k); Cartesian: scale / (2 w_n) for every bead
+    const double tauk = cart ? prm.scale / (2.0 * t.wn) : ((k == 0) ? prm.tau : prm.scale / (2.0 * wk));
     t.c1[k] = std::exp(-t.tO / tauk);
-    t.c2[k] = std::sqrt(1.0 - t.c1[k] * t.c1[k]);
+    t.c2[k] = std::sqrt(1.0 - t.c1[k] * t.c1[k]) / std::sqrt(t.mu[k]);   // noise of sqrt(P kB T / (m^(k) mvv2e))
   }
 }
 }  // namespace pimd
@@ -767,6 +824,9 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   h->integrator = prm.integrator;
   h->thermostat = prm.thermostat;
   h->precision = prm.precision;
+  h->method = prm.method;
+  h->fixcom = prm.fixcom;
+  h->fmass = prm.fmass;
   h->T = T;
   h->dt = dt;
   h->tau = prm.tau;
@@ -831,7 +891,8 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   };
   if ((st = up(h->M, M)) || (st = up(h->Mt, Mt)) || (st = up(h->cA, cA)) || (st = up(h->sA, sA)) ||
       (st = up(h->wsA, wsA)) || (st = up(h->c1, c1v)) || (st = up(h->c2, c2v)) ||
-      (st = up(h->lam, lam)) || (st = up(h->inv_mm, inv_mm)) || (st = up(h->sigv, sigv)) ||
+      (st = up(h->lam, lam)) || (st = up(h->mu, tb.mu)) || (st = up(h->imu, tb.imu)) ||
+      (st = up(h->inv_mm, inv_mm)) || (st = up(h->sigv, sigv)) ||
       (st = up(h->mass_mm, mass_mm)) || (st = up(h->kspring, ksp))) {
     release(h);
     return st;
@@ -922,7 +983,8 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   a.N = h->N;
   a.P = P;
   a.A = h->A_est;
-  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam};
+  a.method = h->method;
+  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam, h->mu, h->imu};
   a.mass_mm = h->mass_mm;
   a.x = h->x;
   a.v = h->v;

@@ -100,8 +100,10 @@ struct ModeTables {
   const double *sA;    // [P] sin(w_k tA)/w_k   (tA for k = 0)
   const double *wsA;   // [P] w_k sin(w_k tA)   (0 for k = 0)
   const double *c1;    // [P] exp(-tO / tau_k)
-  const double *c2;    // [P] sqrt(1 - c1^2)
+  const double *c2;    // [P] sqrt(1 - c1^2) / sqrt(mu_k)  (noise of mode k)
   const double *lam;   // [P] lambda_k (Eq. A2)
+  const double *mu;    // [P] fictitious-mass factor mu_k: m^(k) = mu_k m (fmmode, fmass)
+  const double *imu;   // [P] 1 / mu_k
 };
 
 struct StepArgs {
@@ -125,6 +127,33 @@ struct StepArgs {
   int first;                   // OBABO: 1 if no B+O of a previous step is pending
   int thermo;                  // 1 PILE_L
   uint64_t seed;
+  // Cartesian method (v holds bead velocities): springs -m w_n^2 (2 x_k -
+  // x_{k-1} - x_{k+1}) join the forces, bead masses fmass m; mt.c1/c2 hold
+  // the one bead friction (tau = scale / (2 w_n)) and its noise factor
+  int method;                  // 0 nmpimd, 1 pimd (Cartesian)
+  double ifmass;               // 1 / fmass
+  double wn2;                  // omega_n^2
+  const double *mass_mm;       // [N] m mvv2e
+};
+
+// fixcom: remove the centre-of-mass velocity of the centroid mode (normal
+// modes) or of every bead (Cartesian) as it will stand after the closing
+// B(h/2) that the next kernel applies (the removal belongs at the end of the
+// step; subtracting its predicted value first is the same linear operation).
+struct FixcomArgs {
+  int N, P, method;
+  const double *mass_mm;       // [N] m mvv2e
+  const double *x, *F;         // [N][3][P]
+  double *v;                   // [N][3][P]
+  double half;                 // h/2
+  double imu0;                 // 1 / mu_0 (normal modes) or 1 / fmass (Cartesian)
+  double wn2;                  // omega_n^2 (Cartesian springs)
+  // OBABO with PILE_L: the closing O(h/2) follows the kick, v <- c1 v + c2 sigv eta
+  int obabo_thermo;
+  uint64_t seed;
+  const int64_t *step;         // device counter, already advanced past this step
+  const double *c1, *c2;       // [P] O tables (c2 includes 1 / sqrt(mu_k))
+  const double *sigv;          // [N] sqrt(P kB T / (m mvv2e))
 };
 
 struct ForceArgs {
@@ -197,6 +226,7 @@ struct SplitForceArgs {
 
 struct EstArgs {
   int N, P, A;
+  int method;                  // 0 nmpimd, 1 pimd (Cartesian: v holds bead velocities)
   ModeTables mt;
   const double *mass_mm;       // [N] m mvv2e
   const double *x, *v, *F;

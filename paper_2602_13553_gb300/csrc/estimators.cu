@@ -70,9 +70,30 @@ __global__ void __launch_bounds__(256) k_est_f64(EstArgs a) {
       const double mm = __ldg(a.mass_mm + i);
       const double v0 = vv[k], v1 = vv[P + k], v2 = vv[2 * P + k];
       const double v2s = v0 * v0 + v1 * v1 + v2 * v2;
-      kk = 0.5 * mm * v2s;
-      ss = 0.5 * mm * a.wn2 * __ldg(a.mt.lam + k) * (q0 * q0 + q1 * q1 + q2 * q2);
-      if (k == 0) mv0 += mm * v2s;
+      kk = 0.5 * mm * __ldg(a.mt.mu + k) * v2s;   // fictitious mass m^(k)
+      if (a.method == 0) {
+        ss = 0.5 * mm * a.wn2 * __ldg(a.mt.lam + k) * (q0 * q0 + q1 * q1 + q2 * q2);
+        if (k == 0) mv0 += mm * __ldg(a.mt.mu) * v2s;
+      } else {
+        // Cartesian bead form of output 2, and v~^(0) = sum_k v^(k) / sqrt(P)
+        const int km = k == 0 ? P - 1 : k - 1, kp = k == P - 1 ? 0 : k + 1;
+        double s2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double *xr = xx + d * P;
+          const double dm = xr[k] - xr[km], dp = xr[k] - xr[kp];
+          s2 += dm * dm + dp * dp;
+        }
+        ss = 0.25 * mm * a.wn2 * s2;
+        if (k == 0) {
+          double w2 = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            double sv = 0.0;
+            for (int j = 0; j < P; ++j) sv += vv[d * P + j];
+            w2 += sv * sv;
+          }
+          mv0 += mm * __ldg(a.mt.mu) * w2 / P;
+        }
+      }
       // bead j = k
       const double x0 = xx[k], x1 = xx[P + k], x2 = xx[2 * P + k];
       const double f0 = ff[k], f1 = ff[P + k], f2 = ff[2 * P + k];

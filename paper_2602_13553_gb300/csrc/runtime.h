@@ -17,6 +17,7 @@ struct HostTables {
   std::vector<double> cA, sA, wsA;      // exact A step of length tA
   std::vector<double> c1, c2;           // O step of length tO
   std::vector<double> lam;              // Eq. (A2)
+  std::vector<double> mu, imu;          // fictitious-mass factors m^(k) / m and their inverses
   double wn = 0.0, tA = 0.0, tO = 0.0;  // Eq. (2), A and O durations
 };
 
@@ -26,6 +27,10 @@ void build_tables(int P, double T, double dt, const pimd_params &prm, HostTables
 // fills *prm with the effective parameters (defaults, gamma0 -> tau).
 pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double dt, double gamma0,
                             const pimd_params *params, pimd_params *prm);
+
+// EINVAL unless the keywords are the ones the split-precision, batch and
+// server paths implement (method nmpimd, fmmode physical, fmass 1, fixcom 0).
+pimd_status require_default_keywords(const pimd_params &prm, const char *where);
 
 // Device memory through the optional pimd_set_allocator hooks (else cudaMalloc).
 struct DevAllocator {

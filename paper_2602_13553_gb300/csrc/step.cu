@@ -17,6 +17,8 @@
 // centroid drift since the last neighbour-list build and the bead spread.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace pimd {
 
 __device__ __forceinline__ void rotate(double &q, double &v, double c, double s_over_w, double w_s) {
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
     const double f = fa + fb;
     double q = qa + qb;
     double v = sV[task];
-    const double im = __ldg(a.inv_mm + i);
+    const double im = __ldg(a.inv_mm + i) * __ldg(a.mt.imu + k);   // 1 / (m^(k) mvv2e)
     const double cA = __ldg(a.mt.cA + k), sA = __ldg(a.mt.sA + k), wsA = __ldg(a.mt.wsA + k);
     const double c1 = __ldg(a.mt.c1 + k), c2s = __ldg(a.mt.c2 + k) * __ldg(a.sigv + i);
     if (a.integrator == 0) {
@@ -192,12 +194,201 @@ __global__ void __launch_bounds__(256) k_close_f64(StepArgs a) {
       fb = fma(__ldg(Mt + (j + 1) * P + k), fx[j + 1], fb);
     }
     if (j < P) fa = fma(__ldg(Mt + j * P + k), fx[j], fa);
-    double v = fma(a.half * __ldg(a.inv_mm + i), fa + fb, a.v[base + task]);
+    double v = fma(a.half * (__ldg(a.inv_mm + i) * __ldg(a.mt.imu + k)), fa + fb, a.v[base + task]);
     if (a.integrator == 1 && a.thermo) {
       const double c1 = __ldg(a.mt.c1 + k), c2s = __ldg(a.mt.c2 + k) * __ldg(a.sigv + i);
       v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step, d));
     }
     a.v[base + task] = v;
+  }
+}
+
+// ---- Cartesian method (Sec. III.C "method pimd") ---------------------------
+// Bead velocities v; the springs of Eq. (1) enter the kicks as forces
+// F_s^(k) = -m w_n^2 (2 x^k - x^(k-1) - x^(k+1)) (cyclic); A is the free drift
+// x += tA v; O (App. D) acts on every bead with one friction.  Thread task
+// t = (al * 3 + d) * P + k as in the normal-mode kernel.
+__device__ __forceinline__ double spring_force(const double *row, int k, int P, double mmw2) {
+  const double xm = row[k == 0 ? P - 1 : k - 1], xp = row[k == P - 1 ? 0 : k + 1];
+  return -mmw2 * (2.0 * row[k] - xm - xp);
+}
+
+__global__ void __launch_bounds__(256) k_step_cart_f64(StepArgs a) {
+  extern __shared__ double sm[];
+  const int P = a.P;
+  const int tileLen = a.A * 3 * P;
+  double *sX = sm;               // positions at the start of the step
+  double *sN = sX + tileLen;     // new positions
+  double *sC = sN + tileLen;     // [A][3] new centroids (water skin check)
+  __shared__ double sred[2][8];
+  const int tile0 = blockIdx.x * a.A;
+  const int na = min(a.A, a.N - tile0);
+  const int len = na * 3 * P;
+  const size_t base = (size_t)tile0 * 3 * P;
+  for (int t = threadIdx.x; t < len; t += blockDim.x) sX[t] = a.x[base + t];
+  __syncthreads();
+  const uint64_t step = (uint64_t)(*a.step + a.step_off);
+  const double c1 = __ldg(a.mt.c1), c2 = __ldg(a.mt.c2);
+  for (int task = threadIdx.x; task < len; task += blockDim.x) {
+    const int k = task % P;
+    const int r = task / P;
+    const int d = r % 3;
+    const int i = tile0 + r / 3;
+    const double f = a.F[base + task] + spring_force(sX + r * P, k, P, __ldg(a.mass_mm + i) * a.wn2);
+    const double im = __ldg(a.inv_mm + i) * a.ifmass;
+    const double c2s = c2 * __ldg(a.sigv + i);
+    double v = a.v[base + task];
+    double x = sX[task];
+    if (a.integrator == 0) {
+      v = fma(a.kick * im, f, v);
+      x = fma(a.half, v, x);
+      if (a.thermo) v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+      x = fma(a.half, v, x);
+    } else {
+      const double kb = a.half * im;
+      if (!a.first) {
+        v = fma(kb, f, v);
+        if (a.thermo) v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, d));
+      }
+      if (a.thermo) v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+      v = fma(kb, f, v);
+      x = fma(2.0 * a.half, v, x);
+    }
+    a.v[base + task] = v;
+    a.x[base + task] = x;
+    if (a.x32) a.x32[base + task] = (float)x;
+    sN[task] = x;
+  }
+  if (!a.blkmax) return;
+  // neighbour-list skin check of the oxygens: centroid = bead mean
+  __syncthreads();
+  for (int t = threadIdx.x; t < na * 3; t += blockDim.x) {
+    const double *row = sN + t * P;
+    double sum = 0.0;
+    for (int j = 0; j < P; ++j) sum += row[j];
+    sC[t] = sum / P;
+  }
+  __syncthreads();
+  double vdisp = 0.0, vdev = 0.0;
+  for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
+    const int al = t / P, k = t % P;
+    const int i = tile0 + al;
+    if (i % 3) continue;
+    const double c0 = sC[al * 3], cc1 = sC[al * 3 + 1], cc2 = sC[al * 3 + 2];
+    const double *xs = sN + al * 3 * P;
+    const double e0 = xs[k] - c0, e1 = xs[P + k] - cc1, e2 = xs[2 * P + k] - cc2;
+    vdev = fmax(vdev, e0 * e0 + e1 * e1 + e2 * e2);
+    if (k == 0) {
+      const int m = i / 3;
+      const double g0 = c0 - a.cref[3 * m], g1 = cc1 - a.cref[3 * m + 1], g2 = cc2 - a.cref[3 * m + 2];
+      vdisp = fmax(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
+      a.ccur[3 * m] = c0;
+      a.ccur[3 * m + 1] = cc1;
+      a.ccur[3 * m + 2] = cc2;
+    }
+  }
+  vdisp = warp_max(vdisp);
+  vdev = warp_max(vdev);
+  if ((threadIdx.x & 31) == 0) {
+    sred[0][threadIdx.x >> 5] = vdisp;
+    sred[1][threadIdx.x >> 5] = vdev;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double mx = 0.0;
+    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) mx = fmax(mx, sred[threadIdx.x][w]);
+    a.blkmax[2 * blockIdx.x + threadIdx.x] = (mx == mx) ? sqrt(mx) : 1e300;
+  }
+}
+
+// Closing kick of a call, Cartesian: B(h/2) with the springs (and the final
+// O(h/2) of OBABO).
+__global__ void __launch_bounds__(256) k_close_cart_f64(StepArgs a) {
+  const int P = a.P;
+  const size_t total = (size_t)a.N * 3 * P;
+  const uint64_t step = (uint64_t)(*a.step + a.step_off);
+  const double c1 = __ldg(a.mt.c1), c2 = __ldg(a.mt.c2);
+  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t % P);
+    const size_t r = t / P;
+    const int d = (int)(r % 3);
+    const int i = (int)(r / 3);
+    const double f = a.F[t] + spring_force(a.x + r * P, k, P, __ldg(a.mass_mm + i) * a.wn2);
+    double v = fma(a.half * (__ldg(a.inv_mm + i) * a.ifmass), f, a.v[t]);
+    if (a.integrator == 1 && a.thermo)
+      v = fma(c1, v, c2 * __ldg(a.sigv + i) * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step, d));
+    a.v[t] = v;
+  }
+}
+
+// fixcom: one block; deterministic sums (fixed per-thread strides, then a
+// fixed tree) of m v, F and (Cartesian) m x per (bead or centroid mode,
+// component), then v -= u on every atom.
+__device__ double block_sum(double v, double *red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_fixcom_f64(FixcomArgs a) {
+  __shared__ double red[256];
+  __shared__ double sp[3 * kMaxBeads], sf[3 * kMaxBeads], sx[3 * kMaxBeads], u[3 * kMaxBeads];
+  const int P = a.P, N = a.N;
+  const int nb = a.method == 0 ? 1 : P;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) m += a.mass_mm[i];
+  const double msum = block_sum(m, red);
+  for (int kc = 0; kc < 3 * nb; ++kc) {
+    const int k = kc / 3, c = kc % 3;
+    double pv = 0.0, pf = 0.0, px = 0.0, pn = 0.0;
+    const uint64_t s = (uint64_t)(*a.step - 1);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const size_t row = ((size_t)i * 3 + c) * P;
+      const double mm = a.mass_mm[i];
+      pv = fma(mm, a.v[row + k], pv);
+      if (a.obabo_thermo)
+        pn = fma(mm * a.sigv[i], gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, s, c), pn);
+      if (a.method == 0) {
+        double fs = 0.0;   // sqrt(P) F~_0 = sum over beads
+        for (int j = 0; j < P; ++j) fs += a.F[row + j];
+        pf += fs;
+      } else {
+        pf += a.F[row + k];
+        px = fma(mm, a.x[row + k], px);
+      }
+    }
+    pv = block_sum(pv, red);
+    pf = block_sum(pf, red);
+    px = block_sum(px, red);
+    pn = block_sum(pn, red);
+    if (threadIdx.x == 0) {
+      // the closing O(h/2) scales by c1 and adds c2 sigv eta: remove its mean too
+      sp[kc] = a.obabo_thermo ? pv + a.c2[k] * pn / a.c1[k] : pv;
+      sf[kc] = a.method == 0 ? pf / sqrt((double)P) : pf;
+      sx[kc] = px;
+    }
+  }
+  __syncthreads();
+  for (int kc = threadIdx.x; kc < 3 * nb; kc += blockDim.x) {
+    const int k = kc / 3, c = kc % 3;
+    double f = sf[kc];
+    if (a.method == 1) {
+      const int km = k == 0 ? P - 1 : k - 1, kp = k == P - 1 ? 0 : k + 1;
+      f -= a.wn2 * (2.0 * sx[kc] - sx[3 * km + c] - sx[3 * kp + c]);
+    }
+    u[kc] = fma(a.half * a.imu0, f, sp[kc]) / msum;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N * 3 * nb; t += blockDim.x) {
+    const int k = t % nb;
+    const int ic = t / nb;
+    a.v[(size_t)ic * P + k] -= u[3 * k + ic % 3];
   }
 }
 
@@ -210,14 +401,15 @@ __global__ void k_advance(int64_t *step, int n) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *step += n;
 }
 
-// Initial normal-mode velocities ~ N(0, P kB T / (m mvv2e)), noise stream 2.
-__global__ void k_thermal_v(double *v, const double *sigv, uint64_t seed, int N, int P) {
+// Initial velocities of mode (or bead) k ~ N(0, P kB T / (mu_k m mvv2e)),
+// noise stream 2.
+__global__ void k_thermal_v(double *v, const double *sigv, const double *imu, uint64_t seed, int N, int P) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * P) return;
   const int i = t / P, k = t % P;
   double e0, e1, e2;
   gauss3(seed, (uint32_t)i, (uint32_t)k, kStreamInit, 0ull, e0, e1, e2);
-  const double s = sigv[i];
+  const double s = imu ? sigv[i] * sqrt(imu[k]) : sigv[i];
   v[((size_t)i * 3 + 0) * P + k] = s * e0;
   v[((size_t)i * 3 + 1) * P + k] = s * e1;
   v[((size_t)i * 3 + 2) * P + k] = s * e2;
@@ -252,13 +444,27 @@ size_t close_smem_bytes(int A, int P) { return (size_t)A * 3 * P * sizeof(double
 
 cudaError_t launch_step(const StepArgs &a, int threads, cudaStream_t s) {
   const int grid = (a.N + a.A - 1) / a.A;
+  if (a.method == 1) {
+    k_step_cart_f64<<<grid, threads, step_smem_bytes(a.A, a.P), s>>>(a);
+    return cudaGetLastError();
+  }
   k_step_f64<<<grid, threads, step_smem_bytes(a.A, a.P), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_close(const StepArgs &a, int threads, cudaStream_t s) {
+  if (a.method == 1) {
+    const size_t total = (size_t)a.N * 3 * a.P;
+    k_close_cart_f64<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   const int grid = (a.N + a.A - 1) / a.A;
   k_close_f64<<<grid, threads, close_smem_bytes(a.A, a.P), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixcom(const FixcomArgs &a, cudaStream_t s) {
+  k_fixcom_f64<<<1, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -272,10 +478,10 @@ cudaError_t launch_advance(int64_t *step, int n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_thermal_v(double *v, const double *sigv, uint64_t seed, int N, int P,
+cudaError_t launch_thermal_v(double *v, const double *sigv, const double *imu, uint64_t seed, int N, int P,
                              cudaStream_t s) {
   const int total = N * P;
-  k_thermal_v<<<(total + 255) / 256, 256, 0, s>>>(v, sigv, seed, N, P);
+  k_thermal_v<<<(total + 255) / 256, 256, 0, s>>>(v, sigv, imu, seed, N, P);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,7 @@ def test_exports_every_declared_symbol(L):
 def test_params_default(L):
     p = b.default_params()
     assert (p.thermostat, p.integrator, p.method, p.precision, p.seed) == (1, 0, 0, 0, 1)
-    assert (p.tau, p.scale, p.sp, p.fixcom) == (1.0, 1.0, 1.0, 0)
+    assert (p.tau, p.scale, p.sp, p.fixcom, p.fmmode, p.fmass) == (1.0, 1.0, 1.0, 0, 0, 1.0)
 
 
 def test_status_strings(L):
@@ -74,7 +74,9 @@ def water_sys():
 
 
 @pytest.mark.parametrize("case", ["P0", "P129", "T0", "dt0", "badpot", "badthermo", "badint",
-                                  "fixcom", "tau0", "sp0", "gamma_mismatch", "box_small",
+                                  "fixcom2", "badmethod", "badfmmode", "fmass0", "normal_cartesian",
+                                  "split_cartesian", "split_fixcom", "split_fmass", "split_normal",
+                                  "tau0", "sp0", "gamma_mismatch", "box_small",
                                   "natoms_not3", "mass0", "null_pos"])
 def test_create_rejects_invalid(L, water_sys, case):
     s = water_sys
@@ -87,7 +89,15 @@ def test_create_rejects_invalid(L, water_sys, case):
     elif case == "badpot": s.potential = 7
     elif case == "badthermo": prm.thermostat = 5
     elif case == "badint": prm.integrator = 3
-    elif case == "fixcom": prm.fixcom = 1
+    elif case == "fixcom2": prm.fixcom = 2
+    elif case == "badmethod": prm.method = 5
+    elif case == "badfmmode": prm.fmmode = 3
+    elif case == "fmass0": prm.fmass = 0.0
+    elif case == "normal_cartesian": prm.method, prm.fmmode = b.METHOD_PIMD, b.FMMODE_NORMAL
+    elif case == "split_cartesian": prm.precision, prm.method = b.PREC_SPLIT, b.METHOD_PIMD
+    elif case == "split_fixcom": prm.precision, prm.fixcom = b.PREC_SPLIT, 1
+    elif case == "split_fmass": prm.precision, prm.fmass = b.PREC_SPLIT, 2.0
+    elif case == "split_normal": prm.precision, prm.fmmode = b.PREC_SPLIT, b.FMMODE_NORMAL
     elif case == "tau0": prm.tau = 0.0
     elif case == "sp0": prm.sp = 0.0
     elif case == "gamma_mismatch": kw["gamma0"] = 3.0

@@ -1,0 +1,91 @@
+"""GPU path (FP64, through the C ABI) against the FP64 CPU oracle for the
+method keywords of Sec. III.C: method pimd (Cartesian beads), fmmode normal,
+fmass and fixcom.  Same bars as the normal-mode parity tests: 1e-10 after 100
+steps (harmonic), 1e-8 after 50 steps (water-like), estimators within them."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2602_13553_gb300 import inputs
+from tests._gpu import coord_err, pimd, scalar_err  # noqa: F401
+from tests.test_gpu_parity import _compare_est, _pair
+
+pytestmark = pytest.mark.gpu
+
+HBAR = 4.135667403e-3 / (2 * math.pi)
+OMEGA_HO = 0.1 / HBAR
+
+
+def _water(nmol, P, seed):
+    L = inputs.box_length(nmol)
+    x0, mass = inputs.water_box(nmol, L, P, seed, jitter=0.02)
+    return x0, mass, dict(potential=1, ff=inputs.water_ff_for_box(L), box=(L, L, L))
+
+
+def _run_both(c, g, n, bar):
+    xg, vg, _ = g.get_state()
+    assert coord_err(vg, c.v) < 1e-13          # initial state (thermal draw)
+    c.run(n)
+    g.step(n)
+    xg, vg, st = g.get_state()
+    assert st == n
+    assert coord_err(xg, c.x) < bar
+    assert coord_err(vg, c.v) < bar
+    _compare_est(g.estimators(), c.estimators(), bar)
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_cartesian_harmonic_64x8(orc, pimd, integrator):
+    x0, mass = inputs.harmonic(64, 8, seed=1, std=0.1)
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, potential=0, ff=(OMEGA_HO,),
+                 integrator=integrator, method=1)
+    _run_both(c, g, 100, 1e-10)
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_cartesian_water(orc, pimd, integrator):
+    x0, mass, kw = _water(16, 4, 3)
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, integrator=integrator, method=1, **kw)
+    _run_both(c, g, 50, 1e-8)
+
+
+@pytest.mark.parametrize("fmmode,fmass", [(1, 1.0), (0, 3.0), (1, 0.5)])
+def test_fictitious_masses_harmonic(orc, pimd, fmmode, fmass):
+    x0, mass = inputs.harmonic(64, 8, seed=2, std=0.1)
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, potential=0, ff=(OMEGA_HO,),
+                 fmmode=fmmode, fmass=fmass, tau=0.05)
+    _run_both(c, g, 100, 1e-10)
+
+
+def test_fictitious_masses_water_obabo(orc, pimd):
+    x0, mass, kw = _water(16, 8, 4)
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, integrator=1, fmmode=1, fmass=2.0, **kw)
+    _run_both(c, g, 50, 1e-8)
+
+
+@pytest.mark.parametrize("method,integrator", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_fixcom_water(orc, pimd, method, integrator):
+    x0, mass, kw = _water(16, 4, 5)
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, integrator=integrator, method=method,
+                 fixcom=1, **kw)
+    _run_both(c, g, 50, 1e-8)
+    _, vg, _ = g.get_state()
+    rows = [0] if method == 0 else range(4)
+    scale = (mass[:, None] * np.abs(vg[0])).sum()
+    for k in rows:
+        assert np.abs((mass[:, None] * vg[k]).sum(axis=0)).max() < 1e-11 * scale
+
+
+def test_cartesian_checkpoint_resume_is_bitwise(pimd):
+    x0, mass, kw = _water(16, 4, 6)
+    a = pimd.Simulation(x0, mass, T=300.0, dt=5e-4, method=1, fixcom=1, **kw)
+    a.step(30)
+    x, v, st = a.get_state()
+    a.step(20)
+    b = pimd.Simulation(x0, mass, T=300.0, dt=5e-4, method=1, fixcom=1, **kw)
+    b.set_state(x, v, st)
+    b.step(20)
+    xa, va, _ = a.get_state()
+    xb, vb, _ = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
