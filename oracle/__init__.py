@@ -38,6 +38,8 @@ NMPIMD = 0
 PIMD = 1          # Cartesian method
 FM_PHYSICAL = 0
 FM_NORMAL = 1
+BARO_NONE = 0
+BARO_BZP = 1      # isotropic BZP barostat (App. E), BAOAB only
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +74,8 @@ class _Sim(ctypes.Structure):
         ("step", ctypes.c_int64),
         ("fmmode", ctypes.c_int32), ("fixcom", ctypes.c_int32),
         ("fmass", ctypes.c_double),
+        ("barostat", ctypes.c_int32), ("pad1", ctypes.c_int32),
+        ("pext", ctypes.c_double), ("taup", ctypes.c_double), ("vW", ctypes.c_double),
     ]
 
 
@@ -84,6 +88,8 @@ class _Est(ctypes.Structure):
         ("K_CV", ctypes.c_double), ("P_PR", ctypes.c_double), ("P_MD", ctypes.c_double),
         ("P_CV", ctypes.c_double), ("T_ring", ctypes.c_double),
         ("volume", ctypes.c_double), ("vir_sum", ctypes.c_double),
+        ("vW", ctypes.c_double), ("K_W", ctypes.c_double), ("U_W", ctypes.c_double),
+        ("J_W", ctypes.c_double), ("enthalpy", ctypes.c_double),
     ]
 
 
@@ -229,12 +235,16 @@ class Sim:
     (noise stream 2).  potential 0 = harmonic (ff[0] = omega in 1/ps), 1 =
     water-like (ff = kb, r0, kth, th0, eps, sig, rc).  thermostat 0 = NVE,
     1 = PILE_L.  fmmode 0 = physical, 1 = normal; fmass scales the fictitious
-    masses; fixcom removes the centre-of-mass velocity every step.
+    masses; fixcom removes the centre-of-mass velocity every step.  barostat 1
+    = isotropic BZP (App. E, BAOAB, normal modes) at pext (eV/A^3) with
+    barostat time taup (ps); NpH without a thermostat, NpT with PILE_L.
     """
 
     def __init__(self, x0, mass, *, T, dt, potential=POT_HARMONIC, ff=(0.0,), box=(0.0, 0.0, 0.0),
                  v0=None, thermostat=1, integrator=BAOAB, seed=1, tau=1.0, scale=1.0, sp=1.0,
-                 method=NMPIMD, fmmode=FM_PHYSICAL, fmass=1.0, fixcom=0):
+                 method=NMPIMD, fmmode=FM_PHYSICAL, fmass=1.0, fixcom=0, barostat=BARO_NONE,
+                 pext=0.0, taup=1.0, vW=0.0):
+        assert barostat == BARO_NONE or (integrator == BAOAB and method == NMPIMD and potential == POT_WATERLIKE)
         x0 = np.ascontiguousarray(x0, dtype=np.float64)
         P, N, three = x0.shape
         assert three == 3 and 1 <= P <= 128
@@ -250,6 +260,7 @@ class Sim:
         s.N, s.P = N, P
         s.potential, s.thermostat, s.integrator = potential, thermostat, integrator
         s.method, s.fmmode, s.fixcom, s.fmass = method, fmmode, int(fixcom), float(fmass)
+        s.barostat, s.pext, s.taup, s.vW = int(barostat), float(pext), float(taup), float(vW)
         s.T, s.dt, s.tau, s.scale, s.sp = T, dt, tau, scale, sp
         s.seed = seed
         for a in range(3):
@@ -269,6 +280,14 @@ class Sim:
     def step(self) -> int:
         return int(self._s.step)
 
+    @property
+    def box(self) -> np.ndarray:
+        return np.array(list(self._s.box))
+
+    @property
+    def vW(self) -> float:
+        return float(self._s.vW)
+
     def run(self, nsteps: int) -> None:
         lib().or_run(ctypes.byref(self._s), int(nsteps))
 
@@ -280,7 +299,8 @@ class Sim:
         lib().or_estimators(ctypes.byref(self._s), ctypes.byref(e))
         P = self.P
         out = {k: getattr(e, k) for k in ("H", "K_PR", "K_VR", "K_CV", "P_PR", "P_MD", "P_CV",
-                                          "T_ring", "volume", "vir_sum")}
+                                          "T_ring", "volume", "vir_sum", "vW", "K_W", "U_W", "J_W",
+                                          "enthalpy")}
         out["step"] = int(e.step)
         out["K_mode"] = np.array(e.K_mode[:P])
         out["S_mode"] = np.array(e.S_mode[:P])

@@ -331,6 +331,11 @@ typedef struct {
   int32_t fmmode;      /* 0 physical, 1 normal (Sec. III.C) */
   int32_t fixcom;      /* remove the centre-of-mass velocity every step */
   double fmass;        /* factor on the fictitious masses (Sec. III.C) */
+  int32_t barostat;    /* 0 none, 1 BZP isotropic (App. E); box[] then changes */
+  int32_t pad1;
+  double pext;         /* target pressure (eV/A^3) */
+  double taup;         /* barostat time (ps): W = 3 P N kB T taup^2 (App. A output 12) */
+  double vW;           /* barostat velocity (1/ps) */
 } or_sim;
 
 /* Fictitious-mass factor of mode k (nmpimd), Sec. III.C keywords fmmode and
@@ -410,7 +415,9 @@ static void or_A(or_sim *s, const double *omega, double *q, double tau) {
       for (int a = 0; a < 3; ++a) {
         size_t id = ((size_t)k * N + n) * 3 + a;
         double qq = q[id], vv = s->v[id];
-        if (k == 0 || wk == 0.0) {
+        if (k == 0 && s->barostat) {
+          continue;   /* or_A_baro_centroid */
+        } else if (k == 0 || wk == 0.0) {
           q[id] = qq + tau * vv;
         } else {
           double c = cos(wk * tau), sn = sin(wk * tau);
@@ -518,6 +525,85 @@ static void or_O_cart(or_sim *s, double wn, double dtO, uint32_t stream) {
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* BZP barostat, isotropic (App. E), acting on the centroid mode.            */
+/* ------------------------------------------------------------------------ */
+static double or_baro_W(const or_sim *s) {
+  return 3.0 * s->P * s->N * OR_KB * s->T * s->taup * s->taup;
+}
+
+/* Sum over beads and atoms of (r - r_c) . F, r_c the bead average. */
+static double or_rcF(const or_sim *s) {
+  int N = s->N, P = s->P;
+  double rcF = 0.0;
+  for (int n = 0; n < N; ++n)
+    for (int a = 0; a < 3; ++a) {
+      double rc = 0.0;
+      for (int k = 0; k < P; ++k) rc += s->x[((size_t)k * N + n) * 3 + a];
+      rc /= P;
+      for (int k = 0; k < P; ++k) {
+        size_t id = ((size_t)k * N + n) * 3 + a;
+        rcF += (s->x[id] - rc) * s->F[id];
+      }
+    }
+  return rcF;
+}
+
+/* B_W over a kick of length tB that starts from the current velocities:
+ *   v_W += (3 tB / W) [n V (P_CV - P_ext) + n kB T] + (tB^2 / W) sum F~0 . v~0
+ *          + (tB^3 / (3 W)) sum |F~0|^2 / m,
+ * n V P_CV = (sum m |v~0|^2 - sum (r - r_c).F + sum_k Tr Xi^(k)) / 3 (output
+ * 10); the tB^2 and tB^3 terms integrate the centroid kinetic pressure along
+ * the kick exactly.  The printed "1/(n kB T)" is read as n kB T (an energy,
+ * the volume Jacobian of J_W = -n kB T ln V). */
+static void or_B_baro(or_sim *s, const double *M, double *Ft, double tB) {
+  int N = s->N, P = s->P;
+  or_to_nm(P, N, M, s->F, Ft);
+  double mv2 = 0.0, Fv = 0.0, F2m = 0.0, vir = 0.0;
+  for (int n = 0; n < N; ++n) {
+    double mm = s->mass[n] * or_mode_mu(s, 0) * OR_MVV2E;
+    for (int a = 0; a < 3; ++a) {
+      double v0 = s->v[(size_t)n * 3 + a], f0 = Ft[(size_t)n * 3 + a];
+      mv2 += mm * v0 * v0;
+      Fv += f0 * v0;
+      F2m += f0 * f0 / mm;
+    }
+  }
+  for (int k = 0; k < P; ++k) vir += s->vir[k];
+  double V = s->box[0] * s->box[1] * s->box[2];
+  double W = or_baro_W(s);
+  double nVPcv = (mv2 - or_rcF(s) + vir) / 3.0;
+  s->vW += 3.0 * tB / W * (nVPcv - P * V * s->pext + P * OR_KB * s->T) + tB * tB / W * Fv +
+           tB * tB * tB / (3.0 * W) * F2m;
+}
+
+/* A for the centroid under the barostat (App. E): q~0 <- e^a q~0 +
+ * (e^a - e^-a) / (2 v_W) v~0, v~0 <- e^-a v~0, box <- e^a box, a = tA v_W. */
+static void or_A_baro_centroid(or_sim *s, double *q, double tA) {
+  int N = s->N;
+  double a = tA * s->vW;
+  double ea = exp(a), ema = exp(-a);
+  double sh = fabs(a) < 1e-8 ? tA * (1.0 + a * a / 6.0) : (ea - ema) / (2.0 * s->vW);
+  for (int n = 0; n < N; ++n)
+    for (int c = 0; c < 3; ++c) {
+      size_t id = (size_t)n * 3 + c;
+      q[id] = ea * q[id] + sh * s->v[id];
+      s->v[id] = ema * s->v[id];
+    }
+  for (int c = 0; c < 3; ++c) s->box[c] *= ea;
+}
+
+/* Langevin on the barostat velocity (App. E, NpT): v_W <- c1 v_W +
+ * c2 sqrt(n kB T / W) eta with c1 = exp(-dtO / tau_0) (the centroid damping
+ * time; the printed "m_i" under the root is read as W), eta the first
+ * deviate of Philox atom 0xffffffff, mode 0, stream 3. */
+static void or_O_baro(or_sim *s, double dtO) {
+  double c1 = exp(-dtO / s->tau), c2 = sqrt(1.0 - c1 * c1);
+  double eta[3];
+  or_gauss3(s->seed, 0xffffffffu, 0u, 3u, (uint64_t)s->step, eta);
+  s->vW = c1 * s->vW + c2 * sqrt(s->P * OR_KB * s->T / or_baro_W(s)) * eta[0];
+}
+
 /* n steps.  BAOAB: B(h/2) A(h/2) O(h) A(h/2) [forces] B(h/2).
  *           OBABO: O(h/2) B(h/2) A(h) [forces] B(h/2) O(h/2).
  * The O sub-steps are skipped when thermostat == 0 (NVE); with fixcom the
@@ -553,13 +639,18 @@ void or_run(or_sim *s, int64_t nsteps) {
         if (s->thermostat) or_O_cart(s, wn, 0.5 * h, 1u);
       }
     } else if (s->integrator == 0) {
+      if (s->barostat) or_B_baro(s, M, Ft, 0.5 * h);
       or_B(s, M, Ft, 0.5 * h);
       or_to_nm(P, N, M, s->x, q);
       or_A(s, omega, q, 0.5 * h);
+      if (s->barostat) or_A_baro_centroid(s, q, 0.5 * h);
       if (s->thermostat) or_O(s, omega, h, 0u);
+      if (s->thermostat && s->barostat) or_O_baro(s, h);
       or_A(s, omega, q, 0.5 * h);
+      if (s->barostat) or_A_baro_centroid(s, q, 0.5 * h);
       or_from_nm(P, N, M, q, s->x);
       or_compute_forces(s);
+      if (s->barostat) or_B_baro(s, M, Ft, 0.5 * h);
       or_B(s, M, Ft, 0.5 * h);
     } else {
       if (s->thermostat) or_O(s, omega, 0.5 * h, 0u);
@@ -586,6 +677,7 @@ typedef struct {
   double K_mode[128], S_mode[128], U_bead[128];
   double H, K_PR, K_VR, K_CV, P_PR, P_MD, P_CV, T_ring;
   double volume, vir_sum;
+  double vW, K_W, U_W, J_W, enthalpy;   /* App. A outputs 11-15 (barostat) */
 } or_estimates;
 
 void or_estimators(const or_sim *s, or_estimates *e) {
@@ -685,5 +777,12 @@ void or_estimators(const or_sim *s, or_estimates *e) {
   }
   e->T_ring = 2.0 * Ktot / (3.0 * N * P * OR_KB);
   e->vir_sum = virtot;
+  if (s->barostat) {                                             /* outputs 11-15 */
+    e->vW = s->vW;
+    e->K_W = 0.5 * or_baro_W(s) * s->vW * s->vW;
+    e->U_W = P * s->pext * V;
+    e->J_W = -P * kT * log(V);
+    e->enthalpy = e->H + e->K_W + e->U_W + e->J_W;
+  }
   free(M); free(lam); free(q);
 }

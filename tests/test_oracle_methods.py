@@ -246,3 +246,70 @@ def test_normal_mode_masses_harmonic_x2_matches_discrete_chain(orc):
     ref = discrete_nm_x2(P, T, m, OMEGA_HO, dt, tau, mu)
     assert abs(mean - ref) < 3 * se, (mean, ref, se)
     assert abs(np.mean(tring) - P * T) < 0.02 * P * T
+
+
+# ---- BZP barostat (App. E), isotropic, BAOAB, normal modes ------------------
+
+def _bonded_water(nmol, P, seed, L=None):
+    L = L or inputs.box_length(nmol)
+    x0, mass = inputs.water_box(nmol, L, P, seed, jitter=0.02)
+    ff = list(inputs.water_ff_for_box(L))
+    ff[4] = 0.0          # no Lennard-Jones: no cutoff discontinuity in the energy
+    return x0, mass, dict(potential=1, ff=ff, box=(L, L, L))
+
+
+def test_bzp_frozen_barostat_is_the_plain_integrator(orc):
+    """W -> infinity with v_W = 0: the barostat never moves and the step is the
+    normal-mode BAOAB step (the centroid propagator's sinh(a)/v_W -> tA)."""
+    x0, mass, kw = _bonded_water(8, 4, 41)
+    common = dict(T=300.0, dt=5e-4, thermostat=1, seed=2, **kw)
+    a = orc.Sim(x0, mass, barostat=1, pext=1e-3, taup=1e9, **common)
+    b = orc.Sim(x0, mass, **common)
+    a.run(40)
+    b.run(40)
+    assert abs(a.vW) < 1e-9          # only the thermal kicks of a huge W
+    assert np.abs(a.x - b.x).max() < 1e-12 and np.abs(a.v - b.v).max() < 1e-9
+
+
+def test_bzp_nph_conserves_the_extended_enthalpy(orc):
+    """NpH (no thermostat): output 15, H + K_W + U_W + J_W, is conserved with a
+    second-order error; this fixes the n kB T reading of the barostat force and
+    the exact kick terms (any other force on v_W drifts at first order)."""
+    x0, mass, kw = _bonded_water(16, 4, 42)
+    probe = orc.Sim(x0, mass, T=300.0, dt=1e-4, thermostat=0, **kw)
+    pext = probe.estimators()["P_CV"]      # start near mechanical balance
+    errs = []
+    for dt in (2e-4, 1e-4):
+        s = orc.Sim(x0, mass, T=300.0, dt=dt, thermostat=0, barostat=1, pext=pext, taup=0.02, vW=2.0, **kw)
+        e0 = s.estimators()["enthalpy"]
+        dev = 0.0
+        for _ in range(int(round(0.04 / dt / 10))):
+            s.run(10)
+            dev = max(dev, abs(s.estimators()["enthalpy"] - e0))
+        errs.append(dev)
+        assert abs(s.box[0] / kw["box"][0] - 1.0) > 1e-3     # the box did move
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_bzp_npt_ideal_gas_volume(orc):
+    """NpT, free atoms in a periodic box: <V> = (N + 1) kB T / P_ext (the
+    isothermal-isobaric measure with dV; the J_W term makes the + 1)."""
+    P, N, T = 4, 6, 300.0
+    L0 = 10.0
+    g = np.random.default_rng(5)
+    x0 = np.repeat(g.uniform(0, L0, size=(1, N, 3)), P, axis=0) + g.normal(0, 0.05, size=(P, N, 3))
+    mass = np.full(N, 16.0)
+    ff = (0.0, 1.0, 0.0, 1.8, 0.0, 1.0, 0.5)      # every force constant zero
+    pext = (N + 1) * KB * T / L0 ** 3
+    s = orc.Sim(x0, mass, T=T, dt=2e-3, potential=1, ff=ff, box=(L0, L0, L0), thermostat=1, tau=0.05,
+                seed=9, barostat=1, pext=pext, taup=0.05)
+    s.run(2000)
+    vols = []
+    for _ in range(3000):
+        s.run(20)
+        vols.append(s.box.prod())
+    from tests._stats import block_mean_sigma
+    mu, sig = block_mean_sigma(vols, 30)
+    target = (N + 1) * KB * T / pext
+    assert abs(mu - target) < 3 * sig, (mu, target, sig)
+    assert abs(mu - N * KB * T / pext) > 3 * sig        # distinguishes the + 1
