@@ -70,6 +70,10 @@ enum { PIMD_METHOD_NMPIMD = 0, PIMD_METHOD_PIMD = 1 };
  * m^(k) = m (physical) or lambda_k m (normal, k >= 1; the centroid keeps m
  * because lambda_0 = 0).  Every internal mode then oscillates at omega_n. */
 enum { PIMD_FMMODE_PHYSICAL = 0, PIMD_FMMODE_NORMAL = 1 };
+/* Sec. III.C keywords "barostat" / "iso", App. E: none (NVE/NVT) or the
+ * isotropic Bussi-Zykova-Parrinello barostat on the centroid mode (NpH
+ * without a thermostat, NpT with PILE_L, which also thermostats v_W). */
+enum { PIMD_BARO_NONE = 0, PIMD_BARO_BZP_ISO = 1 };
 /* arithmetic of the step and force kernels:
  *   FP64   every quantity in FP64.
  *   SPLIT  the ring-polymer centroid (position and centroid-mode velocity) in
@@ -123,8 +127,20 @@ typedef struct {
  *           (nmpimd) or of every bead (pimd) at the end of every step.
  *   fmmode  PIMD_FMMODE_PHYSICAL or PIMD_FMMODE_NORMAL (nmpimd only).
  *   fmass   > 0, multiplies every fictitious mass (m^(k) = fmass mu_k m).
- * method pimd, fmmode normal, fmass != 1 and fixcom run in FP64 on a single
- * handle (EINVAL with PIMD_PREC_SPLIT and in the batch engine and server). */
+ *   barostat PIMD_BARO_NONE or PIMD_BARO_BZP_ISO (App. E): every step
+ *           B_W: v_W += (3 tB / W)[n V (P_CV - P_ext) + n kB T]
+ *                      + (tB^2 / W) sum F~0.v~0 + (tB^3 / 3W) sum |F~0|^2 / m
+ *           beside each B(tB) (exact along the kick; the printed 1/(n kB T)
+ *           read as n kB T), the A steps scale the centroid mode and the box
+ *           by exp(tA v_W), and with PILE_L the O step also draws
+ *           v_W <- c1 v_W + c2 sqrt(n kB T / W) eta (c1 = exp(-h / tau),
+ *           Philox atom 0xffffffff, mode 0, stream 3).  n = P, W = 3 P N kB T
+ *           taup^2.  Water-like periodic systems, BAOAB, method nmpimd, FP64.
+ *   pext    target pressure (eV/A^3) of the barostat.
+ *   taup    barostat time (ps) > 0.
+ * method pimd, fmmode normal, fmass != 1, fixcom and the barostat run in FP64
+ * on a single handle (EINVAL with PIMD_PREC_SPLIT and in the batch engine and
+ * server). */
 typedef struct {
   int32_t thermostat;
   int32_t integrator;
@@ -137,6 +153,10 @@ typedef struct {
   int32_t fixcom;
   int32_t fmmode;
   double fmass;
+  int32_t barostat;
+  int32_t reserved;
+  double pext;
+  double taup;
 } pimd_params;
 
 /* App. A outputs 1-10 at integer time, plus bookkeeping.
@@ -156,6 +176,10 @@ typedef struct {
  *   P_CV       output 10: [sum_i m^(0) |v~^(0)|^2 - sum (r - r_c).F + sum_k Tr Xi^(k)] / 3PV
  *              (method pimd: v~^(0) = sum_k v^(k) / sqrt(P))
  *   T_ring     2 sum_k K^(k) / (3 N P kB): equals P T in equilibrium (Sec. IV.A)
+ *   vW, K_W, U_W, J_W, enthalpy   outputs 11-15 with the barostat (zero
+ *              without): v_W (1/ps), 1/2 W v_W^2, n P_ext V, -n kB T ln V and
+ *              H + K_W + U_W + J_W, conserved in NpH (eV)
+ *   box        the current box edges (A)
  * Pressures are eV/A^3 (NaN without a periodic box); volume in A^3;
  * vir_sum = sum_k Tr Xi^(k) (eV). */
 typedef struct {
@@ -167,6 +191,8 @@ typedef struct {
   double U_bead[PIMD_MAX_BEADS];
   double H, K_PR, K_VR, K_CV, P_PR, P_MD, P_CV, T_ring;
   double volume, vir_sum;
+  double vW, K_W, U_W, J_W, enthalpy;
+  double box[3];
 } pimd_estimates;
 
 /* Optional device allocator (for example a framework's caching allocator).
@@ -237,6 +263,13 @@ pimd_status pimd_get_state(pimd_handle *h, double *x, double *v_nm, int64_t *ste
  * pimd_get_state this is checkpoint / resume: the noise is keyed on the step
  * counter, so a resumed run continues bit for bit. */
 pimd_status pimd_set_state(pimd_handle *h, const double *x, const double *v_nm, int64_t step);
+
+/* The barostat state (App. E) for checkpoints: *vW (1/ps) and box[3] (A).
+ * get: either pointer may be NULL; set: EINVAL without a barostat or with a
+ * box edge <= 2 rc; the forces are recomputed for the new box.  Both wait for
+ * the handle's queued work. */
+pimd_status pimd_get_barostat(pimd_handle *h, double *vW, double *box);
+pimd_status pimd_set_barostat(pimd_handle *h, double vW, const double *box);
 
 /* Release the handle and its device memory (waits for its queued work). */
 void pimd_destroy(pimd_handle *h);

@@ -26,6 +26,8 @@ METHOD_NMPIMD = 0
 METHOD_PIMD = 1
 FMMODE_PHYSICAL = 0
 FMMODE_NORMAL = 1
+BARO_NONE = 0
+BARO_BZP_ISO = 1
 PREC_FP64 = 0
 PREC_SPLIT = 1
 MAX_BEADS = 128
@@ -60,6 +62,8 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double), ("scale", ctypes.c_double), ("sp", ctypes.c_double),
         ("fixcom", ctypes.c_int32), ("fmmode", ctypes.c_int32),
         ("fmass", ctypes.c_double),
+        ("barostat", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("pext", ctypes.c_double), ("taup", ctypes.c_double),
     ]
 
 
@@ -72,12 +76,17 @@ class Estimates(ctypes.Structure):
         ("K_CV", ctypes.c_double), ("P_PR", ctypes.c_double), ("P_MD", ctypes.c_double),
         ("P_CV", ctypes.c_double), ("T_ring", ctypes.c_double),
         ("volume", ctypes.c_double), ("vir_sum", ctypes.c_double),
+        ("vW", ctypes.c_double), ("K_W", ctypes.c_double), ("U_W", ctypes.c_double),
+        ("J_W", ctypes.c_double), ("enthalpy", ctypes.c_double),
+        ("box", ctypes.c_double * 3),
     ]
 
     def as_dict(self) -> dict:
         P = self.P
         out = {k: getattr(self, k) for k in ("H", "K_PR", "K_VR", "K_CV", "P_PR", "P_MD", "P_CV",
-                                             "T_ring", "volume", "vir_sum")}
+                                             "T_ring", "volume", "vir_sum", "vW", "K_W", "U_W",
+                                             "J_W", "enthalpy")}
+        out["box"] = np.array(list(self.box))
         out["step"] = int(self.step)
         out["K_mode"] = np.array(self.K_mode[:P])
         out["S_mode"] = np.array(self.S_mode[:P])
@@ -88,7 +97,8 @@ class Estimates(ctypes.Structure):
 # every symbol include/pimd.h declares (checked by the CPU tests)
 EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "pimd_last_error",
            "pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
-           "pimd_set_state", "pimd_destroy", "pimd_set_kernel_timing", "pimd_kernel_times",
+           "pimd_set_state", "pimd_get_barostat", "pimd_set_barostat", "pimd_destroy",
+           "pimd_set_kernel_timing", "pimd_kernel_times",
            "pimd_kernel_launches", "pimd_estimators_noalloc",
            "pimd_batch_replica_bytes", "pimd_batch_create", "pimd_batch_add", "pimd_batch_remove",
            "pimd_batch_run", "pimd_batch_sync", "pimd_batch_status", "pimd_batch_estimators",
@@ -132,6 +142,8 @@ def lib():
         L.pimd_estimators.argtypes = [vp, ctypes.POINTER(Estimates)]
         L.pimd_get_state.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64)]
         L.pimd_set_state.argtypes = [vp, dp, dp, ctypes.c_int64]
+        L.pimd_get_barostat.argtypes = [vp, dp, dp]
+        L.pimd_set_barostat.argtypes = [vp, ctypes.c_double, dp]
         L.pimd_destroy.argtypes = [vp]
         L.pimd_destroy.restype = None
         L.pimd_set_kernel_timing.argtypes = [vp, ctypes.c_int]
@@ -141,7 +153,7 @@ def lib():
         L.pimd_kernel_launches.argtypes = [vp]
         L.pimd_kernel_launches.restype = ctypes.c_int64
         for f in ("pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
-                  "pimd_set_state"):
+                  "pimd_set_state", "pimd_get_barostat", "pimd_set_barostat"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
         return L
@@ -253,6 +265,17 @@ class Simulation:
         x = np.ascontiguousarray(x, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         check(lib().pimd_set_state(self._h, _dp(x), _dp(v), int(step)))
+
+    def get_barostat(self):
+        """(v_W in 1/ps, box edges in A) of the barostat state."""
+        vw = np.zeros(1)
+        box = np.zeros(3)
+        check(lib().pimd_get_barostat(self._h, _dp(vw), _dp(box)))
+        return float(vw[0]), box
+
+    def set_barostat(self, vW: float, box) -> None:
+        box = np.ascontiguousarray(box, dtype=np.float64)
+        check(lib().pimd_set_barostat(self._h, float(vW), _dp(box)))
 
     def set_kernel_timing(self, enable: bool) -> None:
         check(lib().pimd_set_kernel_timing(self._h, 1 if enable else 0))

@@ -28,6 +28,7 @@ cudaError_t launch_to_f32(const double *src, float *dst, size_t n, cudaStream_t 
 cudaError_t launch_thermal_v(double *v, const double *sigv, const double *imu, uint64_t seed, int N, int P,
                              cudaStream_t s);
 cudaError_t launch_fixcom(const FixcomArgs &a, cudaStream_t s);
+cudaError_t launch_baro_kick(const BaroArgs &a, cudaStream_t s);
 cudaError_t launch_pna_to_nap(const double *src, double *dst, int N, int P, cudaStream_t s);
 cudaError_t launch_nap_to_pna(const double *src, double *dst, int N, int P, cudaStream_t s);
 cudaError_t launch_force_harmonic(const ForceArgs &a, cudaStream_t s);
@@ -128,6 +129,9 @@ extern "C" void pimd_params_default(pimd_params *p) {
   p->fixcom = 0;
   p->fmmode = PIMD_FMMODE_PHYSICAL;
   p->fmass = 1.0;
+  p->barostat = PIMD_BARO_NONE;
+  p->pext = 0.0;
+  p->taup = 1.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -135,8 +139,10 @@ extern "C" void pimd_params_default(pimd_params *p) {
 // ---------------------------------------------------------------------------
 struct pimd_handle {
   int N = 0, P = 0, potential = 0, nmol = 0, integrator = 0, thermostat = 0, precision = 0;
-  int method = 0, fixcom = 0;
-  double T = 0, dt = 0, tau = 0, scale = 0, sp = 0, fmass = 1.0;
+  int method = 0, fixcom = 0, barostat = 0;
+  double T = 0, dt = 0, tau = 0, scale = 0, sp = 0, fmass = 1.0, pext = 0, taup = 0;
+  double *baro = nullptr;     // device barostat state (kBaroWords), or null
+  double h_baro[kBaroWords] = {0};
   uint64_t seed = 0;
   double box[3] = {0, 0, 0};
   double ff[8] = {0};
@@ -305,6 +311,7 @@ static StepArgs step_args(pimd_handle *h) {
   a.ifmass = 1.0 / h->fmass;
   a.wn2 = h->wn * h->wn;
   a.mass_mm = h->mass_mm;
+  a.baro = h->baro;
   a.step = h->d_step;
   a.step_off = 0;
   const bool water = h->potential == PIMD_POT_WATERLIKE;
@@ -323,6 +330,7 @@ static StepArgs step_args(pimd_handle *h) {
 
 static ForceArgs force_args(pimd_handle *h) {
   ForceArgs a;
+  a.dbox = h->baro ? h->baro + kBaroL : nullptr;
   a.N = h->N;
   a.P = h->P;
   a.nmol = h->nmol;
@@ -366,6 +374,7 @@ static NbrArgs nbr_args(pimd_handle *h, bool force) {
     a.box[d] = h->box[d];
     a.invbox[d] = 1.0 / h->box[d];
   }
+  a.dbox = h->baro ? h->baro + kBaroL : nullptr;
   a.rlist = h->rlist;
   a.skin = h->skin;
   a.force = force ? 1 : 0;
@@ -498,6 +507,39 @@ static pimd_status enqueue_forces(pimd_handle *h, bool from_outside, bool advanc
   return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_harmonic(fa, h->stream); });
 }
 
+// B_W of the barostat over [t0, t0 + tB] of the kick the next kernel
+// applies (App. E); with step_follows also that step's O_W and box.
+static pimd_status enqueue_baro(pimd_handle *h, double t0, double tB, bool step_follows) {
+  BaroArgs b;
+  b.N = h->N;
+  b.P = h->P;
+  b.nmol = h->nmol;
+  b.x = h->x;
+  b.v = h->v;
+  b.F = h->F;
+  b.Mt = h->Mt;
+  b.mass_mm = h->mass_mm;
+  b.Wpart = h->Wpart;
+  b.baro = h->baro;
+  b.t0 = t0;
+  b.tB = tB;
+  b.tA = 0.5 * h->dt;
+  b.step_follows = step_follows ? 1 : 0;
+  const double kT = kBoltzmann * h->T;
+  b.W = 3.0 * h->P * h->N * kT * h->taup * h->taup;
+  b.nkT = h->P * kT;
+  b.npext = h->P * h->pext;
+  b.mu0 = h->fmass;
+  b.thermo = h->thermostat == PIMD_THERMO_PILE_L;
+  b.c1W = std::exp(-h->dt / h->tau);
+  b.sigW = std::sqrt(1.0 - b.c1W * b.c1W) * std::sqrt(b.nkT / b.W);
+  b.seed = h->seed;
+  b.step = h->d_step;
+  b.Lmin = 2.0 * h->ff[6];
+  b.err = h->d_err;
+  return enqueue(h, PIMD_KIND_OTHER, 1, [&] { return launch_baro_kick(b, h->stream); });
+}
+
 // One full step: the fused integrator kernel, the forces of the new
 // positions, and the step counter.
 static pimd_status enqueue_step(pimd_handle *h, bool first) {
@@ -513,10 +555,17 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
   StepArgs a = step_args(h);
   a.first = first ? 1 : 0;
   a.kick = first ? 0.5 * h->dt : h->dt;
-  pimd_status st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a, h->threads_step, h->stream); });
+  pimd_status st;
+  // the B_W beside this step's opening B(h/2), which follows the previous
+  // step's closing B(h/2) inside a merged kick
+  if (h->baro && (st = enqueue_baro(h, first ? 0.0 : 0.5 * h->dt, 0.5 * h->dt, true)) != PIMD_OK) return st;
+  st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a, h->threads_step, h->stream); });
   if (st != PIMD_OK) return st;
   st = enqueue_forces(h, false, true);
-  if (st != PIMD_OK || !h->fixcom) return st;
+  if (st != PIMD_OK) return st;
+  // the B_W beside this step's closing B(h/2) (applied by the next kernel)
+  if (h->baro && (st = enqueue_baro(h, 0.0, 0.5 * h->dt, false)) != PIMD_OK) return st;
+  if (!h->fixcom) return st;
   // fixcom at the end of this step: the next kernel (step or close) applies
   // this step's closing B(h/2) (and O(h/2)); remove the momentum it will leave
   FixcomArgs f;
@@ -587,6 +636,9 @@ static pimd_status check_device_errors(pimd_handle *h) {
   } else if (*h->h_err & kErrNonFinite) {
     h->latched = PIMD_ENONFINITE;
     snprintf(h->latched_msg, sizeof(h->latched_msg), "non-finite estimator sum");
+  } else if (*h->h_err & kErrBoxSmall) {
+    h->latched = PIMD_EINVAL;
+    snprintf(h->latched_msg, sizeof(h->latched_msg), "the barostat shrank a box edge below 2 rc");
   }
   if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
   return PIMD_OK;
@@ -660,6 +712,7 @@ static void carve(pimd_handle *h, Carver &c) {
   h->est_out = c.take<double>(3 * P + 12);
   h->d_step = c.take<int64_t>(1);
   h->d_err = c.take<unsigned>(4);
+  if (h->barostat) h->baro = c.take<double>(kBaroWords);
   if (h->precision == PIMD_PREC_SPLIT) {
     h->xc = c.take<double>((size_t)N * 3);
     h->v0 = c.take<double>((size_t)N * 3);
@@ -722,6 +775,16 @@ pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double 
     return fail(PIMD_EINVAL, "fmmode normal applies to normal modes (method nmpimd)");
   if (!(prm.fmass > 0.0) || !std::isfinite(prm.fmass)) return fail(PIMD_EINVAL, "fmass must be > 0");
   if (!(prm.sp > 0.0)) return fail(PIMD_EINVAL, "sp must be > 0");
+  if (prm.barostat != PIMD_BARO_NONE && prm.barostat != PIMD_BARO_BZP_ISO)
+    return fail(PIMD_EINVAL, "unknown barostat %d", prm.barostat);
+  if (prm.barostat != PIMD_BARO_NONE) {
+    if (sys->potential != PIMD_POT_WATERLIKE)
+      return fail(PIMD_EINVAL, "the barostat needs a periodic (water-like) system");
+    if (prm.integrator != PIMD_BAOAB) return fail(PIMD_EINVAL, "the barostat is implemented for BAOAB");
+    if (prm.method != PIMD_METHOD_NMPIMD) return fail(PIMD_EINVAL, "the barostat acts on normal modes (nmpimd)");
+    if (!(prm.taup > 0.0) || !std::isfinite(prm.taup)) return fail(PIMD_EINVAL, "taup must be > 0");
+    if (!std::isfinite(prm.pext)) return fail(PIMD_EINVAL, "pext must be finite");
+  }
   if (prm.precision == PIMD_PREC_SPLIT) {
     pimd_status ks = require_default_keywords(prm, "split precision");
     if (ks != PIMD_OK) return ks;
@@ -756,8 +819,9 @@ pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double 
 
 pimd_status require_default_keywords(const pimd_params &prm, const char *where) {
   if (prm.method != PIMD_METHOD_NMPIMD || prm.fmmode != PIMD_FMMODE_PHYSICAL || prm.fmass != 1.0 ||
-      prm.fixcom != 0)
-    return fail(PIMD_EINVAL, "%s implements method nmpimd, fmmode physical, fmass 1 and fixcom 0", where);
+      prm.fixcom != 0 || prm.barostat != PIMD_BARO_NONE)
+    return fail(PIMD_EINVAL, "%s implements method nmpimd, fmmode physical, fmass 1, fixcom 0 and no barostat",
+                where);
   return PIMD_OK;
 }
 
@@ -827,6 +891,9 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   h->method = prm.method;
   h->fixcom = prm.fixcom;
   h->fmass = prm.fmass;
+  h->barostat = prm.barostat;
+  h->pext = prm.pext;
+  h->taup = prm.taup;
   h->T = T;
   h->dt = dt;
   h->tau = prm.tau;
@@ -916,6 +983,13 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   auto init = [&]() -> pimd_status {
     CK(cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
     CK(cudaMemsetAsync(h->d_err, 0, 4 * sizeof(unsigned), h->stream));
+    if (h->baro) {
+      for (int c = 0; c < 3; ++c) {
+        h->h_baro[kBaroL + c] = h->box[c];
+        h->h_baro[kBaroInvL + c] = 1.0 / h->box[c];
+      }
+      CK(cudaMemcpyAsync(h->baro, h->h_baro, sizeof(h->h_baro), cudaMemcpyHostToDevice, h->stream));
+    }
     if (h->potential == PIMD_POT_WATERLIKE) {
       CK(cudaMemsetAsync(h->cref, 0, sizeof(double) * 3 * h->nmol, h->stream));
       CK(cudaMemsetAsync(h->nbr_off, 0,
@@ -1004,12 +1078,15 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   f.kT = kBoltzmann * h->T;
   f.kB = kBoltzmann;
   f.volume = (h->potential == PIMD_POT_WATERLIKE) ? h->box[0] * h->box[1] * h->box[2] : 0.0;
+  f.dbox = h->baro ? h->baro + kBaroL : nullptr;
   f.out = h->est_out;
   f.err = h->d_err;
   st0 = enqueue(h, PIMD_KIND_EST, 1, [&] { return launch_est_final(f, h->stream); });
   if (st0 != PIMD_OK) return st0;
   CK(cudaMemcpyAsync(h->h_est, h->est_out, sizeof(double) * (3 * P + 12), cudaMemcpyDeviceToHost,
                      h->stream));
+  if (h->baro)
+    CK(cudaMemcpyAsync(h->h_baro, h->baro, sizeof(h->h_baro), cudaMemcpyDeviceToHost, h->stream));
   pimd_status st = check_device_errors(h);
   if (st != PIMD_OK) return st;
   std::memset(out, 0, sizeof(*out));
@@ -1033,7 +1110,50 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   out->T_ring = g[7];
   out->volume = g[8];
   out->vir_sum = g[9];
+  for (int c = 0; c < 3; ++c) out->box[c] = h->baro ? h->h_baro[kBaroL + c] : h->box[c];
+  if (h->baro) {   // outputs 11-15
+    const double kT = kBoltzmann * h->T, n = P;
+    const double W = 3.0 * n * h->N * kT * h->taup * h->taup;
+    const double V = out->box[0] * out->box[1] * out->box[2];
+    out->vW = h->h_baro[kBaroV];
+    out->K_W = 0.5 * W * out->vW * out->vW;
+    out->U_W = n * h->pext * V;
+    out->J_W = -n * kT * std::log(V);
+    out->enthalpy = out->H + out->K_W + out->U_W + out->J_W;
+  }
   return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_get_barostat(pimd_handle *h, double *vW, double *box) {
+  if (!h) return fail(PIMD_EINVAL, "handle is NULL");
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  if (h->baro) CK(cudaMemcpyAsync(h->h_baro, h->baro, sizeof(h->h_baro), cudaMemcpyDeviceToHost, h->stream));
+  pimd_status st = check_device_errors(h);
+  if (st != PIMD_OK) return st;
+  if (vW) *vW = h->baro ? h->h_baro[kBaroV] : 0.0;
+  if (box)
+    for (int c = 0; c < 3; ++c) box[c] = h->baro ? h->h_baro[kBaroL + c] : h->box[c];
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_set_barostat(pimd_handle *h, double vW, const double *box) {
+  if (!h || !box) return fail(PIMD_EINVAL, "NULL argument");
+  if (!h->baro) return fail(PIMD_EINVAL, "the handle has no barostat");
+  if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
+  if (!std::isfinite(vW)) return fail(PIMD_EINVAL, "vW must be finite");
+  for (int c = 0; c < 3; ++c)
+    if (!(box[c] > 2.0 * h->ff[6])) return fail(PIMD_EINVAL, "box edge %d must exceed 2 rc", c);
+  CK(cudaStreamSynchronize(h->stream));
+  std::memset(h->h_baro, 0, sizeof(h->h_baro));
+  h->h_baro[kBaroV] = vW;
+  for (int c = 0; c < 3; ++c) {
+    h->h_baro[kBaroL + c] = box[c];
+    h->h_baro[kBaroInvL + c] = 1.0 / box[c];
+  }
+  CK(cudaMemcpyAsync(h->baro, h->h_baro, sizeof(h->h_baro), cudaMemcpyHostToDevice, h->stream));
+  pimd_status st = enqueue_forces(h, true, false);
+  if (st != PIMD_OK) return st;
+  return check_device_errors(h);
 }
 
 extern "C" pimd_status pimd_get_state(pimd_handle *h, double *x, double *v_nm, int64_t *step) {

@@ -21,7 +21,13 @@ constexpr int kLJWarps = 14;            // warps sharing one molecule's O-O neig
 constexpr int kMaxBuckets = 112;        // kLJWarps * max lane groups (8)
 
 // Bits of the device error word (read back at synchronising calls).
-enum : unsigned { kErrNbrOverflow = 1u, kErrNonFinite = 2u };
+enum : unsigned { kErrNbrOverflow = 1u, kErrNonFinite = 2u, kErrBoxSmall = 4u };
+
+// Device barostat state (App. E), [kBaroWords] doubles:
+//   [0] v_W after the last completed sub-step
+//   [1] v_W of this step's first A (after its B_W), [2] after its O
+//   [3..5] box edges L, [6..8] 1 / L
+enum { kBaroV = 0, kBaroVA1 = 1, kBaroVA2 = 2, kBaroL = 3, kBaroInvL = 6, kBaroWords = 16 };
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
@@ -134,6 +140,28 @@ struct StepArgs {
   double ifmass;               // 1 / fmass
   double wn2;                  // omega_n^2
   const double *mass_mm;       // [N] m mvv2e
+  const double *baro;          // barostat state (centroid propagation under v_W), or null
+};
+
+// B_W of the barostat (App. E) over a kick of length tB that starts from the
+// current velocities, and, when a step follows, that step's v_W at its two A
+// sub-steps (O_W in between) and the box they leave.
+struct BaroArgs {
+  int N, P, nmol;
+  const double *x, *v, *F;     // [N][3][P]
+  const double *Mt;            // [P][P]
+  const double *mass_mm;       // [N] m mvv2e
+  const double *Wpart;         // [nmol][P] Tr Xi rows of the force kernel
+  double *baro;
+  double t0, tB, tA;            // the B_W covers [t0, t0 + tB] of the kick that the next kernel applies
+  int step_follows;
+  double W, nkT, npext, mu0;   // W = 3 n N kB T taup^2; n kB T; n P_ext; centroid mass factor
+  int thermo;
+  double c1W, sigW;            // exp(-h / tau_0); c2 sqrt(n kB T / W)
+  uint64_t seed;
+  const int64_t *step;
+  double Lmin;                 // smallest allowed box edge (2 rc)
+  unsigned *err;
 };
 
 // fixcom: remove the centre-of-mass velocity of the centroid mode (normal
@@ -158,6 +186,7 @@ struct FixcomArgs {
 
 struct ForceArgs {
   int N, P, nmol;
+  const double *dbox;          // device box (barostat state at kBaroL), overriding box/invbox, or null
   const double *x;             // [N][3][P]
   const float *x32;            // [N][3][P] FP32 copy of x (water prefilter)
   int64_t *step_inc;           // if not null, block 0 advances the step counter by one
@@ -181,6 +210,7 @@ struct NbrArgs {
   int nbr_groups;
   unsigned *err;
   double box[3], invbox[3];
+  const double *dbox;          // device box (barostat state at kBaroL), overriding box/invbox, or null
   double rlist;                // rc + skin
   double skin;
   int force;                   // rebuild unconditionally
@@ -239,6 +269,7 @@ struct EstFinalArgs {
   const double *part;          // [nblk_est][2P + 4]
   const double *Upart, *Wpart; // [nblk_force][P]
   double kT, volume, kB;
+  const double *dbox;          // device box edges (barostat): volume = L0 L1 L2, or null
   double *out;                 // [3P + 12]
   unsigned *err;
 };

@@ -172,7 +172,8 @@ __global__ void k_est_final(EstFinalArgs a) {
     Wtot += Wv[k];
   }
   const double rF = tot[2 * P], rcF = tot[2 * P + 1], mv0 = tot[2 * P + 2];
-  const double N = (double)a.N, Pd = (double)P, kT = a.kT, V = a.volume;
+  const double N = (double)a.N, Pd = (double)P, kT = a.kT;
+  const double V = a.dbox ? a.dbox[0] * a.dbox[1] * a.dbox[2] : a.volume;
   const double spring = 2.0 * Stot;   // sum_k sum_i m w_n^2 |r^k - r^(k+1)|^2
   double *g = o + 3 * P;
   g[0] = Ktot + Stot + Utot;                                    // H

@@ -100,8 +100,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
   for (int c = 0; c < 11; ++c) acc[c] = 0.0;
   if (u < G && k < P && m < a.nmol) {
     const int o = 3 * m;
-    const double L0 = a.box[0], L1 = a.box[1], L2 = a.box[2];
-    const double i0 = a.invbox[0], i1 = a.invbox[1], i2 = a.invbox[2];
+    const bool db = a.dbox != nullptr;
+    const double L0 = db ? a.dbox[0] : a.box[0], L1 = db ? a.dbox[1] : a.box[1], L2 = db ? a.dbox[2] : a.box[2];
+    const double i0 = db ? a.dbox[3] : a.invbox[0], i1 = db ? a.dbox[4] : a.invbox[1];
+    const double i2 = db ? a.dbox[5] : a.invbox[2];
     const size_t so = (size_t)o * 3 * P + k;
     const double xo0 = a.x[so], xo1 = a.x[so + P], xo2 = a.x[so + 2 * P];
     if (s >= kLJWarps) {
@@ -275,14 +277,18 @@ __global__ void k_nbr_build(NbrArgs a, const double *ccur) {
   const int NS = kLJWarps * a.nbr_groups;
   const double c0 = ccur[3 * m], c1 = ccur[3 * m + 1], c2 = ccur[3 * m + 2];
   const double rl2 = a.rlist * a.rlist;
+  const bool db = a.dbox != nullptr;
+  const double L0 = db ? a.dbox[0] : a.box[0], L1 = db ? a.dbox[1] : a.box[1], L2 = db ? a.dbox[2] : a.box[2];
+  const double i0 = db ? a.dbox[3] : a.invbox[0], i1 = db ? a.dbox[4] : a.invbox[1];
+  const double i2 = db ? a.dbox[5] : a.invbox[2];
   int cnt[kMaxBuckets];
   for (int b = 0; b < NS; ++b) cnt[b] = 0;
   int n = 0;
   for (int j = 0; j < a.nmol; ++j) {
     if (j == m) continue;
-    const double d0 = mic(ccur[3 * j] - c0, a.box[0], a.invbox[0]);
-    const double d1 = mic(ccur[3 * j + 1] - c1, a.box[1], a.invbox[1]);
-    const double d2 = mic(ccur[3 * j + 2] - c2, a.box[2], a.invbox[2]);
+    const double d0 = mic(ccur[3 * j] - c0, L0, i0);
+    const double d1 = mic(ccur[3 * j + 1] - c1, L1, i1);
+    const double d2 = mic(ccur[3 * j + 2] - c2, L2, i2);
     if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
       ++cnt[j % NS];
       ++n;
@@ -305,9 +311,9 @@ __global__ void k_nbr_build(NbrArgs a, const double *ccur) {
   int *nl = a.nbr + (size_t)m * kMaxNeighbours;
   for (int j = 0; j < a.nmol; ++j) {
     if (j == m) continue;
-    const double d0 = mic(ccur[3 * j] - c0, a.box[0], a.invbox[0]);
-    const double d1 = mic(ccur[3 * j + 1] - c1, a.box[1], a.invbox[1]);
-    const double d2 = mic(ccur[3 * j + 2] - c2, a.box[2], a.invbox[2]);
+    const double d0 = mic(ccur[3 * j] - c0, L0, i0);
+    const double d1 = mic(ccur[3 * j + 1] - c1, L1, i1);
+    const double d2 = mic(ccur[3 * j + 2] - c2, L2, i2);
     if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
       const int b = j % NS;
       nl[off[b] + cnt[b]++] = j;

@@ -30,6 +30,16 @@ __device__ __forceinline__ void rotate(double &q, double &v, double c, double s_
   v = vn;
 }
 
+// Centroid mode under the barostat for time tA at v_W (App. E):
+//   q~0 <- e^a q~0 + (e^a - e^-a) / (2 v_W) v~0,  v~0 <- e^-a v~0,  a = tA v_W
+__device__ __forceinline__ void baro_drift(double &q, double &v, double vW, double tA) {
+  const double a = tA * vW;
+  const double ea = exp(a), ema = exp(-a);
+  const double sh = fabs(a) < 1e-8 ? tA * (1.0 + a * a / 6.0) : (ea - ema) / (2.0 * vW);
+  q = ea * q + sh * v;
+  v = ema * v;
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -91,10 +101,17 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
     if (a.integrator == 0) {
       // B(h/2) of this step, merged with the final B(h/2) of the previous one
       v = fma(a.kick * im, f, v);
-      rotate(q, v, cA, sA, wsA);
-      if (a.thermo)
-        v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
-      rotate(q, v, cA, sA, wsA);
+      if (k == 0 && a.baro) {   // the centroid rides on the barostat
+        baro_drift(q, v, a.baro[kBaroVA1], a.half);
+        if (a.thermo)
+          v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+        baro_drift(q, v, a.baro[kBaroVA2], a.half);
+      } else {
+        rotate(q, v, cA, sA, wsA);
+        if (a.thermo)
+          v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+        rotate(q, v, cA, sA, wsA);
+      }
     } else {
       const double kb = a.half * im;
       if (!a.first) {
@@ -392,6 +409,67 @@ __global__ void __launch_bounds__(256) k_fixcom_f64(FixcomArgs a) {
   }
 }
 
+// B_W of the isotropic BZP barostat (App. E) over [t0, t0 + tB] of the kick
+// that the next kernel applies to the current velocities, with n = P:
+//   v_W += (3 tB / W)[n V P_CV - n V P_ext + n kB T] + (tB^2 / W) sum F~0.v~0
+//          + (tB^3 / 3W) sum |F~0|^2 / m~0,
+//   3 n V P_CV = sum m~0 |v~0|^2 - sum (r - r_c).F + sum_k Tr Xi^(k);
+// then, if a step follows, its v_W at the first A, after O_W (PILE_L) and the
+// box after both A sub-steps.  One block; fixed-order sums.
+__global__ void __launch_bounds__(256) k_baro_kick(BaroArgs a) {
+  __shared__ double red[256];
+  const int P = a.P;
+  double mv2 = 0.0, fv = 0.0, f2m = 0.0, rcf = 0.0, vir = 0.0;
+  for (int t = threadIdx.x; t < a.N * 3; t += blockDim.x) {
+    const int i = t / 3;
+    const size_t row = (size_t)t * P;
+    const double mm = a.mass_mm[i] * a.mu0;
+    double f0 = 0.0, xm = 0.0;
+    for (int j = 0; j < P; ++j) {
+      f0 = fma(a.Mt[j * P], a.F[row + j], f0);   // F~0 = (M F)_0
+      xm += a.x[row + j];
+    }
+    xm /= P;
+    for (int j = 0; j < P; ++j) rcf = fma(a.x[row + j] - xm, a.F[row + j], rcf);
+    const double v0 = fma(a.t0, f0 / mm, a.v[row]);   // at t0 into the kick
+    mv2 = fma(mm * v0, v0, mv2);
+    fv = fma(f0, v0, fv);
+    f2m += f0 * f0 / mm;
+  }
+  for (int t = threadIdx.x; t < a.nmol * P; t += blockDim.x) vir += a.Wpart[t];
+  mv2 = block_sum(mv2, red);
+  fv = block_sum(fv, red);
+  f2m = block_sum(f2m, red);
+  rcf = block_sum(rcf, red);
+  vir = block_sum(vir, red);
+  if (threadIdx.x != 0) return;
+  double *b = a.baro;
+  const double V = b[kBaroL] * b[kBaroL + 1] * b[kBaroL + 2];
+  const double tB = a.tB;
+  double vW = b[kBaroV] + 3.0 * tB / a.W * ((mv2 - rcf + vir) / 3.0 - V * a.npext + a.nkT) +
+              tB * tB / a.W * fv + tB * tB * tB / (3.0 * a.W) * f2m;
+  if (!a.step_follows) {
+    b[kBaroV] = vW;
+    return;
+  }
+  double vO = vW;
+  if (a.thermo) {
+    double e0, e1, e2;
+    gauss3(a.seed, 0xffffffffu, 0u, 3u, (uint64_t)*a.step, e0, e1, e2);
+    vO = a.c1W * vW + a.sigW * e0;
+  }
+  b[kBaroVA1] = vW;
+  b[kBaroVA2] = vO;
+  b[kBaroV] = vO;
+  const double s1 = exp(a.tA * vW), s2 = exp(a.tA * vO);
+  for (int c = 0; c < 3; ++c) {
+    const double L = b[kBaroL + c] * s1 * s2;
+    b[kBaroL + c] = L;
+    b[kBaroInvL + c] = 1.0 / L;
+    if (!(L > a.Lmin)) atomicOr(a.err, kErrBoxSmall);
+  }
+}
+
 __global__ void k_to_f32(const double *src, float *dst, size_t n) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) dst[t] = (float)src[t];
@@ -460,6 +538,11 @@ cudaError_t launch_close(const StepArgs &a, int threads, cudaStream_t s) {
   }
   const int grid = (a.N + a.A - 1) / a.A;
   k_close_f64<<<grid, threads, close_smem_bytes(a.A, a.P), s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_baro_kick(const BaroArgs &a, cudaStream_t s) {
+  k_baro_kick<<<1, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,7 @@ def test_params_default(L):
     p = b.default_params()
     assert (p.thermostat, p.integrator, p.method, p.precision, p.seed) == (1, 0, 0, 0, 1)
     assert (p.tau, p.scale, p.sp, p.fixcom, p.fmmode, p.fmass) == (1.0, 1.0, 1.0, 0, 0, 1.0)
+    assert (p.barostat, p.pext, p.taup) == (0, 0.0, 1.0)
 
 
 def test_status_strings(L):
@@ -76,6 +77,7 @@ def water_sys():
 @pytest.mark.parametrize("case", ["P0", "P129", "T0", "dt0", "badpot", "badthermo", "badint",
                                   "fixcom2", "badmethod", "badfmmode", "fmass0", "normal_cartesian",
                                   "split_cartesian", "split_fixcom", "split_fmass", "split_normal",
+                                  "badbaro", "baro_obabo", "baro_cartesian", "baro_taup0", "baro_split",
                                   "tau0", "sp0", "gamma_mismatch", "box_small",
                                   "natoms_not3", "mass0", "null_pos"])
 def test_create_rejects_invalid(L, water_sys, case):
@@ -98,6 +100,11 @@ def test_create_rejects_invalid(L, water_sys, case):
     elif case == "split_fixcom": prm.precision, prm.fixcom = b.PREC_SPLIT, 1
     elif case == "split_fmass": prm.precision, prm.fmass = b.PREC_SPLIT, 2.0
     elif case == "split_normal": prm.precision, prm.fmmode = b.PREC_SPLIT, b.FMMODE_NORMAL
+    elif case == "badbaro": prm.barostat = 4
+    elif case == "baro_obabo": prm.barostat, prm.integrator = b.BARO_BZP_ISO, b.OBABO
+    elif case == "baro_cartesian": prm.barostat, prm.method = b.BARO_BZP_ISO, b.METHOD_PIMD
+    elif case == "baro_taup0": prm.barostat, prm.taup = b.BARO_BZP_ISO, 0.0
+    elif case == "baro_split": prm.barostat, prm.precision = b.BARO_BZP_ISO, b.PREC_SPLIT
     elif case == "tau0": prm.tau = 0.0
     elif case == "sp0": prm.sp = 0.0
     elif case == "gamma_mismatch": kw["gamma0"] = 3.0

@@ -89,3 +89,40 @@ def test_cartesian_checkpoint_resume_is_bitwise(pimd):
     xa, va, _ = a.get_state()
     xb, vb, _ = b.get_state()
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+@pytest.mark.parametrize("thermostat", [1, 0])
+def test_bzp_barostat_water(orc, pimd, thermostat):
+    """Isotropic BZP barostat (App. E), NpT (PILE_L) and NpH, 32 molecules x 4
+    beads, 50 steps: positions, velocities, v_W, box and outputs 11-15."""
+    x0, mass, kw = _water(32, 4, 7)
+    probe = orc.Sim(x0, mass, T=300.0, dt=2.5e-4, thermostat=0, **kw)
+    pext = probe.estimators()["P_CV"] * 0.8
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, thermostat=thermostat, barostat=1,
+                 pext=pext, taup=0.05, **kw)
+    _run_both(c, g, 50, 1e-8)
+    vw, box = g.get_barostat()
+    assert abs(vw - c.vW) < 1e-8 * max(1.0, abs(c.vW))
+    assert np.abs(box - c.box).max() < 1e-10 * c.box.max()
+    assert abs(box[0] / kw["box"][0] - 1.0) > 1e-6          # the box moved
+    eg, ec = g.estimators(), c.estimators()
+    for k in ("vW", "K_W", "U_W", "J_W", "enthalpy"):
+        assert scalar_err(eg[k], ec[k]) < 1e-8, (k, eg[k], ec[k])
+
+
+def test_bzp_checkpoint_resume_is_bitwise(pimd):
+    x0, mass, kw = _water(32, 4, 8)
+    prm = dict(T=300.0, dt=5e-4, barostat=1, pext=1e-3, taup=0.1, **kw)
+    a = pimd.Simulation(x0, mass, **prm)
+    a.step(30)
+    x, v, st = a.get_state()
+    vw, box = a.get_barostat()
+    a.step(20)
+    b = pimd.Simulation(x0, mass, **prm)
+    b.set_barostat(vw, box)
+    b.set_state(x, v, st)
+    b.step(20)
+    xa, va, _ = a.get_state()
+    xb, vb, _ = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert a.get_barostat()[0] == b.get_barostat()[0]
