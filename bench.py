@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="timed steps of the plain FP64 workload (default: --steps)")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--serve-jobs", type=int, default=200)
@@ -208,6 +209,63 @@ def hbm_peak():
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+SWEEP = ((1 << 20, 8), (1 << 18, 32), (1 << 17, 64), (1 << 16, 128))
+
+
+def sweep_bench(stream, steps=4, warmup=2):
+    """The oscillator throughput sweep: N independent 3D oscillators (m = 1.008
+    amu, hbar omega = 0.1 eV, 300 K, dt = 0.25 fs, PILE_L) with N P = 2^23
+    bead-atoms (201 MB of FP64 state, beyond the 129 MB L2) for P = 8, 32,
+    64, 128, in FP64 and in split precision.  Per point: bead-atom-steps/s
+    over `steps` calls of 10 MD steps (CUDA events on the library's stream)
+    and the roofline of the step kernel, from its own CUDA-event time per
+    launch: FP64 against the FP64 pipe (18 P + 51 flops per bead-atom), split
+    against HBM (60 B + 96 B / P per bead-atom)."""
+    import torch
+    from paper_2602_13553_gb300 import binding, inputs
+    hbar = 4.135667403e-3 / (2 * math.pi)
+    omega = 0.1 / hbar
+    hbm, hsrc = hbm_peak()
+    out = []
+    for N, P in SWEEP:
+        x0, mass = inputs.harmonic(N, P, seed=1, std=0.1)
+        for prec, name in ((0, "fp64"), (1, "split")):
+            sim = binding.Simulation(x0, mass, T=300.0, dt=2.5e-4, potential=0, ff=(omega,),
+                                     precision=prec, stream=stream.cuda_stream)
+            for _ in range(warmup):
+                sim.step(10)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                sim.step(10)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            sim.set_kernel_timing(True)
+            sim.step(10)
+            kt = sim.kernel_times()
+            sim.set_kernel_timing(False)
+            step_ms = kt["step"][0] / max(1, kt["step"][1])
+            units = N * P
+            pt = {"N": N, "P": P, "precision": name, "value": units * 10 * steps / (ms / 1e3),
+                  "step_kernel_ms": step_ms}
+            if prec == 0:
+                ach = (18 * P + 51) * units / (step_ms / 1e3) / 1e12
+                pt["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK / 1e12,
+                                  "unit": "TFLOP/s", "frac": ach / (FP64_PEAK / 1e12)}
+            else:
+                ach = (60.0 + 96.0 / P) * units / (step_ms / 1e3) / 1e9
+                pt["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                  "frac": ach / hbm, "peak_source": hsrc}
+            out.append(pt)
+            sim.close()
+            del sim
+    return {"workload": "N 3D oscillators, N P = 2^23 bead-atoms, 300 K, dt 0.25 fs, PILE_L",
+            "unit": METRIC, "points": out}
 
 
 def batched_bench(stream, steps, warmup):
@@ -502,6 +560,8 @@ def run_ours(args):
         line["batched"]["vs_plain_fp64"] = line["batched"]["value"] / value
     if world == 1 and not args.no_serve:
         line["serve"] = serve_bench(stream, args.serve_jobs, args.serve_step_scale)
+    if world == 1 and not args.no_sweep:
+        line["sweep"] = sweep_bench(stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -141,6 +141,7 @@ struct StepArgs {
   double wn2;                  // omega_n^2
   const double *mass_mm;       // [N] m mvv2e
   const double *baro;          // barostat state (centroid propagation under v_W), or null
+  int noise_pre;               // 1: PILE_L deviates drawn once per (atom, mode) into shared memory
 };
 
 // B_W of the barostat (App. E) over a kick of length tB that starts from the

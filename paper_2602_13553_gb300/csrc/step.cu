@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   double *sV = sX + tileLen;
   double *sF = sV + tileLen;
   double *sQ = sF + tileLen;
+  double *sE = sQ + tileLen;     // PILE_L deviates of this step, stream O1, per element
+  double *sE2 = sE + tileLen;    // OBABO: stream O2 of the previous step
   __shared__ double sred[2][8];
   const int tile0 = blockIdx.x * a.A;
   const int na = min(a.A, a.N - tile0);
@@ -67,14 +69,30 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
     sV[t] = a.v[base + t];
     sF[t] = a.F[base + t];
   }
-  __syncthreads();
   const uint64_t step = (uint64_t)(*a.step + a.step_off);
+  // Large grids: one Philox draw and Box-Muller per (atom, mode) serve the
+  // three components (throughput).  Small grids (noise_pre = 0): each element
+  // draws its own component inline, in parallel with the others (latency).
+  if (a.thermo && a.noise_pre) {
+    const bool o2 = a.integrator == 1 && !a.first;
+    for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
+      const int al = t / P, k = t - al * P;
+      const int e = al * 3 * P + k;
+      gauss3(a.seed, (uint32_t)(tile0 + al), (uint32_t)k, kStreamO1, step, sE[e], sE[e + P], sE[e + 2 * P]);
+      if (o2)
+        gauss3(a.seed, (uint32_t)(tile0 + al), (uint32_t)k, kStreamO2, step - 1, sE2[e], sE2[e + P],
+               sE2[e + 2 * P]);
+    }
+  }
+  __syncthreads();
   const double *__restrict__ Mt = a.mt.Mt;
   for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int k = task % P;
     const int r = task / P;
-    const int d = r % 3;
     const int i = tile0 + r / 3;
+    auto noise = [&](uint32_t stream, uint64_t st, const double *pre) {
+      return a.noise_pre ? pre[task] : gauss1(a.seed, (uint32_t)i, (uint32_t)k, stream, st, r % 3);
+    };
     const double *fx = sF + r * P;
     const double *xx = sX + r * P;
     // F~_k = (M F)_k and q~_k = (M x)_k, two independent chains each
@@ -103,13 +121,11 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
       v = fma(a.kick * im, f, v);
       if (k == 0 && a.baro) {   // the centroid rides on the barostat
         baro_drift(q, v, a.baro[kBaroVA1], a.half);
-        if (a.thermo)
-          v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+        if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
         baro_drift(q, v, a.baro[kBaroVA2], a.half);
       } else {
         rotate(q, v, cA, sA, wsA);
-        if (a.thermo)
-          v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+        if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
         rotate(q, v, cA, sA, wsA);
       }
     } else {
@@ -117,11 +133,9 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
       if (!a.first) {
         // the previous step's closing B(h/2) O(h/2)
         v = fma(kb, f, v);
-        if (a.thermo)
-          v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, d));
+        if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO2, step - 1, sE2));
       }
-      if (a.thermo)
-        v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+      if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
       v = fma(kb, f, v);
       rotate(q, v, cA, sA, wsA);
     }
@@ -236,21 +250,36 @@ __global__ void __launch_bounds__(256) k_step_cart_f64(StepArgs a) {
   const int tileLen = a.A * 3 * P;
   double *sX = sm;               // positions at the start of the step
   double *sN = sX + tileLen;     // new positions
-  double *sC = sN + tileLen;     // [A][3] new centroids (water skin check)
+  double *sE = sN + tileLen;     // PILE_L deviates, stream O1, per element
+  double *sE2 = sE + tileLen;    // OBABO: stream O2 of the previous step
+  double *sC = sE2 + tileLen;    // [A][3] new centroids (water skin check)
   __shared__ double sred[2][8];
   const int tile0 = blockIdx.x * a.A;
   const int na = min(a.A, a.N - tile0);
   const int len = na * 3 * P;
   const size_t base = (size_t)tile0 * 3 * P;
   for (int t = threadIdx.x; t < len; t += blockDim.x) sX[t] = a.x[base + t];
-  __syncthreads();
   const uint64_t step = (uint64_t)(*a.step + a.step_off);
+  if (a.thermo && a.noise_pre) {   // one Philox draw per (atom, bead) serves the three components
+    const bool o2 = a.integrator == 1 && !a.first;
+    for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
+      const int al = t / P, k = t - al * P;
+      const int e = al * 3 * P + k;
+      gauss3(a.seed, (uint32_t)(tile0 + al), (uint32_t)k, kStreamO1, step, sE[e], sE[e + P], sE[e + 2 * P]);
+      if (o2)
+        gauss3(a.seed, (uint32_t)(tile0 + al), (uint32_t)k, kStreamO2, step - 1, sE2[e], sE2[e + P],
+               sE2[e + 2 * P]);
+    }
+  }
+  __syncthreads();
   const double c1 = __ldg(a.mt.c1), c2 = __ldg(a.mt.c2);
   for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int k = task % P;
     const int r = task / P;
-    const int d = r % 3;
     const int i = tile0 + r / 3;
+    auto noise = [&](uint32_t stream, uint64_t st, const double *pre) {
+      return a.noise_pre ? pre[task] : gauss1(a.seed, (uint32_t)i, (uint32_t)k, stream, st, r % 3);
+    };
     const double f = a.F[base + task] + spring_force(sX + r * P, k, P, __ldg(a.mass_mm + i) * a.wn2);
     const double im = __ldg(a.inv_mm + i) * a.ifmass;
     const double c2s = c2 * __ldg(a.sigv + i);
@@ -259,15 +288,15 @@ __global__ void __launch_bounds__(256) k_step_cart_f64(StepArgs a) {
     if (a.integrator == 0) {
       v = fma(a.kick * im, f, v);
       x = fma(a.half, v, x);
-      if (a.thermo) v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+      if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
       x = fma(a.half, v, x);
     } else {
       const double kb = a.half * im;
       if (!a.first) {
         v = fma(kb, f, v);
-        if (a.thermo) v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, d));
+        if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO2, step - 1, sE2));
       }
-      if (a.thermo) v = fma(c1, v, c2s * gauss1(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, d));
+      if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
       v = fma(kb, f, v);
       x = fma(2.0 * a.half, v, x);
     }
@@ -517,11 +546,19 @@ __global__ void k_nap_to_pna(const double *src, double *dst, int N, int P) {
 }
 
 // --- host launchers --------------------------------------------------------
-size_t step_smem_bytes(int A, int P) { return (size_t)4 * A * 3 * P * sizeof(double); }
+size_t step_smem_bytes(int A, int P) { return ((size_t)6 * A * 3 * P + 3 * A) * sizeof(double); }
 size_t close_smem_bytes(int A, int P) { return (size_t)A * 3 * P * sizeof(double); }
 
-cudaError_t launch_step(const StepArgs &a, int threads, cudaStream_t s) {
-  const int grid = (a.N + a.A - 1) / a.A;
+cudaError_t launch_step(const StepArgs &a0, int threads, cudaStream_t s) {
+  const int grid = (a0.N + a0.A - 1) / a0.A;
+  StepArgs a = a0;
+  static int nsm = 0;   // SM count of the device (one GPU per process)
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 152;
+  }
+  a.noise_pre = grid >= 4 * nsm ? 1 : 0;
   if (a.method == 1) {
     k_step_cart_f64<<<grid, threads, step_smem_bytes(a.A, a.P), s>>>(a);
     return cudaGetLastError();
