@@ -1252,18 +1252,12 @@ __global__ void k_bnbr(const RepDesc *reps, const int2 *items, const int *count)
 // no cross-lane reduction.  The list is grouped by j mod NS and index-ordered
 // within a group, so the summation order depends only on the interacting
 // pairs (far candidates add nothing): alone-vs-mix and rebuild invariant.
-__global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps, const int4 *__restrict__ items,
-                                                const int *__restrict__ count, int force_all) {
-  const int n = *count;
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int it = gw; it < n; it += nw) {
-    const int4 w = items[it];
-    const RepDesc *__restrict__ Rp = reps + w.x;
-    if (!force_all && !Rp->ctl[kCtlActive]) continue;
-    const RepDesc &R = *Rp;
-    const int P = R.P;
+// One work item of k_bforce; PT > 0 fixes the bead count at compile time
+// (constant strides and lane split), PT = 0 reads it from the descriptor.
+template <int PT>
+__device__ __forceinline__ void bforce_item(const RepDesc &R, const int4 w, int lane) {
+  {
+    const int P = PT > 0 ? PT : R.P;
     const float *__restrict__ dg = R.d;
     const float *__restrict__ xcw = R.xcw;
     const int Bk = P < 32 ? P : 32;
@@ -1271,7 +1265,7 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
     const int u = lane / Bk, kl = lane % Bk;
     const int m = w.y + u;
     const int k = w.z * Bk + kl;
-    if (u >= G || m >= R.nmol || k >= P) continue;
+    if (u >= G || m >= R.nmol || k >= P) return;
     const int o = 3 * m;
     const float L0 = R.boxf[0], L1 = R.boxf[1], L2 = R.boxf[2];
     const float i0 = R.invboxf[0], i1 = R.invboxf[1], i2 = R.invboxf[2];
@@ -1331,7 +1325,7 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
     const int *off = R.nbr_off + (size_t)m * (NS + 1);
     const int q1 = __ldg(off + NS);
     const int *__restrict__ nl = R.nbr + (size_t)m * kMaxNeighbours;
-    const float rc2 = R.rc2f, sig2 = R.sig2f, e4 = R.e4f, e24 = R.e24f;
+    const float rc2 = R.rc2f, sig2 = R.sig2f, e4 = R.e4f, e24 = R.e24f, e48 = 2.0f * R.e24f;
     const float *__restrict__ pO = R.pO;
     const size_t sm = (size_t)m * 3 * P + k;
     const float po0 = pO[sm], po1 = pO[sm + P], po2 = pO[sm + 2 * P];
@@ -1346,11 +1340,12 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
       const float d2 = micb(__ldg(pO + sj + 2 * P) - po2, L2, i2);
       const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
       if (r2 < rc2) {
-        const float inv = __frcp_rn(r2);
+        // 4 eps (s^12 - s^6) = s6 (e4 s6 - e4); f r = 24 eps (2 s^12 - s^6) / r^2 = s6 (e48 s6 - e24) / r^2
+        const float inv = __fdividef(1.0f, r2);
         const float s2 = sig2 * inv;
         const float s6 = s2 * s2 * s2;
-        ulj = fmaf(e4, fmaf(s6, s6, -s6), ulj);
-        const float fr = e24 * fmaf(2.f * s6, s6, -s6) * inv;
+        ulj = fmaf(s6, fmaf(e4, s6, -e4), ulj);
+        const float fr = fmaf(e48, s6, -e24) * s6 * inv;
         fO[0] = fmaf(-fr, d0, fO[0]);
         fO[1] = fmaf(-fr, d1, fO[1]);
         fO[2] = fmaf(-fr, d2, fO[2]);
@@ -1365,6 +1360,26 @@ __global__ void __launch_bounds__(128) k_bforce(const RepDesc *__restrict__ reps
     }
     R.Upart[(size_t)m * P + k] = (double)fmaf(0.5f, ulj, ub);
     R.Wpart[(size_t)m * P + k] = (double)fmaf(0.5f, wlj, wb);
+  }
+}
+
+__global__ void __launch_bounds__(128, 6) k_bforce(const RepDesc *__restrict__ reps, const int4 *__restrict__ items,
+                                                const int *__restrict__ count, int force_all) {
+  const int n = *count;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int it = gw; it < n; it += nw) {
+    const int4 w = items[it];
+    const RepDesc *__restrict__ Rp = reps + w.x;
+    if (!force_all && !Rp->ctl[kCtlActive]) continue;
+    switch (Rp->P) {
+      case 8: bforce_item<8>(*Rp, w, lane); break;
+      case 16: bforce_item<16>(*Rp, w, lane); break;
+      case 32: bforce_item<32>(*Rp, w, lane); break;
+      case 64: bforce_item<64>(*Rp, w, lane); break;
+      default: bforce_item<0>(*Rp, w, lane); break;
+    }
   }
 }
 
