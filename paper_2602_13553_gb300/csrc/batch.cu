@@ -56,6 +56,7 @@ constexpr int kBatchMaxMol = 4096;   // molecules per replica (centroids staged 
 constexpr int kNbrMolPerItem = 8;    // molecules per neighbour-list work item
 constexpr size_t kNbrSmem = 3 * kBatchMaxMol * sizeof(float);
 constexpr int kOutStride = 3 * kMaxBeads + 10;  // pimd_estimates layout from K_mode on
+constexpr int kEstItems = 64;        // estimator work items (e-blocks) per replica, at most
 // Per-replica control words.  kCtlSkin holds two 32-bit maxima of this step
 // (bit patterns of non-negative floats, merged by atomicMax): the squared
 // centroid drift of the oxygens since the last rebuild and their squared bead
@@ -1617,7 +1618,7 @@ size_t layout_replica(Replica &r, char *base) {
   d.nbr_off = carve_ptr<int>(base, off, nmol * (NS + 1));
   d.Upart = carve_ptr<double>(base, off, nmol * P);
   d.Wpart = carve_ptr<double>(base, off, nmol * P);
-  d.epart = carve_ptr<double>(base, off, 8 * (2 * P + 4));
+  d.epart = carve_ptr<double>(base, off, kEstItems * (2 * P + 4));
   r.d_items_step = carve_ptr<int2>(base, off, N);
   r.d_items_nbr = carve_ptr<int2>(base, off, (nmol + kNbrMolPerItem - 1) / kNbrMolPerItem);
   r.d_items_clu = carve_ptr<int4>(base, off, nmol * ((P + 31) / 32));
@@ -1704,7 +1705,7 @@ pimd_status grow(pimd_batch *b, T **ptr, size_t *cap, size_t need) {
 void replica_items(pimd_batch *b, int slot, Replica &r) {
   r.A = warp_class(r.P) ? kWAtoms : (b->tileA[r.P] > 0 ? b->tileA[r.P] : default_tile(r.P));
   r.ntiles = (r.N + r.A - 1) / r.A;
-  r.ne = std::min(r.ntiles, 8);
+  r.ne = std::min(r.ntiles, kEstItems);
   r.items_step.clear();
   for (int t = 0; t < r.ntiles; ++t) r.items_step.push_back(make_int2(slot, t));
   r.items_nbr.clear();
@@ -1717,7 +1718,7 @@ void replica_items(pimd_batch *b, int slot, Replica &r) {
     for (int c = 0; c < nchunk; ++c) r.items_clu.push_back(make_int4(slot, m, c, 0));
   r.items_est.clear();
   const int Ae = r.P >= 128 ? 1 : 128 / r.P;
-  r.ne = std::min((r.N + Ae - 1) / Ae, 8);
+  r.ne = std::min((r.N + Ae - 1) / Ae, kEstItems);
   for (int e = 0; e < r.ne; ++e) r.items_est.push_back(make_int2(slot, e));
   r.desc.A = r.A;
   r.desc.nstep_items = r.ntiles;
@@ -1979,7 +1980,7 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
   b->grid_step = occ((const void *)k_bstep);
   b->grid_clu = occ((const void *)k_bforce);
   b->grid_nbr = occ((const void *)k_bnbr, kNbrSmem);
-  b->grid_est = 2 * nsm;
+  b->grid_est = 8 * nsm;
   auto fail_free = [&](pimd_status st) {
     pimd_batch_destroy(b);
     return st;

@@ -355,6 +355,14 @@ static ForceArgs force_args(pimd_handle *h) {
   a.nbr = h->nbr;
   a.nbr_off = h->nbr_off;
   a.nbr_groups = h->nbr_groups;
+  a.check_nbr = 0;
+  a.blkmax = h->blkmax;
+  a.nblk_check = (h->N + h->A_step - 1) / h->A_step;
+  a.skin = h->skin;
+  a.rlist = h->rlist;
+  a.ccur = h->ccur;
+  a.cref = h->cref;
+  a.err = h->d_err;
   return a;
 }
 
@@ -498,10 +506,14 @@ static pimd_status enqueue_forces(pimd_handle *h, bool from_outside, bool advanc
       });
       if (st != PIMD_OK) return st;
     }
-    st = enqueue(h, PIMD_KIND_NBR, 1, [&] {
-      return launch_nbr_build(nbr_args(h, from_outside), h->ccur, h->stream);
-    });
-    if (st != PIMD_OK) return st;
+    if (from_outside) {
+      st = enqueue(h, PIMD_KIND_NBR, 1, [&] {
+        return launch_nbr_build(nbr_args(h, true), h->ccur, h->stream);
+      });
+      if (st != PIMD_OK) return st;
+    } else {
+      fa.check_nbr = 1;   // the skin test and any rebuild run inside the force kernel
+    }
     return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_water(fa, h->stream); });
   }
   return enqueue(h, PIMD_KIND_FORCE, 1, [&] { return launch_force_harmonic(fa, h->stream); });

@@ -196,9 +196,19 @@ struct ForceArgs {
   const double *kspring;       // harmonic: [N] m mvv2e omega^2
   double box[3], invbox[3];
   double kb, r0, kth, th0, eps, sig, rc;
-  const int *nbr;              // [nmol][kMaxNeighbours] neighbours grouped by bucket j mod NS
-  const int *nbr_off;          // [nmol][NS + 1] bucket offsets into the molecule's row
+  int *nbr;                    // [nmol][kMaxNeighbours] neighbours grouped by bucket j mod NS
+  int *nbr_off;                // [nmol][NS + 1] bucket offsets into the molecule's row
   int nbr_groups;              // G: lane groups per warp; NS = kLJWarps * G buckets
+  // check_nbr: the force kernel itself takes the step's rebuild decision
+  // (the skin test of k_nbr_build on the step kernel's per-block maxima) and,
+  // when it rebuilds, lists its molecule's neighbours before the pair loop
+  int check_nbr;
+  const double *blkmax;        // [nblk_check][2]
+  int nblk_check;
+  double skin, rlist;
+  const double *ccur;          // [nmol][3] current centroids of the oxygens
+  double *cref;                // [nmol][3] centroids at the last build (written on rebuild)
+  unsigned *err;
 };
 
 struct NbrArgs {

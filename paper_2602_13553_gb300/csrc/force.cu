@@ -98,6 +98,69 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
   double acc[11];
 #pragma unroll
   for (int c = 0; c < 11; ++c) acc[c] = 0.0;
+  // the neighbour list of molecule m: the stored one, or rebuilt here when
+  // this step's skin test fails (every block takes the same decision from the
+  // same maxima and builds the same list into its own shared memory; the
+  // cluster of chunk 0 also stores it and the new reference centroid)
+  __shared__ int s_nl[kMaxNeighbours];
+  __shared__ int s_off[kMaxBuckets + 1];
+  __shared__ int s_go;
+  if (a.check_nbr) {
+    if (warp == 0) {
+      double md = 0.0, me = 0.0;
+      for (int b = lane; b < a.nblk_check; b += 32) {
+        md = fmax(md, a.blkmax[2 * b]);
+        me = fmax(me, a.blkmax[2 * b + 1]);
+      }
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o2));
+        me = fmax(me, __shfl_xor_sync(0xffffffffu, me, o2));
+      }
+      int go = 2.0 * md + 2.0 * me > a.skin;
+      if (go && m < a.nmol) {
+        // bucket b holds the neighbours j = b mod NS in increasing j
+        const bool db0 = a.dbox != nullptr;
+        const double B0 = db0 ? a.dbox[0] : a.box[0], B1 = db0 ? a.dbox[1] : a.box[1], B2 = db0 ? a.dbox[2] : a.box[2];
+        const double I0 = db0 ? a.dbox[3] : a.invbox[0], I1 = db0 ? a.dbox[4] : a.invbox[1];
+        const double I2 = db0 ? a.dbox[5] : a.invbox[2];
+        const double c0 = a.ccur[3 * m], c1 = a.ccur[3 * m + 1], c2 = a.ccur[3 * m + 2];
+        const double rl2 = a.rlist * a.rlist;
+        int total = 0;
+        for (int b = 0; b < NS; ++b) {
+          if (lane == 0) s_off[b] = total;
+          for (int j0 = b; j0 < a.nmol; j0 += 32 * NS) {
+            const int j = j0 + lane * NS;
+            bool hit = false;
+            if (j < a.nmol && j != m) {
+              const double d0 = mic(a.ccur[3 * j] - c0, B0, I0);
+              const double d1 = mic(a.ccur[3 * j + 1] - c1, B1, I1);
+              const double d2 = mic(a.ccur[3 * j + 2] - c2, B2, I2);
+              hit = d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, hit);
+            const int pos = total + __popc(mask & ((1u << lane) - 1u));
+            if (hit && pos < kMaxNeighbours) s_nl[pos] = j;
+            total += __popc(mask);
+          }
+        }
+        if (total > kMaxNeighbours) {   // report, and use an empty list
+          if (lane == 0 && rank == 0 && chunk == 0) atomicOr(a.err, kErrNbrOverflow);
+          for (int b = lane; b <= NS; b += 32) s_off[b] = 0;
+          total = 0;
+        }
+        if (lane == 0) s_off[NS] = total;
+        __syncwarp();
+        if (rank == 0 && chunk == 0) {   // keep it for the following steps
+          for (int q = lane; q < total; q += 32) a.nbr[(size_t)m * kMaxNeighbours + q] = s_nl[q];
+          for (int b = lane; b <= NS; b += 32) a.nbr_off[(size_t)m * (NS + 1) + b] = s_off[b];
+          if (lane < 3 && total <= kMaxNeighbours) a.cref[3 * m + lane] = a.ccur[3 * m + lane];
+        }
+      }
+      if (lane == 0) s_go = go;
+    }
+    __syncthreads();
+  }
   if (u < G && k < P && m < a.nmol) {
     const int o = 3 * m;
     const bool db = a.dbox != nullptr;
@@ -165,9 +228,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
     } else {
     // O-O Lennard-Jones over bucket b of the neighbour list
     const int b = s * G + u;          // neighbours j with j mod (kLJWarps G) = b
-    const int *off = a.nbr_off + (size_t)m * (NS + 1);
-    const int q0 = __ldg(off + b), q1 = __ldg(off + b + 1);
-    const int *nl = a.nbr + (size_t)m * kMaxNeighbours;
+    const bool own = a.check_nbr && s_go;   // rebuilt in this block's shared memory
+    const int *off = own ? s_off : a.nbr_off + (size_t)m * (NS + 1);
+    const int q0 = off[b], q1 = off[b + 1];
+    const int *nl = own ? s_nl : a.nbr + (size_t)m * kMaxNeighbours;
     const float xf0 = a.x32[so], xf1 = a.x32[so + P], xf2 = a.x32[so + 2 * P];
     const float Lf0 = (float)L0, Lf1 = (float)L1, Lf2 = (float)L2;
     const float if0 = (float)i0, if1 = (float)i1, if2 = (float)i2;
@@ -178,7 +242,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
     const double e4 = 4.0 * a.eps, e24 = 24.0 * a.eps;
     double f0 = 0.0, f1 = 0.0, f2 = 0.0, ulj = 0.0, wlj = 0.0;
     for (int q = q0; q < q1; ++q) {
-      const int j = __ldg(nl + q);
+      const int j = nl[q];
       const size_t sj = (size_t)(3 * j) * 3 * P + k;
       float d0f = __ldg(a.x32 + sj) - xf0, d1f = __ldg(a.x32 + sj + P) - xf1;
       float d2f = __ldg(a.x32 + sj + 2 * P) - xf2;
