@@ -115,3 +115,38 @@ def test_autotune_changes_no_trajectory(pimd):
         x2, v2, s2 = plain.get_state(p)
         assert s1 == s2 == used + 30
         assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+
+
+def test_full_replica_mix_sampled_against_oracle(orc, pimd):
+    """The 256-replica mix of the benchmark (32-512 molecules, P in {8, 16, 32,
+    64}, T 100-400 K, H or D), autotuned launch shape as in bench.py, 20 steps;
+    four replicas sampled across the mix (the largest, a P = 64, a P = 8 and a
+    deuterated one) are compared with the oracle one by one."""
+    reps = inputs.replica_mix(256, seed=1)
+    b = pimd.Batch(256)
+    systems = []
+    for r in reps:
+        x0, mass = inputs.water_box(r.nmol, r.L, r.P, r.seed, jitter=0.02, deuterium=r.deuterium)
+        kw = dict(T=r.T, dt=5e-4, ff=inputs.water_ff_for_box(r.L), box=(r.L,) * 3, seed=r.seed)
+        systems.append((x0, mass, kw))
+        b.add(x0, mass, nsteps=10 ** 9, **kw)
+    b.autotune(1)
+    st0, _ = b.status()
+    used = int(st0[0])
+    b.run(20)
+    picks = {max(range(256), key=lambda i: reps[i].nmol),
+             next(i for i in range(256) if reps[i].P == 64),
+             next(i for i in range(256) if reps[i].P == 8),
+             next(i for i in range(256) if reps[i].deuterium and reps[i].P == 16)}
+    est = b.estimators()
+    for s in sorted(picks):
+        x0, mass, kw = systems[s]
+        c = orc.Sim(x0, mass, potential=1, **kw)
+        c.run(used + 20)
+        x, v, st = b.get_state(s)
+        assert st == used + 20
+        assert np.max(np.abs(x - c.x)) < 1e-4, s
+        ec = c.estimators()
+        for k in ("K_CV", "T_ring"):
+            assert abs(est[s][k] - ec[k]) < 1e-3 * abs(ec[k]), (s, k)
+    b.close()
