@@ -40,6 +40,7 @@ FM_PHYSICAL = 0
 FM_NORMAL = 1
 BARO_NONE = 0
 BARO_BZP = 1      # isotropic BZP barostat (App. E), BAOAB only
+BARO_BZP_ANISO = 2  # one BZP barostat per axis in baro_axes (bits x = 1, y = 2, z = 4)
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +77,8 @@ class _Sim(ctypes.Structure):
         ("fmass", ctypes.c_double),
         ("barostat", ctypes.c_int32), ("pad1", ctypes.c_int32),
         ("pext", ctypes.c_double), ("taup", ctypes.c_double), ("vW", ctypes.c_double),
+        ("baro_axes", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("vWa", ctypes.c_double * 3), ("vir3", ctypes.c_double * 384),
     ]
 
 
@@ -90,6 +93,7 @@ class _Est(ctypes.Structure):
         ("volume", ctypes.c_double), ("vir_sum", ctypes.c_double),
         ("vW", ctypes.c_double), ("K_W", ctypes.c_double), ("U_W", ctypes.c_double),
         ("J_W", ctypes.c_double), ("enthalpy", ctypes.c_double),
+        ("vWa", ctypes.c_double * 3),
     ]
 
 
@@ -238,12 +242,14 @@ class Sim:
     masses; fixcom removes the centre-of-mass velocity every step.  barostat 1
     = isotropic BZP (App. E, BAOAB, normal modes) at pext (eV/A^3) with
     barostat time taup (ps); NpH without a thermostat, NpT with PILE_L.
+    barostat 2 = anisotropic BZP: one barostat per box edge in the bit mask
+    baro_axes (x = 1, y = 2, z = 4), the other edges fixed.
     """
 
     def __init__(self, x0, mass, *, T, dt, potential=POT_HARMONIC, ff=(0.0,), box=(0.0, 0.0, 0.0),
                  v0=None, thermostat=1, integrator=BAOAB, seed=1, tau=1.0, scale=1.0, sp=1.0,
                  method=NMPIMD, fmmode=FM_PHYSICAL, fmass=1.0, fixcom=0, barostat=BARO_NONE,
-                 pext=0.0, taup=1.0, vW=0.0):
+                 pext=0.0, taup=1.0, vW=0.0, baro_axes=7):
         assert barostat == BARO_NONE or (integrator == BAOAB and method == NMPIMD and potential == POT_WATERLIKE)
         x0 = np.ascontiguousarray(x0, dtype=np.float64)
         P, N, three = x0.shape
@@ -261,6 +267,7 @@ class Sim:
         s.potential, s.thermostat, s.integrator = potential, thermostat, integrator
         s.method, s.fmmode, s.fixcom, s.fmass = method, fmmode, int(fixcom), float(fmass)
         s.barostat, s.pext, s.taup, s.vW = int(barostat), float(pext), float(taup), float(vW)
+        s.baro_axes = int(baro_axes)
         s.T, s.dt, s.tau, s.scale, s.sp = T, dt, tau, scale, sp
         s.seed = seed
         for a in range(3):
@@ -288,6 +295,10 @@ class Sim:
     def vW(self) -> float:
         return float(self._s.vW)
 
+    @property
+    def vWa(self) -> np.ndarray:
+        return np.array(list(self._s.vWa))
+
     def run(self, nsteps: int) -> None:
         lib().or_run(ctypes.byref(self._s), int(nsteps))
 
@@ -302,6 +313,7 @@ class Sim:
                                           "T_ring", "volume", "vir_sum", "vW", "K_W", "U_W", "J_W",
                                           "enthalpy")}
         out["step"] = int(e.step)
+        out["vWa"] = np.array(list(e.vWa))
         out["K_mode"] = np.array(e.K_mode[:P])
         out["S_mode"] = np.array(e.S_mode[:P])
         out["U_bead"] = np.array(e.U_bead[:P])

@@ -240,14 +240,15 @@ void or_force_harmonic(int N, const double *mass, double omega, const double *x,
  *     + sum_{O-O pairs, r < rc} 4 eps [(sig/r)^12 - (sig/r)^6]   (no shift)
  * ff = {kb, r0, kth, th0 (rad), eps, sig, rc}.  All pair vectors are minimum
  * image.  *vir = Tr Xi = sum over interaction terms of r_rel . f (App. A,
- * virial of the bead).  x, F: [3*nmol][3]. */
-void or_force_water(int nmol, const double box[3], const double ff[7], const double *x,
-                    double *F, double *U, double *vir) {
+ * virial of the bead); vir3 (or NULL) receives the diagonal Xi_aa, summed per
+ * component a (App. E, the anisotropic barostat).  x, F: [3*nmol][3]. */
+void or_force_water_v(int nmol, const double box[3], const double ff[7], const double *x,
+                      double *F, double *U, double *vir, double *vir3) {
   const double kb = ff[0], r0 = ff[1], kth = ff[2], th0 = ff[3];
   const double eps = ff[4], sig = ff[5], rc = ff[6];
   int N = 3 * nmol;
   for (int i = 0; i < 3 * N; ++i) F[i] = 0.0;
-  double u = 0.0, w = 0.0;
+  double u = 0.0, w = 0.0, w3[3] = {0.0, 0.0, 0.0};
   for (int m = 0; m < nmol; ++m) {
     int o = 3 * m;
     double dv[2][3], r[2];
@@ -263,6 +264,7 @@ void or_force_water(int nmol, const double box[3], const double ff[7], const dou
         F[3 * hh + a] += fa;
         F[3 * o + a] -= fa;
         w += dv[h][a] * fa;
+        w3[a] += dv[h][a] * fa;
       }
     }
     /* angle H1-O-H2 */
@@ -284,6 +286,7 @@ void or_force_water(int nmol, const double box[3], const double ff[7], const dou
         F[3 * hh + a] += fa;
         F[3 * o + a] -= fa;
         w += dv[h][a] * fa;
+        w3[a] += dv[h][a] * fa;
       }
     }
   }
@@ -303,12 +306,20 @@ void or_force_water(int nmol, const double box[3], const double ff[7], const dou
           F[3 * oj + a] += fr * d[a];
           F[3 * oi + a] -= fr * d[a];
           w += d[a] * fr * d[a];
+          w3[a] += d[a] * fr * d[a];
         }
       }
     }
   }
   *U = u;
   *vir = w;
+  if (vir3)
+    for (int a = 0; a < 3; ++a) vir3[a] = w3[a];
+}
+
+void or_force_water(int nmol, const double box[3], const double ff[7], const double *x,
+                    double *F, double *U, double *vir) {
+  or_force_water_v(nmol, box, ff, x, F, U, vir, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -336,6 +347,10 @@ typedef struct {
   double pext;         /* target pressure (eV/A^3) */
   double taup;         /* barostat time (ps): W = 3 P N kB T taup^2 (App. A output 12) */
   double vW;           /* barostat velocity (1/ps) */
+  int32_t baro_axes;   /* barostat 2 (anisotropic): axes that move, bits x = 1, y = 2, z = 4 */
+  int32_t pad2;
+  double vWa[3];       /* barostat 2: velocity of each axis (1/ps) */
+  double vir3[3 * 128]; /* [P][3] diagonal virial Xi_aa of every bead */
 } or_sim;
 
 /* Fictitious-mass factor of mode k (nmpimd), Sec. III.C keywords fmmode and
@@ -360,7 +375,7 @@ void or_compute_forces(or_sim *s) {
     if (s->potential == 0)
       or_force_harmonic(N, s->mass, s->ff[0], xk, Fk, &s->U[k], &s->vir[k]);
     else
-      or_force_water(N / 3, s->box, s->ff, xk, Fk, &s->U[k], &s->vir[k]);
+      or_force_water_v(N / 3, s->box, s->ff, xk, Fk, &s->U[k], &s->vir[k], &s->vir3[3 * k]);
   }
 }
 
@@ -604,6 +619,70 @@ static void or_O_baro(or_sim *s, double dtO) {
   s->vW = c1 * s->vW + c2 * sqrt(s->P * OR_KB * s->T / or_baro_W(s)) * eta[0];
 }
 
+/* ---- anisotropic BZP barostat (App. E, "aniso" / "x" "y" "z") ---------- */
+/* Each axis a in baro_axes has its own v_Wa with W = n N kB T taup^2:
+ *   v_Wa += (tB / W)[n V (P_CV^aa - P_ext) + n kB T] + (tB^2 / W) sum F~0a v~0a
+ *           + (tB^3 / 3W) sum F~0a^2 / m,
+ *   n V P_CV^aa = sum m v~0a^2 - sum (r - r_c)_a F_a + sum_k Xi^(k)_aa,
+ * the A steps scale component a of the centroid mode and L_a by
+ * exp(tA v_Wa), and O draws each v_Wa from component a of the barostat's
+ * deviates.  The printed 1/(n kB T) is read as n kB T, as for "iso". */
+static double or_baro_Wa(const or_sim *s) {
+  return s->P * s->N * OR_KB * s->T * s->taup * s->taup;
+}
+
+static void or_B_baro_aniso(or_sim *s, const double *M, double *Ft, double tB) {
+  int N = s->N, P = s->P;
+  or_to_nm(P, N, M, s->F, Ft);
+  double W = or_baro_Wa(s), V = s->box[0] * s->box[1] * s->box[2];
+  for (int a = 0; a < 3; ++a) {
+    if (!(s->baro_axes >> a & 1)) continue;
+    double mv2 = 0.0, Fv = 0.0, F2m = 0.0, vir = 0.0, rcF = 0.0;
+    for (int n = 0; n < N; ++n) {
+      double mm = s->mass[n] * or_mode_mu(s, 0) * OR_MVV2E;
+      double v0 = s->v[(size_t)n * 3 + a], f0 = Ft[(size_t)n * 3 + a];
+      mv2 += mm * v0 * v0;
+      Fv += f0 * v0;
+      F2m += f0 * f0 / mm;
+      double rc = 0.0;
+      for (int k = 0; k < P; ++k) rc += s->x[((size_t)k * N + n) * 3 + a];
+      rc /= P;
+      for (int k = 0; k < P; ++k) {
+        size_t id = ((size_t)k * N + n) * 3 + a;
+        rcF += (s->x[id] - rc) * s->F[id];
+      }
+    }
+    for (int k = 0; k < P; ++k) vir += s->vir3[3 * k + a];
+    s->vWa[a] += tB / W * (mv2 - rcF + vir - P * V * s->pext + P * OR_KB * s->T) + tB * tB / W * Fv +
+                 tB * tB * tB / (3.0 * W) * F2m;
+  }
+}
+
+static void or_A_baro_centroid_aniso(or_sim *s, double *q, double tA) {
+  int N = s->N;
+  for (int c = 0; c < 3; ++c) {
+    double vw = s->vWa[c];
+    double a = tA * vw;
+    double ea = exp(a), ema = exp(-a);
+    double sh = fabs(a) < 1e-8 ? tA * (1.0 + a * a / 6.0) : (ea - ema) / (2.0 * vw);
+    for (int n = 0; n < N; ++n) {
+      size_t id = (size_t)n * 3 + c;
+      q[id] = ea * q[id] + sh * s->v[id];
+      s->v[id] = ema * s->v[id];
+    }
+    s->box[c] *= ea;
+  }
+}
+
+static void or_O_baro_aniso(or_sim *s, double dtO) {
+  double c1 = exp(-dtO / s->tau), c2 = sqrt(1.0 - c1 * c1);
+  double eta[3];
+  or_gauss3(s->seed, 0xffffffffu, 0u, 3u, (uint64_t)s->step, eta);
+  double sig = sqrt(s->P * OR_KB * s->T / or_baro_Wa(s));
+  for (int a = 0; a < 3; ++a)
+    if (s->baro_axes >> a & 1) s->vWa[a] = c1 * s->vWa[a] + c2 * sig * eta[a];
+}
+
 /* n steps.  BAOAB: B(h/2) A(h/2) O(h) A(h/2) [forces] B(h/2).
  *           OBABO: O(h/2) B(h/2) A(h) [forces] B(h/2) O(h/2).
  * The O sub-steps are skipped when thermostat == 0 (NVE); with fixcom the
@@ -639,18 +718,24 @@ void or_run(or_sim *s, int64_t nsteps) {
         if (s->thermostat) or_O_cart(s, wn, 0.5 * h, 1u);
       }
     } else if (s->integrator == 0) {
-      if (s->barostat) or_B_baro(s, M, Ft, 0.5 * h);
+      int iso = s->barostat == 1, ani = s->barostat == 2;
+      if (iso) or_B_baro(s, M, Ft, 0.5 * h);
+      if (ani) or_B_baro_aniso(s, M, Ft, 0.5 * h);
       or_B(s, M, Ft, 0.5 * h);
       or_to_nm(P, N, M, s->x, q);
       or_A(s, omega, q, 0.5 * h);
-      if (s->barostat) or_A_baro_centroid(s, q, 0.5 * h);
+      if (iso) or_A_baro_centroid(s, q, 0.5 * h);
+      if (ani) or_A_baro_centroid_aniso(s, q, 0.5 * h);
       if (s->thermostat) or_O(s, omega, h, 0u);
-      if (s->thermostat && s->barostat) or_O_baro(s, h);
+      if (s->thermostat && iso) or_O_baro(s, h);
+      if (s->thermostat && ani) or_O_baro_aniso(s, h);
       or_A(s, omega, q, 0.5 * h);
-      if (s->barostat) or_A_baro_centroid(s, q, 0.5 * h);
+      if (iso) or_A_baro_centroid(s, q, 0.5 * h);
+      if (ani) or_A_baro_centroid_aniso(s, q, 0.5 * h);
       or_from_nm(P, N, M, q, s->x);
       or_compute_forces(s);
-      if (s->barostat) or_B_baro(s, M, Ft, 0.5 * h);
+      if (iso) or_B_baro(s, M, Ft, 0.5 * h);
+      if (ani) or_B_baro_aniso(s, M, Ft, 0.5 * h);
       or_B(s, M, Ft, 0.5 * h);
     } else {
       if (s->thermostat) or_O(s, omega, 0.5 * h, 0u);
@@ -678,6 +763,7 @@ typedef struct {
   double H, K_PR, K_VR, K_CV, P_PR, P_MD, P_CV, T_ring;
   double volume, vir_sum;
   double vW, K_W, U_W, J_W, enthalpy;   /* App. A outputs 11-15 (barostat) */
+  double vWa[3];                        /* output 11, anisotropic barostat */
 } or_estimates;
 
 void or_estimators(const or_sim *s, or_estimates *e) {
@@ -780,8 +866,21 @@ void or_estimators(const or_sim *s, or_estimates *e) {
   if (s->barostat) {                                             /* outputs 11-15 */
     e->vW = s->vW;
     e->K_W = 0.5 * or_baro_W(s) * s->vW * s->vW;
+    if (s->barostat == 2) {
+      e->vW = 0.0;
+      e->K_W = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        e->vWa[a] = s->vWa[a];
+        e->K_W += 0.5 * or_baro_Wa(s) * s->vWa[a] * s->vWa[a];
+      }
+    }
     e->U_W = P * s->pext * V;
     e->J_W = -P * kT * log(V);
+    if (s->barostat == 2) {           /* one ln L_a per barostat axis */
+      e->J_W = 0.0;
+      for (int a = 0; a < 3; ++a)
+        if (s->baro_axes >> a & 1) e->J_W -= P * kT * log(s->box[a]);
+    }
     e->enthalpy = e->H + e->K_W + e->U_W + e->J_W;
   }
   free(M); free(lam); free(q);

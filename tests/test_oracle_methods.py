@@ -313,3 +313,64 @@ def test_bzp_npt_ideal_gas_volume(orc):
     target = (N + 1) * KB * T / pext
     assert abs(mu - target) < 3 * sig, (mu, target, sig)
     assert abs(mu - N * KB * T / pext) > 3 * sig        # distinguishes the + 1
+
+
+# ---- BZP barostat (App. E), anisotropic: one v_W per box edge --------------
+
+def test_bzp_aniso_nph_conserves_the_extended_enthalpy(orc):
+    """NpH with all three edges free: output 15 (with K_W summed over the axes
+    and J_W = -n kB T sum_a ln L_a) is conserved with a second-order error, and
+    the three edges move apart from one another."""
+    x0, mass, kw = _bonded_water(16, 4, 43)
+    probe = orc.Sim(x0, mass, T=300.0, dt=1e-4, thermostat=0, **kw)
+    pext = probe.estimators()["P_CV"]
+    errs = []
+    for dt in (2e-4, 1e-4):
+        s = orc.Sim(x0, mass, T=300.0, dt=dt, thermostat=0, barostat=2, baro_axes=7, pext=pext,
+                    taup=0.02, **kw)
+        e0 = s.estimators()["enthalpy"]
+        dev = 0.0
+        for _ in range(int(round(0.04 / dt / 10))):
+            s.run(10)
+            dev = max(dev, abs(s.estimators()["enthalpy"] - e0))
+        errs.append(dev)
+        rel = s.box / kw["box"][0] - 1.0
+        assert np.abs(rel).min() > 1e-4                     # every edge moved
+        assert np.ptp(rel) > 1e-4                           # and not together
+    assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+def test_bzp_aniso_masked_axes_stay_fixed(orc):
+    """baro_axes = z: v_Wx = v_Wy = 0 and L_x, L_y unchanged through NpT; the
+    x and y centroid components then follow the barostat-free step."""
+    x0, mass, kw = _bonded_water(8, 4, 44)
+    s = orc.Sim(x0, mass, T=300.0, dt=5e-4, thermostat=1, seed=3, barostat=2, baro_axes=4,
+                pext=1e-3, taup=0.05, **kw)
+    s.run(60)
+    assert s.vWa[0] == 0.0 and s.vWa[1] == 0.0 and s.vWa[2] != 0.0
+    assert s.box[0] == kw["box"][0] and s.box[1] == kw["box"][1]
+    assert s.box[2] != kw["box"][2]
+
+
+def test_bzp_aniso_one_axis_ideal_gas_length(orc):
+    """NpT, free atoms, only L_z free: L_z samples L^N exp(-P_ext A L / kB T) dL,
+    so <L_z> = (N + 1) kB T / (P_ext L_x L_y)."""
+    P, N, T = 4, 6, 300.0
+    L0 = 10.0
+    g = np.random.default_rng(6)
+    x0 = np.repeat(g.uniform(0, L0, size=(1, N, 3)), P, axis=0) + g.normal(0, 0.05, size=(P, N, 3))
+    mass = np.full(N, 16.0)
+    ff = (0.0, 1.0, 0.0, 1.8, 0.0, 1.0, 0.5)
+    pext = (N + 1) * KB * T / L0 ** 3
+    s = orc.Sim(x0, mass, T=T, dt=2e-3, potential=1, ff=ff, box=(L0, L0, L0), thermostat=1, tau=0.05,
+                seed=11, barostat=2, baro_axes=4, pext=pext, taup=0.05)
+    s.run(2000)
+    lz = []
+    for _ in range(3000):
+        s.run(20)
+        lz.append(s.box[2])
+    from tests._stats import block_mean_sigma
+    mu, sig = block_mean_sigma(lz, 30)
+    target = (N + 1) * KB * T / (pext * L0 * L0)
+    assert abs(mu - target) < 3 * sig, (mu, target, sig)
+    assert abs(mu - N * KB * T / (pext * L0 * L0)) > 3 * sig
