@@ -70,10 +70,13 @@ enum { PIMD_METHOD_NMPIMD = 0, PIMD_METHOD_PIMD = 1 };
  * m^(k) = m (physical) or lambda_k m (normal, k >= 1; the centroid keeps m
  * because lambda_0 = 0).  Every internal mode then oscillates at omega_n. */
 enum { PIMD_FMMODE_PHYSICAL = 0, PIMD_FMMODE_NORMAL = 1 };
-/* Sec. III.C keywords "barostat" / "iso", App. E: none (NVE/NVT) or the
- * isotropic Bussi-Zykova-Parrinello barostat on the centroid mode (NpH
- * without a thermostat, NpT with PILE_L, which also thermostats v_W). */
-enum { PIMD_BARO_NONE = 0, PIMD_BARO_BZP_ISO = 1 };
+/* Sec. III.C keywords "barostat" / "iso" / "aniso" / "x" "y" "z", App. E:
+ * none (NVE/NVT), the isotropic Bussi-Zykova-Parrinello barostat on the
+ * centroid mode, or the anisotropic one (one v_W per box edge in baro_axes);
+ * NpH without a thermostat, NpT with PILE_L, which also thermostats v_W. */
+enum { PIMD_BARO_NONE = 0, PIMD_BARO_BZP_ISO = 1, PIMD_BARO_BZP_ANISO = 2 };
+/* bits of pimd_params.baro_axes (anisotropic barostat only) */
+enum { PIMD_AXIS_X = 1, PIMD_AXIS_Y = 2, PIMD_AXIS_Z = 4 };
 /* arithmetic of the step and force kernels:
  *   FP64   every quantity in FP64.
  *   SPLIT  the ring-polymer centroid (position and centroid-mode velocity) in
@@ -136,6 +139,16 @@ typedef struct {
  *           v_W <- c1 v_W + c2 sqrt(n kB T / W) eta (c1 = exp(-h / tau),
  *           Philox atom 0xffffffff, mode 0, stream 3).  n = P, W = 3 P N kB T
  *           taup^2.  Water-like periodic systems, BAOAB, method nmpimd, FP64.
+ *           PIMD_BARO_BZP_ANISO: each edge a in baro_axes has its own
+ *           v_Wa with W = P N kB T taup^2 and
+ *             v_Wa += (tB / W)[n V (P_CV^aa - P_ext) + n kB T]
+ *                     + (tB^2 / W) sum F~0a v~0a + (tB^3 / 3W) sum F~0a^2 / m,
+ *           n V P_CV^aa = sum m v~0a^2 - sum (r - r_c)_a F_a + sum_k Xi^(k)_aa;
+ *           the A steps scale component a of the centroid mode and L_a by
+ *           exp(tA v_Wa), the O step draws v_Wa from component a of the
+ *           same deviates; the other edges stay fixed.
+ *   baro_axes  PIMD_AXIS_* mask, nonzero (anisotropic barostat; ignored
+ *           otherwise; default all three).
  *   pext    target pressure (eV/A^3) of the barostat.
  *   taup    barostat time (ps) > 0.
  * method pimd, fmmode normal, fmass != 1, fixcom and the barostat run in FP64
@@ -154,7 +167,7 @@ typedef struct {
   int32_t fmmode;
   double fmass;
   int32_t barostat;
-  int32_t reserved;
+  int32_t baro_axes;
   double pext;
   double taup;
 } pimd_params;
@@ -178,8 +191,11 @@ typedef struct {
  *   T_ring     2 sum_k K^(k) / (3 N P kB): equals P T in equilibrium (Sec. IV.A)
  *   vW, K_W, U_W, J_W, enthalpy   outputs 11-15 with the barostat (zero
  *              without): v_W (1/ps), 1/2 W v_W^2, n P_ext V, -n kB T ln V and
- *              H + K_W + U_W + J_W, conserved in NpH (eV)
+ *              H + K_W + U_W + J_W, conserved in NpH (eV).  Anisotropic: vW
+ *              is 0, K_W = sum_a 1/2 W v_Wa^2 and J_W = -n kB T sum_a ln L_a
+ *              over the barostat axes
  *   box        the current box edges (A)
+ *   vWa        the anisotropic barostat's v_Wa per edge (1/ps; zero otherwise)
  * Pressures are eV/A^3 (NaN without a periodic box); volume in A^3;
  * vir_sum = sum_k Tr Xi^(k) (eV). */
 typedef struct {
@@ -193,6 +209,7 @@ typedef struct {
   double volume, vir_sum;
   double vW, K_W, U_W, J_W, enthalpy;
   double box[3];
+  double vWa[3];
 } pimd_estimates;
 
 /* Optional device allocator (for example a framework's caching allocator).
@@ -264,12 +281,14 @@ pimd_status pimd_get_state(pimd_handle *h, double *x, double *v_nm, int64_t *ste
  * counter, so a resumed run continues bit for bit. */
 pimd_status pimd_set_state(pimd_handle *h, const double *x, const double *v_nm, int64_t step);
 
-/* The barostat state (App. E) for checkpoints: *vW (1/ps) and box[3] (A).
- * get: either pointer may be NULL; set: EINVAL without a barostat or with a
- * box edge <= 2 rc; the forces are recomputed for the new box.  Both wait for
- * the handle's queued work. */
+/* The barostat state (App. E) for checkpoints: vW (1/ps) and box[3] (A).
+ * vW points to one double (isotropic) or three, x y z (anisotropic; edges
+ * outside baro_axes hold 0 and set requires 0 there).  get: either pointer
+ * may be NULL; set: EINVAL without a barostat or with a box edge <= 2 rc; the
+ * forces are recomputed for the new box.  Both wait for the handle's queued
+ * work. */
 pimd_status pimd_get_barostat(pimd_handle *h, double *vW, double *box);
-pimd_status pimd_set_barostat(pimd_handle *h, double vW, const double *box);
+pimd_status pimd_set_barostat(pimd_handle *h, const double *vW, const double *box);
 
 /* Release the handle and its device memory (waits for its queued work). */
 void pimd_destroy(pimd_handle *h);

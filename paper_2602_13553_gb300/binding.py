@@ -28,6 +28,8 @@ FMMODE_PHYSICAL = 0
 FMMODE_NORMAL = 1
 BARO_NONE = 0
 BARO_BZP_ISO = 1
+BARO_BZP_ANISO = 2
+AXIS_X, AXIS_Y, AXIS_Z = 1, 2, 4
 PREC_FP64 = 0
 PREC_SPLIT = 1
 MAX_BEADS = 128
@@ -62,7 +64,7 @@ class Params(ctypes.Structure):
         ("tau", ctypes.c_double), ("scale", ctypes.c_double), ("sp", ctypes.c_double),
         ("fixcom", ctypes.c_int32), ("fmmode", ctypes.c_int32),
         ("fmass", ctypes.c_double),
-        ("barostat", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("barostat", ctypes.c_int32), ("baro_axes", ctypes.c_int32),
         ("pext", ctypes.c_double), ("taup", ctypes.c_double),
     ]
 
@@ -79,6 +81,7 @@ class Estimates(ctypes.Structure):
         ("vW", ctypes.c_double), ("K_W", ctypes.c_double), ("U_W", ctypes.c_double),
         ("J_W", ctypes.c_double), ("enthalpy", ctypes.c_double),
         ("box", ctypes.c_double * 3),
+        ("vWa", ctypes.c_double * 3),
     ]
 
     def as_dict(self) -> dict:
@@ -87,6 +90,7 @@ class Estimates(ctypes.Structure):
                                              "T_ring", "volume", "vir_sum", "vW", "K_W", "U_W",
                                              "J_W", "enthalpy")}
         out["box"] = np.array(list(self.box))
+        out["vWa"] = np.array(list(self.vWa))
         out["step"] = int(self.step)
         out["K_mode"] = np.array(self.K_mode[:P])
         out["S_mode"] = np.array(self.S_mode[:P])
@@ -143,7 +147,7 @@ def lib():
         L.pimd_get_state.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_int64)]
         L.pimd_set_state.argtypes = [vp, dp, dp, ctypes.c_int64]
         L.pimd_get_barostat.argtypes = [vp, dp, dp]
-        L.pimd_set_barostat.argtypes = [vp, ctypes.c_double, dp]
+        L.pimd_set_barostat.argtypes = [vp, dp, dp]
         L.pimd_destroy.argtypes = [vp]
         L.pimd_destroy.restype = None
         L.pimd_set_kernel_timing.argtypes = [vp, ctypes.c_int]
@@ -175,7 +179,10 @@ def _dp(a):
 def default_params(**kw) -> Params:
     p = Params()
     lib().pimd_params_default(ctypes.byref(p))
+    names = {f[0] for f in Params._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown pimd_params field {k!r}")
         setattr(p, k, v)
     return p
 
@@ -214,7 +221,8 @@ class Simulation:
     x0: [P][N][3] positions (A); v0: [P][N][3] velocities -- normal-mode
     (method nmpimd) or bead (method pimd) -- or None (thermal draw).  Keyword
     arguments map onto pimd_params fields (thermostat, integrator, method,
-    precision, seed, tau, scale, sp, fixcom, fmmode, fmass).
+    precision, seed, tau, scale, sp, fixcom, fmmode, fmass, barostat, baro_axes,
+    pext, taup); an unknown name raises TypeError.
     """
 
     def __init__(self, x0, mass, *, T, dt, potential=POT_HARMONIC, ff=(0.0,), box=(0.0, 0.0, 0.0),
@@ -237,6 +245,7 @@ class Simulation:
         for a in range(8):
             s.ff[a] = float(ffl[a])
         prm = default_params(**params)
+        self._aniso = prm.barostat == BARO_BZP_ANISO
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream) if stream else None
         check(lib().pimd_create(ctypes.byref(s), P, T, dt, gamma0, ctypes.byref(prm), st,
@@ -267,15 +276,18 @@ class Simulation:
         check(lib().pimd_set_state(self._h, _dp(x), _dp(v), int(step)))
 
     def get_barostat(self):
-        """(v_W in 1/ps, box edges in A) of the barostat state."""
-        vw = np.zeros(1)
+        """(v_W in 1/ps, box edges in A) of the barostat state; v_W is a float
+        (isotropic) or an array of the three edges' v_Wa (anisotropic)."""
+        vw = np.zeros(3)
         box = np.zeros(3)
         check(lib().pimd_get_barostat(self._h, _dp(vw), _dp(box)))
-        return float(vw[0]), box
+        return (vw.copy() if self._aniso else float(vw[0])), box
 
-    def set_barostat(self, vW: float, box) -> None:
+    def set_barostat(self, vW, box) -> None:
         box = np.ascontiguousarray(box, dtype=np.float64)
-        check(lib().pimd_set_barostat(self._h, float(vW), _dp(box)))
+        vw = np.zeros(3)
+        vw[:] = np.asarray(vW, dtype=np.float64).reshape(-1)[:3] if self._aniso else float(vW)
+        check(lib().pimd_set_barostat(self._h, _dp(vw), _dp(box)))
 
     def set_kernel_timing(self, enable: bool) -> None:
         check(lib().pimd_set_kernel_timing(self._h, 1 if enable else 0))

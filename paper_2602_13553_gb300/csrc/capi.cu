@@ -130,6 +130,7 @@ extern "C" void pimd_params_default(pimd_params *p) {
   p->fmmode = PIMD_FMMODE_PHYSICAL;
   p->fmass = 1.0;
   p->barostat = PIMD_BARO_NONE;
+  p->baro_axes = PIMD_AXIS_X | PIMD_AXIS_Y | PIMD_AXIS_Z;
   p->pext = 0.0;
   p->taup = 1.0;
 }
@@ -140,6 +141,8 @@ extern "C" void pimd_params_default(pimd_params *p) {
 struct pimd_handle {
   int N = 0, P = 0, potential = 0, nmol = 0, integrator = 0, thermostat = 0, precision = 0;
   int method = 0, fixcom = 0, barostat = 0;
+  int baro_axes = 0;          // anisotropic barostat: mask of edges with their own v_W (0: isotropic)
+  double *W3part = nullptr;   // anisotropic barostat: [nmol][P][3] diagonal virial rows
   double T = 0, dt = 0, tau = 0, scale = 0, sp = 0, fmass = 1.0, pext = 0, taup = 0;
   double *baro = nullptr;     // device barostat state (kBaroWords), or null
   double h_baro[kBaroWords] = {0};
@@ -340,6 +343,7 @@ static ForceArgs force_args(pimd_handle *h) {
   a.F = h->F;
   a.Upart = h->Upart;
   a.Wpart = h->Wpart;
+  a.W3part = h->W3part;
   a.kspring = h->kspring;
   for (int d = 0; d < 3; ++d) {
     a.box[d] = h->box[d];
@@ -532,13 +536,15 @@ static pimd_status enqueue_baro(pimd_handle *h, double t0, double tB, bool step_
   b.Mt = h->Mt;
   b.mass_mm = h->mass_mm;
   b.Wpart = h->Wpart;
+  b.W3part = h->W3part;
+  b.axes = h->baro_axes;
   b.baro = h->baro;
   b.t0 = t0;
   b.tB = tB;
   b.tA = 0.5 * h->dt;
   b.step_follows = step_follows ? 1 : 0;
   const double kT = kBoltzmann * h->T;
-  b.W = 3.0 * h->P * h->N * kT * h->taup * h->taup;
+  b.W = (h->baro_axes ? 1.0 : 3.0) * h->P * h->N * kT * h->taup * h->taup;
   b.nkT = h->P * kT;
   b.npext = h->P * h->pext;
   b.mu0 = h->fmass;
@@ -725,6 +731,7 @@ static void carve(pimd_handle *h, Carver &c) {
   h->d_step = c.take<int64_t>(1);
   h->d_err = c.take<unsigned>(4);
   if (h->barostat) h->baro = c.take<double>(kBaroWords);
+  if (h->baro_axes) h->W3part = c.take<double>((size_t)h->nmol * P * 3);
   if (h->precision == PIMD_PREC_SPLIT) {
     h->xc = c.take<double>((size_t)N * 3);
     h->v0 = c.take<double>((size_t)N * 3);
@@ -787,8 +794,11 @@ pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double 
     return fail(PIMD_EINVAL, "fmmode normal applies to normal modes (method nmpimd)");
   if (!(prm.fmass > 0.0) || !std::isfinite(prm.fmass)) return fail(PIMD_EINVAL, "fmass must be > 0");
   if (!(prm.sp > 0.0)) return fail(PIMD_EINVAL, "sp must be > 0");
-  if (prm.barostat != PIMD_BARO_NONE && prm.barostat != PIMD_BARO_BZP_ISO)
+  if (prm.barostat != PIMD_BARO_NONE && prm.barostat != PIMD_BARO_BZP_ISO &&
+      prm.barostat != PIMD_BARO_BZP_ANISO)
     return fail(PIMD_EINVAL, "unknown barostat %d", prm.barostat);
+  if (prm.barostat == PIMD_BARO_BZP_ANISO && (prm.baro_axes < 1 || prm.baro_axes > 7))
+    return fail(PIMD_EINVAL, "baro_axes must be a nonzero mask of PIMD_AXIS_X/Y/Z");
   if (prm.barostat != PIMD_BARO_NONE) {
     if (sys->potential != PIMD_POT_WATERLIKE)
       return fail(PIMD_EINVAL, "the barostat needs a periodic (water-like) system");
@@ -904,6 +914,7 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   h->fixcom = prm.fixcom;
   h->fmass = prm.fmass;
   h->barostat = prm.barostat;
+  h->baro_axes = prm.barostat == PIMD_BARO_BZP_ANISO ? prm.baro_axes : 0;
   h->pext = prm.pext;
   h->taup = prm.taup;
   h->T = T;
@@ -1125,12 +1136,24 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   for (int c = 0; c < 3; ++c) out->box[c] = h->baro ? h->h_baro[kBaroL + c] : h->box[c];
   if (h->baro) {   // outputs 11-15
     const double kT = kBoltzmann * h->T, n = P;
-    const double W = 3.0 * n * h->N * kT * h->taup * h->taup;
     const double V = out->box[0] * out->box[1] * out->box[2];
-    out->vW = h->h_baro[kBaroV];
-    out->K_W = 0.5 * W * out->vW * out->vW;
+    if (h->baro_axes) {   // one barostat per edge in baro_axes, W = n N kB T taup^2 each
+      const double W = n * h->N * kT * h->taup * h->taup;
+      out->vW = 0.0;
+      out->K_W = 0.0;
+      out->J_W = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        out->vWa[c] = h->h_baro[kBaroV + c];
+        out->K_W += 0.5 * W * out->vWa[c] * out->vWa[c];
+        if (h->baro_axes >> c & 1) out->J_W -= n * kT * std::log(out->box[c]);
+      }
+    } else {
+      const double W = 3.0 * n * h->N * kT * h->taup * h->taup;
+      out->vW = h->h_baro[kBaroV];
+      out->K_W = 0.5 * W * out->vW * out->vW;
+      out->J_W = -n * kT * std::log(V);
+    }
     out->U_W = n * h->pext * V;
-    out->J_W = -n * kT * std::log(V);
     out->enthalpy = out->H + out->K_W + out->U_W + out->J_W;
   }
   return PIMD_OK;
@@ -1142,22 +1165,34 @@ extern "C" pimd_status pimd_get_barostat(pimd_handle *h, double *vW, double *box
   if (h->baro) CK(cudaMemcpyAsync(h->h_baro, h->baro, sizeof(h->h_baro), cudaMemcpyDeviceToHost, h->stream));
   pimd_status st = check_device_errors(h);
   if (st != PIMD_OK) return st;
-  if (vW) *vW = h->baro ? h->h_baro[kBaroV] : 0.0;
+  if (vW) {
+    if (h->baro_axes)
+      for (int c = 0; c < 3; ++c) vW[c] = h->h_baro[kBaroV + c];
+    else
+      *vW = h->baro ? h->h_baro[kBaroV] : 0.0;
+  }
   if (box)
     for (int c = 0; c < 3; ++c) box[c] = h->baro ? h->h_baro[kBaroL + c] : h->box[c];
   return PIMD_OK;
 }
 
-extern "C" pimd_status pimd_set_barostat(pimd_handle *h, double vW, const double *box) {
+extern "C" pimd_status pimd_set_barostat(pimd_handle *h, const double *vW, const double *box) {
   if (!h || !box) return fail(PIMD_EINVAL, "NULL argument");
   if (!h->baro) return fail(PIMD_EINVAL, "the handle has no barostat");
   if (h->latched != PIMD_OK) return fail(h->latched, "%s", h->latched_msg);
-  if (!std::isfinite(vW)) return fail(PIMD_EINVAL, "vW must be finite");
+  if (!vW) return fail(PIMD_EINVAL, "NULL argument");
+  double vw3[3];
+  for (int c = 0; c < 3; ++c) {
+    vw3[c] = h->baro_axes ? vW[c] : vW[0];
+    if (!std::isfinite(vw3[c])) return fail(PIMD_EINVAL, "vW must be finite");
+    if (h->baro_axes && !(h->baro_axes >> c & 1) && vw3[c] != 0.0)
+      return fail(PIMD_EINVAL, "vW of edge %d (outside baro_axes) must be 0", c);
+  }
   for (int c = 0; c < 3; ++c)
     if (!(box[c] > 2.0 * h->ff[6])) return fail(PIMD_EINVAL, "box edge %d must exceed 2 rc", c);
   CK(cudaStreamSynchronize(h->stream));
   std::memset(h->h_baro, 0, sizeof(h->h_baro));
-  h->h_baro[kBaroV] = vW;
+  for (int c = 0; c < 3; ++c) h->h_baro[kBaroV + c] = vw3[c];
   for (int c = 0; c < 3; ++c) {
     h->h_baro[kBaroL + c] = box[c];
     h->h_baro[kBaroInvL + c] = 1.0 / box[c];

@@ -23,11 +23,12 @@ constexpr int kMaxBuckets = 112;        // kLJWarps * max lane groups (8)
 // Bits of the device error word (read back at synchronising calls).
 enum : unsigned { kErrNbrOverflow = 1u, kErrNonFinite = 2u, kErrBoxSmall = 4u };
 
-// Device barostat state (App. E), [kBaroWords] doubles:
-//   [0] v_W after the last completed sub-step
-//   [1] v_W of this step's first A (after its B_W), [2] after its O
-//   [3..5] box edges L, [6..8] 1 / L
-enum { kBaroV = 0, kBaroVA1 = 1, kBaroVA2 = 2, kBaroL = 3, kBaroInvL = 6, kBaroWords = 16 };
+// Device barostat state (App. E), [kBaroWords] doubles, one v_W per box edge
+// (the isotropic barostat keeps the three equal):
+//   [0..2] v_W after the last completed sub-step
+//   [3..5] v_W of this step's first A (after its B_W), [6..8] after its O
+//   [9..11] box edges L, [12..14] 1 / L (the layout of ForceArgs::dbox)
+enum { kBaroV = 0, kBaroVA1 = 3, kBaroVA2 = 6, kBaroL = 9, kBaroInvL = 12, kBaroWords = 16 };
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
@@ -153,10 +154,12 @@ struct BaroArgs {
   const double *Mt;            // [P][P]
   const double *mass_mm;       // [N] m mvv2e
   const double *Wpart;         // [nmol][P] Tr Xi rows of the force kernel
+  const double *W3part;        // [nmol][P][3] diagonal Xi_aa rows (anisotropic), or null
+  int axes;                    // 0: isotropic; else the mask of edges with their own v_W
   double *baro;
   double t0, tB, tA;            // the B_W covers [t0, t0 + tB] of the kick that the next kernel applies
   int step_follows;
-  double W, nkT, npext, mu0;   // W = 3 n N kB T taup^2; n kB T; n P_ext; centroid mass factor
+  double W, nkT, npext, mu0;   // W (3 n N kB T taup^2, or n N kB T taup^2 per edge); n kB T; n P_ext; mu_0
   int thermo;
   double c1W, sigW;            // exp(-h / tau_0); c2 sqrt(n kB T / W)
   uint64_t seed;
@@ -193,6 +196,7 @@ struct ForceArgs {
   int64_t *step_inc;           // if not null, block 0 advances the step counter by one
   double *F;                   // [N][3][P]
   double *Upart, *Wpart;       // [rows][P] bead sums of U and Tr Xi (rows: blocks or molecules)
+  double *W3part;              // water: [nmol][P][3] diagonal Xi_aa as well, or null
   const double *kspring;       // harmonic: [N] m mvv2e omega^2
   double box[3], invbox[3];
   double kb, r0, kth, th0, eps, sig, rc;

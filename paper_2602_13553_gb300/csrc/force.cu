@@ -79,9 +79,13 @@ __global__ void __launch_bounds__(256) k_force_harmonic_f64(ForceArgs a) {
 // Reduction: warps and groups in shared memory, then the 4 blocks of the
 // cluster through distributed shared memory in rank order -- deterministic,
 // no atomics, no global scratch.
+// kDiag (anisotropic barostat) also accumulates the diagonal of the virial
+// tensor, Xi_aa = sum d_a f_a, into W3part.
+template <bool kDiag>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f64(ForceArgs a) {
-  __shared__ double sacc[11][128];
-  __shared__ double red[11][32];
+  constexpr int NC = kDiag ? 14 : 11;   // F (9), U, Tr Xi, then Xi_xx, Xi_yy, Xi_zz
+  __shared__ double sacc[NC][128];
+  __shared__ double red[NC][32];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int P = a.P;
@@ -95,9 +99,9 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
   const int s = rank * 4 + warp;     // 0..kLJWarps-1: LJ buckets; then bonds, angle
   const int u = lane / Bk, kl = lane % Bk;
   const int k = chunk * Bk + kl;
-  double acc[11];
+  double acc[NC];
 #pragma unroll
-  for (int c = 0; c < 11; ++c) acc[c] = 0.0;
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
   // the neighbour list of molecule m: the stored one, or rebuilt here when
   // this step's skin test fails (every block takes the same decision from the
   // same maxima and builds the same list into its own shared memory; the
@@ -196,6 +200,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
               acc[3 + 3 * h + c] = fc;
               acc[c] -= fc;
               w = fma(dv[h][c], fc, w);
+              if (kDiag) acc[11 + c] = fma(dv[h][c], fc, acc[11 + c]);
             }
           }
           acc[9] = uu;
@@ -219,6 +224,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
               acc[3 + 3 * h + c] = fa;
               acc[c] -= fa;
               w = fma(dv[h][c], fa, w);
+              if (kDiag) acc[11 + c] = fma(dv[h][c], fa, acc[11 + c]);
             }
           }
           acc[9] = 0.5 * a.kth * dth * dth;
@@ -241,6 +247,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
     const double sig2 = a.sig * a.sig;
     const double e4 = 4.0 * a.eps, e24 = 24.0 * a.eps;
     double f0 = 0.0, f1 = 0.0, f2 = 0.0, ulj = 0.0, wlj = 0.0;
+    double wx = 0.0, wy = 0.0, wz = 0.0;
     for (int q = q0; q < q1; ++q) {
       const int j = nl[q];
       const size_t sj = (size_t)(3 * j) * 3 * P + k;
@@ -265,6 +272,11 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
         f1 = fma(-fr, d1, f1);
         f2 = fma(-fr, d2, f2);
         wlj = fma(fr, r2, wlj);
+        if (kDiag) {
+          wx = fma(fr * d0, d0, wx);
+          wy = fma(fr * d1, d1, wy);
+          wz = fma(fr * d2, d2, wz);
+        }
       }
     }
     // each molecule takes half of every pair's energy and virial
@@ -273,12 +285,17 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
     acc[2] = f2;
     acc[9] = 0.5 * ulj;
     acc[10] = 0.5 * wlj;
+    if (kDiag) {
+      acc[11] = 0.5 * wx;
+      acc[12] = 0.5 * wy;
+      acc[13] = 0.5 * wz;
+    }
     }
   }
 #pragma unroll
-  for (int c = 0; c < 11; ++c) sacc[c][threadIdx.x] = acc[c];
+  for (int c = 0; c < NC; ++c) sacc[c][threadIdx.x] = acc[c];
   __syncthreads();
-  for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
+  for (int t = threadIdx.x; t < NC * Bk; t += blockDim.x) {
     const int comp = t / Bk, kk = t % Bk;
     double sum = 0.0;
     for (int w = 0; w < 4; ++w)
@@ -287,7 +304,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
   }
   cluster.sync();
   if (rank == 0 && m < a.nmol) {
-    for (int t = threadIdx.x; t < 11 * Bk; t += blockDim.x) {
+    for (int t = threadIdx.x; t < NC * Bk; t += blockDim.x) {
       const int comp = t / Bk, kk = t % Bk;
       const int k2 = chunk * Bk + kk;
       if (k2 >= P) continue;
@@ -297,8 +314,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
         a.F[(size_t)(3 * m + comp / 3) * 3 * P + (comp % 3) * P + k2] = sum;
       else if (comp == 9)
         a.Upart[(size_t)m * P + k2] = sum;
-      else
+      else if (comp == 10)
         a.Wpart[(size_t)m * P + k2] = sum;
+      else
+        a.W3part[((size_t)m * P + k2) * 3 + (comp - 11)] = sum;
     }
     if (a.step_inc && blockIdx.x == 0 && threadIdx.x == 0) *a.step_inc += 1;
   }
@@ -437,7 +456,10 @@ cudaError_t launch_force_harmonic(const ForceArgs &a, cudaStream_t s) {
 }
 
 cudaError_t launch_force_water(const ForceArgs &a, cudaStream_t s) {
-  k_force_water_f64<<<water_force_blocks(a.nmol, a.P), 128, 0, s>>>(a);
+  if (a.W3part)
+    k_force_water_f64<true><<<water_force_blocks(a.nmol, a.P), 128, 0, s>>>(a);
+  else
+    k_force_water_f64<false><<<water_force_blocks(a.nmol, a.P), 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -120,9 +120,9 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
       // B(h/2) of this step, merged with the final B(h/2) of the previous one
       v = fma(a.kick * im, f, v);
       if (k == 0 && a.baro) {   // the centroid rides on the barostat
-        baro_drift(q, v, a.baro[kBaroVA1], a.half);
+        baro_drift(q, v, a.baro[kBaroVA1 + r % 3], a.half);
         if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
-        baro_drift(q, v, a.baro[kBaroVA2], a.half);
+        baro_drift(q, v, a.baro[kBaroVA2 + r % 3], a.half);
       } else {
         rotate(q, v, cA, sA, wsA);
         if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
@@ -438,61 +438,92 @@ __global__ void __launch_bounds__(256) k_fixcom_f64(FixcomArgs a) {
   }
 }
 
-// B_W of the isotropic BZP barostat (App. E) over [t0, t0 + tB] of the kick
-// that the next kernel applies to the current velocities, with n = P:
+// B_W of the BZP barostat (App. E) over [t0, t0 + tB] of the kick that the
+// next kernel applies to the current velocities, with n = P.  Isotropic:
 //   v_W += (3 tB / W)[n V P_CV - n V P_ext + n kB T] + (tB^2 / W) sum F~0.v~0
 //          + (tB^3 / 3W) sum |F~0|^2 / m~0,
 //   3 n V P_CV = sum m~0 |v~0|^2 - sum (r - r_c).F + sum_k Tr Xi^(k);
-// then, if a step follows, its v_W at the first A, after O_W (PILE_L) and the
-// box after both A sub-steps.  One block; fixed-order sums.
+// anisotropic, for each edge a in the mask, the same with the a components
+// alone, W the per-edge mass and 3 n V P_CV -> n V P_CV^aa (the Xi_aa rows).
+// Then, if a step follows, its v_W at the first A, after O_W (PILE_L: each
+// edge its own deviate) and the box after both A sub-steps.  One block;
+// fixed-order sums.
 __global__ void __launch_bounds__(256) k_baro_kick(BaroArgs a) {
   __shared__ double red[256];
   const int P = a.P;
-  double mv2 = 0.0, fv = 0.0, f2m = 0.0, rcf = 0.0, vir = 0.0;
-  for (int t = threadIdx.x; t < a.N * 3; t += blockDim.x) {
-    const int i = t / 3;
-    const size_t row = (size_t)t * P;
+  double mv2[3] = {0.0, 0.0, 0.0}, fv[3] = {0.0, 0.0, 0.0}, f2m[3] = {0.0, 0.0, 0.0};
+  double rcf[3] = {0.0, 0.0, 0.0}, vir[3] = {0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < a.N; i += blockDim.x) {
     const double mm = a.mass_mm[i] * a.mu0;
-    double f0 = 0.0, xm = 0.0;
-    for (int j = 0; j < P; ++j) {
-      f0 = fma(a.Mt[j * P], a.F[row + j], f0);   // F~0 = (M F)_0
-      xm += a.x[row + j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t row = ((size_t)i * 3 + c) * P;
+      double f0 = 0.0, xm = 0.0;
+      for (int j = 0; j < P; ++j) {
+        f0 = fma(a.Mt[j * P], a.F[row + j], f0);   // F~0 = (M F)_0
+        xm += a.x[row + j];
+      }
+      xm /= P;
+      for (int j = 0; j < P; ++j) rcf[c] = fma(a.x[row + j] - xm, a.F[row + j], rcf[c]);
+      const double v0 = fma(a.t0, f0 / mm, a.v[row]);   // at t0 into the kick
+      mv2[c] = fma(mm * v0, v0, mv2[c]);
+      fv[c] = fma(f0, v0, fv[c]);
+      f2m[c] += f0 * f0 / mm;
     }
-    xm /= P;
-    for (int j = 0; j < P; ++j) rcf = fma(a.x[row + j] - xm, a.F[row + j], rcf);
-    const double v0 = fma(a.t0, f0 / mm, a.v[row]);   // at t0 into the kick
-    mv2 = fma(mm * v0, v0, mv2);
-    fv = fma(f0, v0, fv);
-    f2m += f0 * f0 / mm;
   }
-  for (int t = threadIdx.x; t < a.nmol * P; t += blockDim.x) vir += a.Wpart[t];
-  mv2 = block_sum(mv2, red);
-  fv = block_sum(fv, red);
-  f2m = block_sum(f2m, red);
-  rcf = block_sum(rcf, red);
-  vir = block_sum(vir, red);
+  if (a.axes) {
+    for (int t = threadIdx.x; t < a.nmol * P; t += blockDim.x)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) vir[c] += a.W3part[(size_t)t * 3 + c];
+  } else {
+    for (int t = threadIdx.x; t < a.nmol * P; t += blockDim.x) vir[0] += a.Wpart[t];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    mv2[c] = block_sum(mv2[c], red);
+    fv[c] = block_sum(fv[c], red);
+    f2m[c] = block_sum(f2m[c], red);
+    rcf[c] = block_sum(rcf[c], red);
+    vir[c] = block_sum(vir[c], red);
+  }
   if (threadIdx.x != 0) return;
   double *b = a.baro;
   const double V = b[kBaroL] * b[kBaroL + 1] * b[kBaroL + 2];
   const double tB = a.tB;
-  double vW = b[kBaroV] + 3.0 * tB / a.W * ((mv2 - rcf + vir) / 3.0 - V * a.npext + a.nkT) +
-              tB * tB / a.W * fv + tB * tB * tB / (3.0 * a.W) * f2m;
+  double vW[3];
+  if (a.axes) {
+    for (int c = 0; c < 3; ++c)
+      vW[c] = (a.axes >> c & 1)
+                  ? b[kBaroV + c] + tB / a.W * (mv2[c] - rcf[c] + vir[c] - V * a.npext + a.nkT) +
+                        tB * tB / a.W * fv[c] + tB * tB * tB / (3.0 * a.W) * f2m[c]
+                  : 0.0;
+  } else {
+    const double smv2 = mv2[0] + mv2[1] + mv2[2], srcf = rcf[0] + rcf[1] + rcf[2];
+    const double sfv = fv[0] + fv[1] + fv[2], sf2m = f2m[0] + f2m[1] + f2m[2];
+    const double w = b[kBaroV] + 3.0 * tB / a.W * ((smv2 - srcf + vir[0]) / 3.0 - V * a.npext + a.nkT) +
+                     tB * tB / a.W * sfv + tB * tB * tB / (3.0 * a.W) * sf2m;
+    vW[0] = vW[1] = vW[2] = w;
+  }
   if (!a.step_follows) {
-    b[kBaroV] = vW;
+    for (int c = 0; c < 3; ++c) b[kBaroV + c] = vW[c];
     return;
   }
-  double vO = vW;
+  double vO[3] = {vW[0], vW[1], vW[2]};
   if (a.thermo) {
-    double e0, e1, e2;
-    gauss3(a.seed, 0xffffffffu, 0u, 3u, (uint64_t)*a.step, e0, e1, e2);
-    vO = a.c1W * vW + a.sigW * e0;
+    double e[3];
+    gauss3(a.seed, 0xffffffffu, 0u, 3u, (uint64_t)*a.step, e[0], e[1], e[2]);
+    if (a.axes) {
+      for (int c = 0; c < 3; ++c)
+        if (a.axes >> c & 1) vO[c] = a.c1W * vW[c] + a.sigW * e[c];
+    } else {
+      vO[0] = vO[1] = vO[2] = a.c1W * vW[0] + a.sigW * e[0];
+    }
   }
-  b[kBaroVA1] = vW;
-  b[kBaroVA2] = vO;
-  b[kBaroV] = vO;
-  const double s1 = exp(a.tA * vW), s2 = exp(a.tA * vO);
   for (int c = 0; c < 3; ++c) {
-    const double L = b[kBaroL + c] * s1 * s2;
+    b[kBaroVA1 + c] = vW[c];
+    b[kBaroVA2 + c] = vO[c];
+    b[kBaroV + c] = vO[c];
+    const double L = b[kBaroL + c] * exp(a.tA * vW[c]) * exp(a.tA * vO[c]);
     b[kBaroL + c] = L;
     b[kBaroInvL + c] = 1.0 / L;
     if (!(L > a.Lmin)) atomicOr(a.err, kErrBoxSmall);

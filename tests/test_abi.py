@@ -42,7 +42,12 @@ def test_params_default(L):
     p = b.default_params()
     assert (p.thermostat, p.integrator, p.method, p.precision, p.seed) == (1, 0, 0, 0, 1)
     assert (p.tau, p.scale, p.sp, p.fixcom, p.fmmode, p.fmass) == (1.0, 1.0, 1.0, 0, 0, 1.0)
-    assert (p.barostat, p.pext, p.taup) == (0, 0.0, 1.0)
+    assert (p.barostat, p.pext, p.taup, p.baro_axes) == (0, 0.0, 1.0, 7)
+
+
+def test_params_reject_unknown_names(L):
+    with pytest.raises(TypeError):
+        b.default_params(baro_axis=3)
 
 
 def test_status_strings(L):
@@ -78,6 +83,7 @@ def water_sys():
                                   "fixcom2", "badmethod", "badfmmode", "fmass0", "normal_cartesian",
                                   "split_cartesian", "split_fixcom", "split_fmass", "split_normal",
                                   "badbaro", "baro_obabo", "baro_cartesian", "baro_taup0", "baro_split",
+                                  "aniso_axes0", "aniso_axes8", "aniso_obabo",
                                   "tau0", "sp0", "gamma_mismatch", "box_small",
                                   "natoms_not3", "mass0", "null_pos"])
 def test_create_rejects_invalid(L, water_sys, case):
@@ -105,6 +111,9 @@ def test_create_rejects_invalid(L, water_sys, case):
     elif case == "baro_cartesian": prm.barostat, prm.method = b.BARO_BZP_ISO, b.METHOD_PIMD
     elif case == "baro_taup0": prm.barostat, prm.taup = b.BARO_BZP_ISO, 0.0
     elif case == "baro_split": prm.barostat, prm.precision = b.BARO_BZP_ISO, b.PREC_SPLIT
+    elif case == "aniso_axes0": prm.barostat, prm.baro_axes = b.BARO_BZP_ANISO, 0
+    elif case == "aniso_axes8": prm.barostat, prm.baro_axes = b.BARO_BZP_ANISO, 8
+    elif case == "aniso_obabo": prm.barostat, prm.integrator = b.BARO_BZP_ANISO, b.OBABO
     elif case == "tau0": prm.tau = 0.0
     elif case == "sp0": prm.sp = 0.0
     elif case == "gamma_mismatch": kw["gamma0"] = 3.0

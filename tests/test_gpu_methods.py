@@ -126,3 +126,49 @@ def test_bzp_checkpoint_resume_is_bitwise(pimd):
     xb, vb, _ = b.get_state()
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     assert a.get_barostat()[0] == b.get_barostat()[0]
+
+
+@pytest.mark.parametrize("thermostat,axes", [(1, 7), (0, 7), (1, 4), (1, 3)])
+def test_bzp_aniso_barostat_water(orc, pimd, thermostat, axes):
+    """Anisotropic BZP barostat (one v_W per edge in baro_axes), 32 molecules
+    x 4 beads, 50 steps: positions, velocities, v_Wa, box and outputs 11-15;
+    edges outside the mask stay exactly fixed."""
+    x0, mass, kw = _water(32, 4, 9)
+    probe = orc.Sim(x0, mass, T=300.0, dt=2.5e-4, thermostat=0, **kw)
+    pext = probe.estimators()["P_CV"] * 0.8
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, thermostat=thermostat, barostat=2,
+                 baro_axes=axes, pext=pext, taup=0.05, **kw)
+    _run_both(c, g, 50, 1e-8)
+    vw, box = g.get_barostat()
+    assert np.abs(vw - c.vWa).max() < 1e-8 * max(1.0, np.abs(c.vWa).max())
+    assert np.abs(box - c.box).max() < 1e-10 * c.box.max()
+    for a in range(3):
+        if axes >> a & 1:
+            assert abs(box[a] / kw["box"][a] - 1.0) > 1e-6
+        else:
+            assert box[a] == kw["box"][a] and vw[a] == 0.0
+    eg, ec = g.estimators(), c.estimators()
+    for k in ("K_W", "U_W", "J_W", "enthalpy"):
+        assert scalar_err(eg[k], ec[k]) < 1e-8, (k, eg[k], ec[k])
+    assert np.abs(eg["vWa"] - ec["vWa"]).max() < 1e-8 * max(1.0, np.abs(ec["vWa"]).max())
+    assert eg["vW"] == 0.0
+
+
+def test_bzp_aniso_checkpoint_resume_is_bitwise(pimd):
+    x0, mass, kw = _water(32, 4, 10)
+    prm = dict(T=300.0, dt=5e-4, barostat=2, baro_axes=5, pext=1e-3, taup=0.1, **kw)
+    a = pimd.Simulation(x0, mass, **prm)
+    a.step(30)
+    x, v, st = a.get_state()
+    vw, box = a.get_barostat()
+    a.step(20)
+    b = pimd.Simulation(x0, mass, **prm)
+    b.set_barostat(vw, box)
+    b.set_state(x, v, st)
+    b.step(20)
+    xa, va, _ = a.get_state()
+    xb, vb, _ = b.get_state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(a.get_barostat()[0], b.get_barostat()[0])
+    with pytest.raises(pimd.PimdError):
+        b.set_barostat(np.array([0.0, 1.0, 0.0]), box)      # y is outside the mask
