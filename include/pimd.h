@@ -138,7 +138,9 @@ typedef struct {
  *           by exp(tA v_W), and with PILE_L the O step also draws
  *           v_W <- c1 v_W + c2 sqrt(n kB T / W) eta (c1 = exp(-h / tau),
  *           Philox atom 0xffffffff, mode 0, stream 3).  n = P, W = 3 P N kB T
- *           taup^2.  Water-like periodic systems, BAOAB, method nmpimd, FP64.
+ *           taup^2.  OBABO: each O(h/2) draws v_W with c1 = exp(-h / 2tau)
+ *           (mode 0 the first, mode 1 the second), one A(h) scales by
+ *           exp(h v_W).  Water-like periodic systems, method nmpimd, FP64.
  *           PIMD_BARO_BZP_ANISO: each edge a in baro_axes has its own
  *           v_Wa with W = P N kB T taup^2 and
  *             v_Wa += (tB / W)[n V (P_CV^aa - P_ext) + n kB T]

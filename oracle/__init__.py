@@ -39,7 +39,7 @@ PIMD = 1          # Cartesian method
 FM_PHYSICAL = 0
 FM_NORMAL = 1
 BARO_NONE = 0
-BARO_BZP = 1      # isotropic BZP barostat (App. E), BAOAB only
+BARO_BZP = 1      # isotropic BZP barostat (App. E)
 BARO_BZP_ANISO = 2  # one BZP barostat per axis in baro_axes (bits x = 1, y = 2, z = 4)
 
 
@@ -240,8 +240,9 @@ class Sim:
     water-like (ff = kb, r0, kth, th0, eps, sig, rc).  thermostat 0 = NVE,
     1 = PILE_L.  fmmode 0 = physical, 1 = normal; fmass scales the fictitious
     masses; fixcom removes the centre-of-mass velocity every step.  barostat 1
-    = isotropic BZP (App. E, BAOAB, normal modes) at pext (eV/A^3) with
-    barostat time taup (ps); NpH without a thermostat, NpT with PILE_L.
+    = isotropic BZP (App. E, normal modes) at pext (eV/A^3) with
+    barostat time taup (ps); NpH without a thermostat, NpT with PILE_L;
+    BAOAB or OBABO.
     barostat 2 = anisotropic BZP: one barostat per box edge in the bit mask
     baro_axes (x = 1, y = 2, z = 4), the other edges fixed.
     """
@@ -250,7 +251,7 @@ class Sim:
                  v0=None, thermostat=1, integrator=BAOAB, seed=1, tau=1.0, scale=1.0, sp=1.0,
                  method=NMPIMD, fmmode=FM_PHYSICAL, fmass=1.0, fixcom=0, barostat=BARO_NONE,
                  pext=0.0, taup=1.0, vW=0.0, baro_axes=7):
-        assert barostat == BARO_NONE or (integrator == BAOAB and method == NMPIMD and potential == POT_WATERLIKE)
+        assert barostat == BARO_NONE or (method == NMPIMD and potential == POT_WATERLIKE)
         x0 = np.ascontiguousarray(x0, dtype=np.float64)
         P, N, three = x0.shape
         assert three == 3 and 1 <= P <= 128

@@ -611,11 +611,12 @@ static void or_A_baro_centroid(or_sim *s, double *q, double tA) {
 /* Langevin on the barostat velocity (App. E, NpT): v_W <- c1 v_W +
  * c2 sqrt(n kB T / W) eta with c1 = exp(-dtO / tau_0) (the centroid damping
  * time; the printed "m_i" under the root is read as W), eta the first
- * deviate of Philox atom 0xffffffff, mode 0, stream 3. */
-static void or_O_baro(or_sim *s, double dtO) {
+ * deviate of Philox atom 0xffffffff, stream 3, mode 0 (the O of BAOAB, the
+ * first O(h/2) of OBABO) or 1 (the second O(h/2) of OBABO). */
+static void or_O_baro(or_sim *s, double dtO, uint32_t mode) {
   double c1 = exp(-dtO / s->tau), c2 = sqrt(1.0 - c1 * c1);
   double eta[3];
-  or_gauss3(s->seed, 0xffffffffu, 0u, 3u, (uint64_t)s->step, eta);
+  or_gauss3(s->seed, 0xffffffffu, mode, 3u, (uint64_t)s->step, eta);
   s->vW = c1 * s->vW + c2 * sqrt(s->P * OR_KB * s->T / or_baro_W(s)) * eta[0];
 }
 
@@ -674,10 +675,10 @@ static void or_A_baro_centroid_aniso(or_sim *s, double *q, double tA) {
   }
 }
 
-static void or_O_baro_aniso(or_sim *s, double dtO) {
+static void or_O_baro_aniso(or_sim *s, double dtO, uint32_t mode) {
   double c1 = exp(-dtO / s->tau), c2 = sqrt(1.0 - c1 * c1);
   double eta[3];
-  or_gauss3(s->seed, 0xffffffffu, 0u, 3u, (uint64_t)s->step, eta);
+  or_gauss3(s->seed, 0xffffffffu, mode, 3u, (uint64_t)s->step, eta);
   double sig = sqrt(s->P * OR_KB * s->T / or_baro_Wa(s));
   for (int a = 0; a < 3; ++a)
     if (s->baro_axes >> a & 1) s->vWa[a] = c1 * s->vWa[a] + c2 * sig * eta[a];
@@ -727,8 +728,8 @@ void or_run(or_sim *s, int64_t nsteps) {
       if (iso) or_A_baro_centroid(s, q, 0.5 * h);
       if (ani) or_A_baro_centroid_aniso(s, q, 0.5 * h);
       if (s->thermostat) or_O(s, omega, h, 0u);
-      if (s->thermostat && iso) or_O_baro(s, h);
-      if (s->thermostat && ani) or_O_baro_aniso(s, h);
+      if (s->thermostat && iso) or_O_baro(s, h, 0u);
+      if (s->thermostat && ani) or_O_baro_aniso(s, h, 0u);
       or_A(s, omega, q, 0.5 * h);
       if (iso) or_A_baro_centroid(s, q, 0.5 * h);
       if (ani) or_A_baro_centroid_aniso(s, q, 0.5 * h);
@@ -738,14 +739,27 @@ void or_run(or_sim *s, int64_t nsteps) {
       if (ani) or_B_baro_aniso(s, M, Ft, 0.5 * h);
       or_B(s, M, Ft, 0.5 * h);
     } else {
+      /* OBABO; with the barostat each O(h/2) also thermostats v_W, each
+       * B(h/2) carries its B_W and A(h) drives the centroid and the box */
+      int iso = s->barostat == 1, ani = s->barostat == 2;
       if (s->thermostat) or_O(s, omega, 0.5 * h, 0u);
+      if (s->thermostat && iso) or_O_baro(s, 0.5 * h, 0u);
+      if (s->thermostat && ani) or_O_baro_aniso(s, 0.5 * h, 0u);
+      if (iso) or_B_baro(s, M, Ft, 0.5 * h);
+      if (ani) or_B_baro_aniso(s, M, Ft, 0.5 * h);
       or_B(s, M, Ft, 0.5 * h);
       or_to_nm(P, N, M, s->x, q);
       or_A(s, omega, q, h);
+      if (iso) or_A_baro_centroid(s, q, h);
+      if (ani) or_A_baro_centroid_aniso(s, q, h);
       or_from_nm(P, N, M, q, s->x);
       or_compute_forces(s);
+      if (iso) or_B_baro(s, M, Ft, 0.5 * h);
+      if (ani) or_B_baro_aniso(s, M, Ft, 0.5 * h);
       or_B(s, M, Ft, 0.5 * h);
       if (s->thermostat) or_O(s, omega, 0.5 * h, 1u);
+      if (s->thermostat && iso) or_O_baro(s, 0.5 * h, 1u);
+      if (s->thermostat && ani) or_O_baro_aniso(s, 0.5 * h, 1u);
     }
     if (s->fixcom) or_fixcom(s);
     s->step += 1;

@@ -315,6 +315,7 @@ static StepArgs step_args(pimd_handle *h) {
   a.wn2 = h->wn * h->wn;
   a.mass_mm = h->mass_mm;
   a.baro = h->baro;
+  a.phase = 0;
   a.step = h->d_step;
   a.step_off = 0;
   const bool water = h->potential == PIMD_POT_WATERLIKE;
@@ -541,15 +542,16 @@ static pimd_status enqueue_baro(pimd_handle *h, double t0, double tB, bool step_
   b.baro = h->baro;
   b.t0 = t0;
   b.tB = tB;
-  b.tA = 0.5 * h->dt;
+  b.tA = b.obabo ? h->dt : 0.5 * h->dt;
   b.step_follows = step_follows ? 1 : 0;
+  b.obabo = h->integrator == PIMD_OBABO;
   const double kT = kBoltzmann * h->T;
   b.W = (h->baro_axes ? 1.0 : 3.0) * h->P * h->N * kT * h->taup * h->taup;
   b.nkT = h->P * kT;
   b.npext = h->P * h->pext;
   b.mu0 = h->fmass;
   b.thermo = h->thermostat == PIMD_THERMO_PILE_L;
-  b.c1W = std::exp(-h->dt / h->tau);
+  b.c1W = std::exp(-(b.obabo ? 0.5 * h->dt : h->dt) / h->tau);   // the O_W's own duration
   b.sigW = std::sqrt(1.0 - b.c1W * b.c1W) * std::sqrt(b.nkT / b.W);
   b.seed = h->seed;
   b.step = h->d_step;
@@ -574,11 +576,25 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
   a.first = first ? 1 : 0;
   a.kick = first ? 0.5 * h->dt : h->dt;
   pimd_status st;
-  // the B_W beside this step's opening B(h/2), which follows the previous
-  // step's closing B(h/2) inside a merged kick
-  if (h->baro && (st = enqueue_baro(h, first ? 0.0 : 0.5 * h->dt, 0.5 * h->dt, true)) != PIMD_OK) return st;
-  st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a, h->threads_step, h->stream); });
-  if (st != PIMD_OK) return st;
+  if (h->baro && h->integrator == PIMD_OBABO) {
+    // OBABO: the opening B_W needs the velocities after both O(h/2), so the
+    // step runs as [closing B O + opening O] -> O_W, B_W, box -> [B, A(h)]
+    StepArgs a1 = a, a2 = a;
+    a1.phase = 1;
+    a2.phase = 2;
+    st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a1, h->threads_step, h->stream); });
+    if (st != PIMD_OK) return st;
+    if ((st = enqueue_baro(h, 0.0, 0.5 * h->dt, true)) != PIMD_OK) return st;
+    st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a2, h->threads_step, h->stream); });
+    if (st != PIMD_OK) return st;
+  } else {
+    // the B_W beside this step's opening B(h/2), which follows the previous
+    // step's closing B(h/2) inside a merged kick
+    if (h->baro && (st = enqueue_baro(h, first ? 0.0 : 0.5 * h->dt, 0.5 * h->dt, true)) != PIMD_OK)
+      return st;
+    st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step(a, h->threads_step, h->stream); });
+    if (st != PIMD_OK) return st;
+  }
   st = enqueue_forces(h, false, true);
   if (st != PIMD_OK) return st;
   // the B_W beside this step's closing B(h/2) (applied by the next kernel)
@@ -802,7 +818,6 @@ pimd_status validate_create(const pimd_system *sys, int32_t P, double T, double 
   if (prm.barostat != PIMD_BARO_NONE) {
     if (sys->potential != PIMD_POT_WATERLIKE)
       return fail(PIMD_EINVAL, "the barostat needs a periodic (water-like) system");
-    if (prm.integrator != PIMD_BAOAB) return fail(PIMD_EINVAL, "the barostat is implemented for BAOAB");
     if (prm.method != PIMD_METHOD_NMPIMD) return fail(PIMD_EINVAL, "the barostat acts on normal modes (nmpimd)");
     if (!(prm.taup > 0.0) || !std::isfinite(prm.taup)) return fail(PIMD_EINVAL, "taup must be > 0");
     if (!std::isfinite(prm.pext)) return fail(PIMD_EINVAL, "pext must be finite");

@@ -142,6 +142,11 @@ struct StepArgs {
   double wn2;                  // omega_n^2
   const double *mass_mm;       // [N] m mvv2e
   const double *baro;          // barostat state (centroid propagation under v_W), or null
+  // OBABO with the barostat runs a step in two launches around the B_W that
+  // needs the velocities after the O(h/2) sub-steps: phase 1 = the previous
+  // step's closing B O and this step's O (velocities only), phase 2 = B(h/2)
+  // A(h) and the new positions; phase 0 = the whole step in one launch
+  int phase;
   int noise_pre;               // 1: PILE_L deviates drawn once per (atom, mode) into shared memory
 };
 
@@ -159,6 +164,10 @@ struct BaroArgs {
   double *baro;
   double t0, tB, tA;            // the B_W covers [t0, t0 + tB] of the kick that the next kernel applies
   int step_follows;
+  // OBABO: the start-of-step call first applies the opening O_W (mode 0) and
+  // scales the box once by exp(tA v_W), tA = h; the end-of-step call applies
+  // the closing O_W (mode 1, keyed on the step just completed) after its B_W
+  int obabo;
   double W, nkT, npext, mu0;   // W (3 n N kB T taup^2, or n N kB T taup^2 per edge); n kB T; n P_ext; mu_0
   int thermo;
   double c1W, sigW;            // exp(-h / tau_0); c2 sqrt(n kB T / W)

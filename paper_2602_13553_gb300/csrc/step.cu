@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   // Large grids: one Philox draw and Box-Muller per (atom, mode) serve the
   // three components (throughput).  Small grids (noise_pre = 0): each element
   // draws its own component inline, in parallel with the others (latency).
-  if (a.thermo && a.noise_pre) {
+  if (a.thermo && a.noise_pre && a.phase != 2) {
     const bool o2 = a.integrator == 1 && !a.first;
     for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
       const int al = t / P, k = t - al * P;
@@ -130,18 +130,26 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
       }
     } else {
       const double kb = a.half * im;
-      if (!a.first) {
-        // the previous step's closing B(h/2) O(h/2)
-        v = fma(kb, f, v);
-        if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO2, step - 1, sE2));
+      if (a.phase != 2) {
+        if (!a.first) {
+          // the previous step's closing B(h/2) O(h/2)
+          v = fma(kb, f, v);
+          if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO2, step - 1, sE2));
+        }
+        if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
       }
-      if (a.thermo) v = fma(c1, v, c2s * noise(kStreamO1, step, sE));
-      v = fma(kb, f, v);
-      rotate(q, v, cA, sA, wsA);
+      if (a.phase != 1) {
+        v = fma(kb, f, v);
+        if (k == 0 && a.baro)   // A(h) of the centroid under the barostat
+          baro_drift(q, v, a.baro[kBaroVA1 + r % 3], 2.0 * a.half);
+        else
+          rotate(q, v, cA, sA, wsA);
+      }
     }
     sQ[task] = q;
     a.v[base + task] = v;
   }
+  if (a.phase == 1) return;   // velocities only: the barostat's B_W reads them next
   __syncthreads();
   const double *__restrict__ M = a.mt.M;
   for (int task = threadIdx.x; task < len; task += blockDim.x) {
@@ -490,40 +498,50 @@ __global__ void __launch_bounds__(256) k_baro_kick(BaroArgs a) {
   double *b = a.baro;
   const double V = b[kBaroL] * b[kBaroL + 1] * b[kBaroL + 2];
   const double tB = a.tB;
-  double vW[3];
+  // O_W: v_W <- c1 v_W + sigW eta, eta from Philox atom 0xffffffff, stream 3,
+  // the given mode; each edge its own deviate, the isotropic v_W the first
+  auto langevin = [&](double *w, uint32_t mode, uint64_t st) {
+    double e[3];
+    gauss3(a.seed, 0xffffffffu, mode, 3u, st, e[0], e[1], e[2]);
+    if (a.axes) {
+      for (int c = 0; c < 3; ++c)
+        if (a.axes >> c & 1) w[c] = a.c1W * w[c] + a.sigW * e[c];
+    } else {
+      w[0] = w[1] = w[2] = a.c1W * w[0] + a.sigW * e[0];
+    }
+  };
+  const uint64_t step = (uint64_t)*a.step;
+  double vW[3] = {b[kBaroV], b[kBaroV + 1], b[kBaroV + 2]};
+  if (a.obabo && a.step_follows && a.thermo) langevin(vW, 0u, step);   // this step's first O(h/2)
   if (a.axes) {
     for (int c = 0; c < 3; ++c)
       vW[c] = (a.axes >> c & 1)
-                  ? b[kBaroV + c] + tB / a.W * (mv2[c] - rcf[c] + vir[c] - V * a.npext + a.nkT) +
+                  ? vW[c] + tB / a.W * (mv2[c] - rcf[c] + vir[c] - V * a.npext + a.nkT) +
                         tB * tB / a.W * fv[c] + tB * tB * tB / (3.0 * a.W) * f2m[c]
                   : 0.0;
   } else {
     const double smv2 = mv2[0] + mv2[1] + mv2[2], srcf = rcf[0] + rcf[1] + rcf[2];
     const double sfv = fv[0] + fv[1] + fv[2], sf2m = f2m[0] + f2m[1] + f2m[2];
-    const double w = b[kBaroV] + 3.0 * tB / a.W * ((smv2 - srcf + vir[0]) / 3.0 - V * a.npext + a.nkT) +
+    const double w = vW[0] + 3.0 * tB / a.W * ((smv2 - srcf + vir[0]) / 3.0 - V * a.npext + a.nkT) +
                      tB * tB / a.W * sfv + tB * tB * tB / (3.0 * a.W) * sf2m;
     vW[0] = vW[1] = vW[2] = w;
   }
   if (!a.step_follows) {
+    // OBABO: the closing O(h/2) of the step just completed (the counter has
+    // already been advanced past it)
+    if (a.obabo && a.thermo) langevin(vW, 1u, step - 1);
     for (int c = 0; c < 3; ++c) b[kBaroV + c] = vW[c];
     return;
   }
   double vO[3] = {vW[0], vW[1], vW[2]};
-  if (a.thermo) {
-    double e[3];
-    gauss3(a.seed, 0xffffffffu, 0u, 3u, (uint64_t)*a.step, e[0], e[1], e[2]);
-    if (a.axes) {
-      for (int c = 0; c < 3; ++c)
-        if (a.axes >> c & 1) vO[c] = a.c1W * vW[c] + a.sigW * e[c];
-    } else {
-      vO[0] = vO[1] = vO[2] = a.c1W * vW[0] + a.sigW * e[0];
-    }
-  }
+  if (a.thermo && !a.obabo) langevin(vO, 0u, step);
   for (int c = 0; c < 3; ++c) {
     b[kBaroVA1 + c] = vW[c];
     b[kBaroVA2 + c] = vO[c];
     b[kBaroV + c] = vO[c];
-    const double L = b[kBaroL + c] * exp(a.tA * vW[c]) * exp(a.tA * vO[c]);
+    // BAOAB: A(h/2) at v_W, O_W, A(h/2) at v_O; OBABO: one A(h) at v_W
+    const double L = a.obabo ? b[kBaroL + c] * exp(a.tA * vW[c])
+                             : b[kBaroL + c] * exp(a.tA * vW[c]) * exp(a.tA * vO[c]);
     b[kBaroL + c] = L;
     b[kBaroInvL + c] = 1.0 / L;
     if (!(L > a.Lmin)) atomicOr(a.err, kErrBoxSmall);

@@ -82,8 +82,8 @@ def water_sys():
 @pytest.mark.parametrize("case", ["P0", "P129", "T0", "dt0", "badpot", "badthermo", "badint",
                                   "fixcom2", "badmethod", "badfmmode", "fmass0", "normal_cartesian",
                                   "split_cartesian", "split_fixcom", "split_fmass", "split_normal",
-                                  "badbaro", "baro_obabo", "baro_cartesian", "baro_taup0", "baro_split",
-                                  "aniso_axes0", "aniso_axes8", "aniso_obabo",
+                                  "badbaro", "baro_cartesian", "baro_taup0", "baro_split",
+                                  "aniso_axes0", "aniso_axes8", "aniso_cartesian",
                                   "tau0", "sp0", "gamma_mismatch", "box_small",
                                   "natoms_not3", "mass0", "null_pos"])
 def test_create_rejects_invalid(L, water_sys, case):
@@ -107,13 +107,12 @@ def test_create_rejects_invalid(L, water_sys, case):
     elif case == "split_fmass": prm.precision, prm.fmass = b.PREC_SPLIT, 2.0
     elif case == "split_normal": prm.precision, prm.fmmode = b.PREC_SPLIT, b.FMMODE_NORMAL
     elif case == "badbaro": prm.barostat = 4
-    elif case == "baro_obabo": prm.barostat, prm.integrator = b.BARO_BZP_ISO, b.OBABO
     elif case == "baro_cartesian": prm.barostat, prm.method = b.BARO_BZP_ISO, b.METHOD_PIMD
     elif case == "baro_taup0": prm.barostat, prm.taup = b.BARO_BZP_ISO, 0.0
     elif case == "baro_split": prm.barostat, prm.precision = b.BARO_BZP_ISO, b.PREC_SPLIT
     elif case == "aniso_axes0": prm.barostat, prm.baro_axes = b.BARO_BZP_ANISO, 0
     elif case == "aniso_axes8": prm.barostat, prm.baro_axes = b.BARO_BZP_ANISO, 8
-    elif case == "aniso_obabo": prm.barostat, prm.integrator = b.BARO_BZP_ANISO, b.OBABO
+    elif case == "aniso_cartesian": prm.barostat, prm.method = b.BARO_BZP_ANISO, b.METHOD_PIMD
     elif case == "tau0": prm.tau = 0.0
     elif case == "sp0": prm.sp = 0.0
     elif case == "gamma_mismatch": kw["gamma0"] = 3.0

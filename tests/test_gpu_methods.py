@@ -91,15 +91,16 @@ def test_cartesian_checkpoint_resume_is_bitwise(pimd):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
-@pytest.mark.parametrize("thermostat", [1, 0])
-def test_bzp_barostat_water(orc, pimd, thermostat):
-    """Isotropic BZP barostat (App. E), NpT (PILE_L) and NpH, 32 molecules x 4
-    beads, 50 steps: positions, velocities, v_W, box and outputs 11-15."""
+@pytest.mark.parametrize("thermostat,integrator", [(1, 0), (0, 0), (1, 1), (0, 1)])
+def test_bzp_barostat_water(orc, pimd, thermostat, integrator):
+    """Isotropic BZP barostat (App. E), NpT (PILE_L) and NpH, BAOAB and OBABO,
+    32 molecules x 4 beads, 50 steps: positions, velocities, v_W, box and
+    outputs 11-15."""
     x0, mass, kw = _water(32, 4, 7)
     probe = orc.Sim(x0, mass, T=300.0, dt=2.5e-4, thermostat=0, **kw)
     pext = probe.estimators()["P_CV"] * 0.8
     c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, thermostat=thermostat, barostat=1,
-                 pext=pext, taup=0.05, **kw)
+                 pext=pext, taup=0.05, integrator=integrator, **kw)
     _run_both(c, g, 50, 1e-8)
     vw, box = g.get_barostat()
     assert abs(vw - c.vW) < 1e-8 * max(1.0, abs(c.vW))
@@ -110,9 +111,10 @@ def test_bzp_barostat_water(orc, pimd, thermostat):
         assert scalar_err(eg[k], ec[k]) < 1e-8, (k, eg[k], ec[k])
 
 
-def test_bzp_checkpoint_resume_is_bitwise(pimd):
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_bzp_checkpoint_resume_is_bitwise(pimd, integrator):
     x0, mass, kw = _water(32, 4, 8)
-    prm = dict(T=300.0, dt=5e-4, barostat=1, pext=1e-3, taup=0.1, **kw)
+    prm = dict(T=300.0, dt=5e-4, barostat=1, pext=1e-3, taup=0.1, integrator=integrator, **kw)
     a = pimd.Simulation(x0, mass, **prm)
     a.step(30)
     x, v, st = a.get_state()
@@ -128,8 +130,9 @@ def test_bzp_checkpoint_resume_is_bitwise(pimd):
     assert a.get_barostat()[0] == b.get_barostat()[0]
 
 
-@pytest.mark.parametrize("thermostat,axes", [(1, 7), (0, 7), (1, 4), (1, 3)])
-def test_bzp_aniso_barostat_water(orc, pimd, thermostat, axes):
+@pytest.mark.parametrize("thermostat,axes,integrator", [(1, 7, 0), (0, 7, 0), (1, 4, 0), (1, 3, 0),
+                                                       (1, 7, 1), (1, 2, 1)])
+def test_bzp_aniso_barostat_water(orc, pimd, thermostat, axes, integrator):
     """Anisotropic BZP barostat (one v_W per edge in baro_axes), 32 molecules
     x 4 beads, 50 steps: positions, velocities, v_Wa, box and outputs 11-15;
     edges outside the mask stay exactly fixed."""
@@ -137,7 +140,7 @@ def test_bzp_aniso_barostat_water(orc, pimd, thermostat, axes):
     probe = orc.Sim(x0, mass, T=300.0, dt=2.5e-4, thermostat=0, **kw)
     pext = probe.estimators()["P_CV"] * 0.8
     c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, thermostat=thermostat, barostat=2,
-                 baro_axes=axes, pext=pext, taup=0.05, **kw)
+                 baro_axes=axes, pext=pext, taup=0.05, integrator=integrator, **kw)
     _run_both(c, g, 50, 1e-8)
     vw, box = g.get_barostat()
     assert np.abs(vw - c.vWa).max() < 1e-8 * max(1.0, np.abs(c.vWa).max())

@@ -374,3 +374,46 @@ def test_bzp_aniso_one_axis_ideal_gas_length(orc):
     target = (N + 1) * KB * T / (pext * L0 * L0)
     assert abs(mu - target) < 3 * sig, (mu, target, sig)
     assert abs(mu - N * KB * T / (pext * L0 * L0)) > 3 * sig
+
+
+# ---- BZP barostat with OBABO -------------------------------------------------
+
+@pytest.mark.parametrize("barostat", [1, 2])
+def test_bzp_obabo_nph_is_the_baoab_nph(orc, barostat):
+    """Without a thermostat OBABO is B A(h) B and BAOAB is B A(h/2) A(h/2) B:
+    the barostat's centroid flow composes exactly (e^a e^a = e^2a, and the
+    sinh form of two halves at one v_W is the sinh form of the whole), so the
+    two NpH trajectories agree to rounding."""
+    x0, mass, kw = _bonded_water(8, 4, 45)
+    common = dict(T=300.0, dt=2e-4, thermostat=0, barostat=barostat, pext=1e-3, taup=0.05, vW=0.5, **kw)
+    a = orc.Sim(x0, mass, integrator=0, **common)
+    b = orc.Sim(x0, mass, integrator=1, **common)
+    a.run(60)
+    b.run(60)
+    assert np.abs(a.x - b.x).max() < 1e-11 and np.abs(a.v - b.v).max() < 1e-8
+    assert np.abs(a.box - b.box).max() < 1e-11 * a.box.max()
+    assert abs(a.box[0] / kw["box"][0] - 1.0) > 1e-5
+
+
+def test_bzp_obabo_npt_ideal_gas_volume(orc):
+    """NpT with OBABO (two O(h/2) per step on particles and on v_W): free atoms
+    give <V> = (N + 1) kB T / P_ext as with BAOAB."""
+    P, N, T = 4, 6, 300.0
+    L0 = 10.0
+    g = np.random.default_rng(7)
+    x0 = np.repeat(g.uniform(0, L0, size=(1, N, 3)), P, axis=0) + g.normal(0, 0.05, size=(P, N, 3))
+    mass = np.full(N, 16.0)
+    ff = (0.0, 1.0, 0.0, 1.8, 0.0, 1.0, 0.5)
+    pext = (N + 1) * KB * T / L0 ** 3
+    s = orc.Sim(x0, mass, T=T, dt=2e-3, potential=1, ff=ff, box=(L0, L0, L0), thermostat=1, tau=0.05,
+                seed=13, barostat=1, pext=pext, taup=0.05, integrator=1)
+    s.run(2000)
+    vols = []
+    for _ in range(3000):
+        s.run(20)
+        vols.append(s.box.prod())
+    from tests._stats import block_mean_sigma
+    mu, sig = block_mean_sigma(vols, 30)
+    target = (N + 1) * KB * T / pext
+    assert abs(mu - target) < 3 * sig, (mu, target, sig)
+    assert abs(mu - N * KB * T / pext) > 3 * sig
