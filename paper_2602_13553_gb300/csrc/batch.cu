@@ -1901,7 +1901,7 @@ void fragment_tables(const std::vector<double> &A, int P, std::vector<float> &hi
 }
 
 SplitStepArgs replica_split_args(const Replica &r) {
-  SplitStepArgs a;
+  SplitStepArgs a{};
   std::memset(&a, 0, sizeof(a));
   a.N = r.N;
   a.P = r.P;
@@ -2201,7 +2201,7 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   }
   if (e == cudaSuccess) e = launch_compress_split(replica_split_args(r), b->stg_x, b->stg_v, b->stream);
   if (e == cudaSuccess) {
-    NbrArgs na;
+    NbrArgs na{};
     std::memset(&na, 0, sizeof(na));
     na.nmol = r.nmol;
     na.P = P;

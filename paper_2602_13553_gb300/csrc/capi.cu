@@ -300,7 +300,7 @@ static int est_threads(int A, int P) {
 }
 
 static StepArgs step_args(pimd_handle *h) {
-  StepArgs a;
+  StepArgs a{};
   a.N = h->N;
   a.P = h->P;
   a.A = h->A_step;
@@ -333,7 +333,7 @@ static StepArgs step_args(pimd_handle *h) {
 }
 
 static ForceArgs force_args(pimd_handle *h) {
-  ForceArgs a;
+  ForceArgs a{};
   a.dbox = h->baro ? h->baro + kBaroL : nullptr;
   a.N = h->N;
   a.P = h->P;
@@ -399,7 +399,7 @@ static NbrArgs nbr_args(pimd_handle *h, bool force) {
 // set_state), so the centroids are recomputed and the list rebuilt.
 // advance: the force kernel also advances the device step counter.
 static SplitStepArgs split_args(pimd_handle *h) {
-  SplitStepArgs a;
+  SplitStepArgs a{};
   a.N = h->N;
   a.P = h->P;
   a.A = h->A_step;
@@ -442,7 +442,7 @@ static SplitStepArgs split_args(pimd_handle *h) {
 
 static SplitForceArgs split_force_args(pimd_handle *h) {
   const ForceArgs f = force_args(h);
-  SplitForceArgs a;
+  SplitForceArgs a{};
   a.N = h->N;
   a.P = h->P;
   a.nmol = h->nmol;
@@ -527,7 +527,8 @@ static pimd_status enqueue_forces(pimd_handle *h, bool from_outside, bool advanc
 // B_W of the barostat over [t0, t0 + tB] of the kick the next kernel
 // applies (App. E); with step_follows also that step's O_W and box.
 static pimd_status enqueue_baro(pimd_handle *h, double t0, double tB, bool step_follows) {
-  BaroArgs b;
+  BaroArgs b{};
+  b.obabo = h->integrator == PIMD_OBABO;
   b.N = h->N;
   b.P = h->P;
   b.nmol = h->nmol;
@@ -544,7 +545,6 @@ static pimd_status enqueue_baro(pimd_handle *h, double t0, double tB, bool step_
   b.tB = tB;
   b.tA = b.obabo ? h->dt : 0.5 * h->dt;
   b.step_follows = step_follows ? 1 : 0;
-  b.obabo = h->integrator == PIMD_OBABO;
   const double kT = kBoltzmann * h->T;
   b.W = (h->baro_axes ? 1.0 : 3.0) * h->P * h->N * kT * h->taup * h->taup;
   b.nkT = h->P * kT;
@@ -602,7 +602,7 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
   if (!h->fixcom) return st;
   // fixcom at the end of this step: the next kernel (step or close) applies
   // this step's closing B(h/2) (and O(h/2)); remove the momentum it will leave
-  FixcomArgs f;
+  FixcomArgs f{};
   f.N = h->N;
   f.P = h->P;
   f.method = h->method;
@@ -1091,7 +1091,7 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
     pimd_status se = expand_split(h, true);
     if (se != PIMD_OK) return se;
   }
-  EstArgs a;
+  EstArgs a{};
   a.N = h->N;
   a.P = P;
   a.A = h->A_est;
@@ -1105,7 +1105,7 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   a.part = h->est_part;
   pimd_status st0 = enqueue(h, PIMD_KIND_EST, 1, [&] { return launch_est(a, h->threads_est, h->stream); });
   if (st0 != PIMD_OK) return st0;
-  EstFinalArgs f;
+  EstFinalArgs f{};
   f.N = h->N;
   f.P = P;
   f.nblk_est = h->nblk_est;
