@@ -160,10 +160,11 @@ class Clocks:
 
 def step_flops_per_bead_atom(P):
     """Algorithmic FP64 flops of the fused step kernel per bead-atom: three
-    dense P-term normal-mode transforms of 3 components (18 P), the merged
-    kick (6), two exact rotations (36) and the O update (9); the Box-Muller
-    noise is not counted."""
-    return 18 * P + 51
+    folded normal-mode transforms of 3 components, each output a sum over one
+    half of its folded row (P/2 + 1 FMAs: 9 P + 18), the folding and
+    recombination adds (9), the merged kick (6), two exact rotations (36) and
+    the O update (9); the Box-Muller noise is not counted."""
+    return 9 * P + 78
 
 
 def force_flops(x, L, rc, rlist):

@@ -167,6 +167,7 @@ struct pimd_handle {
   double *inv_mm = nullptr, *sigv = nullptr, *mass_mm = nullptr, *kspring = nullptr;
   double *M = nullptr, *Mt = nullptr, *cA = nullptr, *sA = nullptr, *wsA = nullptr;
   double *c1 = nullptr, *c2 = nullptr, *lam = nullptr, *mu = nullptr, *imu = nullptr;
+  double *Tf = nullptr, *Ti = nullptr;   // folded transforms, [P/2 + 1][P]
   double *Upart = nullptr, *Wpart = nullptr;
   int nblk_force = 0;
   double *cref = nullptr, *ccur = nullptr, *blkmax = nullptr;
@@ -304,7 +305,7 @@ static StepArgs step_args(pimd_handle *h) {
   a.N = h->N;
   a.P = h->P;
   a.A = h->A_step;
-  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam, h->mu, h->imu};
+  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam, h->mu, h->imu, h->Tf, h->Ti};
   a.inv_mm = h->inv_mm;
   a.sigv = h->sigv;
   a.x = h->x;
@@ -729,6 +730,8 @@ static void carve(pimd_handle *h, Carver &c) {
   h->lam = c.take<double>(P);
   h->mu = c.take<double>(P);
   h->imu = c.take<double>(P);
+  h->Tf = c.take<double>((size_t)(P / 2 + 1) * P);
+  h->Ti = c.take<double>((size_t)(P / 2 + 1) * P);
   // rows of per-bead U / Tr Xi sums: one per molecule (water) or per block
   h->nblk_force = h->potential == PIMD_POT_WATERLIKE ? h->nmol : force_blocks(h->N, P);
   h->Upart = c.take<double>((size_t)h->nblk_force * P);
@@ -867,6 +870,18 @@ void build_tables(int P, double T, double dt, const pimd_params &prm, HostTables
   t.Mt.assign((size_t)P * P, 0.0);
   for (int i = 0; i < P; ++i)
     for (int j = 0; j < P; ++j) t.Mt[(size_t)j * P + i] = t.M[(size_t)i * P + j];
+  // folded transforms: rows k <= H of M are even under j -> P - j, rows k > H
+  // odd, so each output needs one half of a folded row
+  const int H = P / 2;
+  t.Tf.assign((size_t)(H + 1) * P, 0.0);
+  t.Ti.assign((size_t)(H + 1) * P, 0.0);
+  for (int i = 0; i <= H; ++i)
+    for (int k = 0; k < P; ++k) {
+      const int pos = H + 1 + i;   // odd rows: folded position, holding x_{P-pos} - x_pos
+      t.Tf[(size_t)i * P + k] = k <= H ? t.M[(size_t)k * P + i] : (pos < P ? t.M[(size_t)k * P + (P - pos)] : 0.0);
+      const int kodd = H + 1 + i;  // inverse of bead k > H: odd mode kodd at bead P - k
+      t.Ti[(size_t)i * P + k] = k <= H ? t.M[(size_t)i * P + k] : (kodd < P ? t.M[(size_t)kodd * P + (P - k)] : 0.0);
+    }
   const double hbar = prm.sp * kPlanck / (2.0 * kPi);
   t.wn = P * kBoltzmann * T / hbar;                      // Eq. (2)
   t.tA = prm.integrator == PIMD_BAOAB ? 0.5 * dt : dt;
@@ -997,6 +1012,7 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   if ((st = up(h->M, M)) || (st = up(h->Mt, Mt)) || (st = up(h->cA, cA)) || (st = up(h->sA, sA)) ||
       (st = up(h->wsA, wsA)) || (st = up(h->c1, c1v)) || (st = up(h->c2, c2v)) ||
       (st = up(h->lam, lam)) || (st = up(h->mu, tb.mu)) || (st = up(h->imu, tb.imu)) ||
+      (st = up(h->Tf, tb.Tf)) || (st = up(h->Ti, tb.Ti)) ||
       (st = up(h->inv_mm, inv_mm)) || (st = up(h->sigv, sigv)) ||
       (st = up(h->mass_mm, mass_mm)) || (st = up(h->kspring, ksp))) {
     release(h);
@@ -1096,7 +1112,7 @@ extern "C" pimd_status pimd_estimators(pimd_handle *h, pimd_estimates *out) {
   a.P = P;
   a.A = h->A_est;
   a.method = h->method;
-  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam, h->mu, h->imu};
+  a.mt = ModeTables{h->M, h->Mt, h->cA, h->sA, h->wsA, h->c1, h->c2, h->lam, h->mu, h->imu, h->Tf, h->Ti};
   a.mass_mm = h->mass_mm;
   a.x = h->x;
   a.v = h->v;

@@ -111,6 +111,11 @@ struct ModeTables {
   const double *lam;   // [P] lambda_k (Eq. A2)
   const double *mu;    // [P] fictitious-mass factor mu_k: m^(k) = mu_k m (fmmode, fmass)
   const double *imu;   // [P] 1 / mu_k
+  // folded transforms (H = floor(P/2)), [H + 1][P] each:
+  //   Tf[i][k]: k <= H: M[k][i]; k > H: M[k][P - (H + 1 + i)] (0 past the row)
+  //   Ti[i][j]: j <= H: M[i][j]; j > H: M[H + 1 + i][P - j] (0 past the modes)
+  const double *Tf;
+  const double *Ti;
 };
 
 struct StepArgs {

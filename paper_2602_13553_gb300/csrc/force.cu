@@ -263,7 +263,12 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
       const double d2 = fma(-(double)n2, L2, a.x[sj + 2 * P] - xo2);
       const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
       if (r2 < rc2) {
-        const double inv = 1.0 / r2;
+        // 1 / r2 by Newton's iteration x <- x (2 - r2 x) from the FP32
+        // reciprocal: each step squares the relative error (2^-23 -> 2^-46
+        // -> below FP64 rounding), two FMAs each on the FP64 pipe
+        double inv = (double)__frcp_rn((float)r2);
+        inv = fma(inv, fma(-r2, inv, 1.0), inv);
+        inv = fma(inv, fma(-r2, inv, 1.0), inv);
         const double s2 = sig2 * inv;
         const double s6 = s2 * s2 * s2;
         ulj = fma(e4, fma(s6, s6, -s6), ulj);

@@ -14,6 +14,7 @@ namespace pimd {
 // Per-mode tables of App. B / App. D for one (P, T, dt, params), FP64.
 struct HostTables {
   std::vector<double> M, Mt;            // [P][P] Eq. (A1) and its transpose
+  std::vector<double> Tf, Ti;           // [P/2 + 1][P] folded forward / inverse (ModeTables)
   std::vector<double> cA, sA, wsA;      // exact A step of length tA
   std::vector<double> c1, c2;           // O step of length tO
   std::vector<double> lam;              // Eq. (A2)

@@ -49,6 +49,13 @@ __device__ __forceinline__ double warp_max(double v) {
 // Thread task t = (al * 3 + d) * P + k: atom al of the tile, component d,
 // mode k (forward) or bead j = k (inverse).  This is also the offset of the
 // element in the tile, so loads, stores and shared memory share one index.
+// The transforms use the parity of the rows of M (Eq. A1) under j -> P - j:
+// modes k <= H = floor(P/2) (constant, cosine and alternating rows) are even,
+// the sine rows k > H odd.  Staging each row folded -- u_j = x_j + x_{P-j}
+// and u_{P-j} = x_j - x_{P-j} for 0 < j < P - j, x_0 and x_{P/2} kept --
+// makes every forward output a sum over one half of the row (Tf), and every
+// inverse pair x_j, x_{P-j} = C_j +- S_j of an even-mode sum C_j and an
+// odd-mode sum S_j (Ti): about P/2 FMAs per output instead of P.
 __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   extern __shared__ double sm[];
   const int P = a.P;
@@ -64,10 +71,21 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   const int na = min(a.A, a.N - tile0);
   const int len = na * 3 * P;
   const size_t base = (size_t)tile0 * 3 * P;
+  const int H = P >> 1;
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
-    sX[t] = a.x[base + t];
-    sV[t] = a.v[base + t];
-    sF[t] = a.F[base + t];
+    // folded staging of x and F: the partner bead P - j of bead j
+    const int j = t % P, pj = j == 0 ? 0 : P - j;
+    const size_t g = base + t, gp = g - j + pj;
+    const double xa = a.x[g], fa = a.F[g];
+    double xu = xa, fu = fa;
+    if (pj != j) {
+      const double xb = a.x[gp], fb = a.F[gp];
+      xu = j < pj ? xa + xb : xb - xa;
+      fu = j < pj ? fa + fb : fb - fa;
+    }
+    sX[t] = xu;
+    sF[t] = fu;
+    sV[t] = a.v[g];
   }
   const uint64_t step = (uint64_t)(*a.step + a.step_off);
   // Large grids: one Philox draw and Box-Muller per (atom, mode) serve the
@@ -85,7 +103,7 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
     }
   }
   __syncthreads();
-  const double *__restrict__ Mt = a.mt.Mt;
+  const double *__restrict__ Tf = a.mt.Tf;
   for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int k = task % P;
     const int r = task / P;
@@ -93,20 +111,24 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
     auto noise = [&](uint32_t stream, uint64_t st, const double *pre) {
       return a.noise_pre ? pre[task] : gauss1(a.seed, (uint32_t)i, (uint32_t)k, stream, st, r % 3);
     };
-    const double *fx = sF + r * P;
-    const double *xx = sX + r * P;
-    // F~_k = (M F)_k and q~_k = (M x)_k, two independent chains each
+    // F~_k = (M F)_k and q~_k = (M x)_k over the even (k <= H) or odd half
+    // of the folded row, two independent chains each
+    const bool even = k <= H;
+    const int n = even ? H + 1 : P - H - 1;
+    const double *fx = sF + r * P + (even ? 0 : H + 1);
+    const double *xx = sX + r * P + (even ? 0 : H + 1);
+    const double *tf = Tf + k;
     double fa = 0.0, fb = 0.0, qa = 0.0, qb = 0.0;
     int j = 0;
-    for (; j + 1 < P; j += 2) {
-      const double m0 = __ldg(Mt + j * P + k), m1 = __ldg(Mt + (j + 1) * P + k);
+    for (; j + 1 < n; j += 2) {
+      const double m0 = __ldg(tf + j * P), m1 = __ldg(tf + (j + 1) * P);
       fa = fma(m0, fx[j], fa);
       fb = fma(m1, fx[j + 1], fb);
       qa = fma(m0, xx[j], qa);
       qb = fma(m1, xx[j + 1], qb);
     }
-    if (j < P) {
-      const double m0 = __ldg(Mt + j * P + k);
+    if (j < n) {
+      const double m0 = __ldg(tf + j * P);
       fa = fma(m0, fx[j], fa);
       qa = fma(m0, xx[j], qa);
     }
@@ -151,18 +173,30 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   }
   if (a.phase == 1) return;   // velocities only: the barostat's B_W reads them next
   __syncthreads();
-  const double *__restrict__ M = a.mt.M;
+  // inverse, first half: C_j (bead j <= H, even modes) or S_{P-j} (bead
+  // j > H, odd modes) into sF, which the forward pass no longer needs
+  const double *__restrict__ Ti = a.mt.Ti;
   for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int j = task % P;
-    const double *qq = sQ + (task / P) * P;
+    const bool even = j <= H;
+    const int n = even ? H + 1 : P - H - 1;
+    const double *qq = sQ + (task - j) + (even ? 0 : H + 1);
+    const double *ti = Ti + j;
     double xa = 0.0, xb = 0.0;
     int k = 0;
-    for (; k + 1 < P; k += 2) {
-      xa = fma(__ldg(M + k * P + j), qq[k], xa);
-      xb = fma(__ldg(M + (k + 1) * P + j), qq[k + 1], xb);
+    for (; k + 1 < n; k += 2) {
+      xa = fma(__ldg(ti + k * P), qq[k], xa);
+      xb = fma(__ldg(ti + (k + 1) * P), qq[k + 1], xb);
     }
-    if (k < P) xa = fma(__ldg(M + k * P + j), qq[k], xa);
-    const double xn = xa + xb;
+    if (k < n) xa = fma(__ldg(ti + k * P), qq[k], xa);
+    sF[task] = xa + xb;
+  }
+  __syncthreads();
+  // second half: x_j = C_j + S_j (j <= H), x_{P-j} = C_j - S_j
+  for (int task = threadIdx.x; task < len; task += blockDim.x) {
+    const int j = task % P, pj = j == 0 ? 0 : P - j;
+    const int row0 = task - j;
+    const double xn = j <= H ? sF[task] + (pj > H ? sF[row0 + pj] : 0.0) : sF[row0 + pj] - sF[task];
     a.x[base + task] = xn;
     if (a.x32) a.x32[base + task] = (float)xn;
     sX[task] = xn;
