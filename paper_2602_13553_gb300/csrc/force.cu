@@ -109,18 +109,31 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
   __shared__ int s_nl[kMaxNeighbours];
   __shared__ int s_off[kMaxBuckets + 1];
   __shared__ int s_go;
+  __shared__ double s_mx[4][2];
   if (a.check_nbr) {
-    if (warp == 0) {
-      double md = 0.0, me = 0.0;
-      for (int b = lane; b < a.nblk_check; b += 32) {
-        md = fmax(md, a.blkmax[2 * b]);
-        me = fmax(me, a.blkmax[2 * b + 1]);
-      }
+    // the step kernel's per-block maxima: every thread loads its share (one
+    // 16-byte pair per block entry, all loads in flight at once), then warp
+    // and block maxima
+    double md = 0.0, me = 0.0;
+    const double2 *bm = reinterpret_cast<const double2 *>(a.blkmax);
+    for (int b = threadIdx.x; b < a.nblk_check; b += blockDim.x) {
+      const double2 e = bm[b];
+      md = fmax(md, e.x);
+      me = fmax(me, e.y);
+    }
 #pragma unroll
-      for (int o2 = 16; o2 > 0; o2 >>= 1) {
-        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o2));
-        me = fmax(me, __shfl_xor_sync(0xffffffffu, me, o2));
-      }
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+      md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o2));
+      me = fmax(me, __shfl_xor_sync(0xffffffffu, me, o2));
+    }
+    if (lane == 0) {
+      s_mx[warp][0] = md;
+      s_mx[warp][1] = me;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      md = fmax(fmax(s_mx[0][0], s_mx[1][0]), fmax(s_mx[2][0], s_mx[3][0]));
+      me = fmax(fmax(s_mx[0][1], s_mx[1][1]), fmax(s_mx[2][1], s_mx[3][1]));
       int go = 2.0 * md + 2.0 * me > a.skin;
       if (go && m < a.nmol) {
         // bucket b holds the neighbours j = b mod NS in increasing j
