@@ -411,6 +411,59 @@ def cpu_baseline(target_s=12.0):
                       "%.1f s wall" % (n, dt)}
 
 
+def _time_oracle(sim, units_per_step, chunk, budget_s, with_est):
+    """Bead-atom-steps/s of the oracle on `sim` over about budget_s seconds
+    (whole chunks of `chunk` MD steps, estimators after each if asked)."""
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        sim.run(chunk)
+        if with_est:
+            sim.estimators()
+        done += chunk
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            return units_per_step * done / dt, done, dt
+
+
+def oracle_configs(budget_s=2.5):
+    """The oracle on the other workloads of the study, on all host cores and,
+    for the benchmark system, on one core: 64 harmonic oscillators x 8 beads,
+    the 192-atom x 32-bead water box, 512 molecules x 64 beads (a few steps
+    of it) and one replica of the 256-replica mix (its median size)."""
+    import oracle
+    from paper_2602_13553_gb300 import inputs
+    ncores = os.cpu_count() or 1
+    out = []
+    hbar = 4.135667403e-3 / (2 * math.pi)
+
+    def rec(name, sim, units, chunk, threads, with_est=True):
+        oracle.set_threads(threads)
+        v, n, dt = _time_oracle(sim, units, chunk, budget_s, with_est)
+        out.append({"config": name, "value": v, "unit": METRIC, "cores": oracle.max_threads(),
+                    "sample": "%d MD steps, %.1f s" % (n, dt)})
+
+    x0, mass = inputs.harmonic(64, 8, seed=1, std=0.1)
+    rec("64 harmonic oscillators x 8 beads", oracle.Sim(x0, mass, T=300.0, dt=2.5e-4, potential=0,
+                                                         ff=(0.1 / hbar,), seed=1), 64 * 8, 100, ncores)
+    x0, mass, kw = system(1)
+    rec("water-like 192 atoms x 32 beads, one core", oracle.Sim(x0, mass, **kw), 192 * 32, 100, 1)
+    rec("water-like 192 atoms x 32 beads", oracle.Sim(x0, mass, **kw), 192 * 32, 100, ncores)
+    L2 = inputs.box_length(512)
+    x0, mass = inputs.water_box(512, L2, 64, 1, jitter=0.02)
+    rec("water-like 1536 atoms x 64 beads", oracle.Sim(x0, mass, T=300.0, dt=5e-4, potential=1,
+                                                      ff=inputs.water_ff_for_box(L2), box=(L2,) * 3, seed=1),
+        1536 * 64, 2, ncores, with_est=False)
+    reps = sorted(inputs.replica_mix(256, 1), key=lambda r: r.nmol * r.P)
+    r = reps[len(reps) // 2]
+    x0, mass = inputs.water_box(r.nmol, r.L, r.P, r.seed, jitter=0.02, deuterium=r.deuterium)
+    rec("median replica of the mix: %d molecules x %d beads" % (r.nmol, r.P),
+        oracle.Sim(x0, mass, T=r.T, dt=5e-4, potential=1, ff=inputs.water_ff_for_box(r.L), box=(r.L,) * 3,
+                   seed=1), 3 * r.nmol * r.P, 20, ncores)
+    oracle.set_threads(ncores)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -566,6 +619,7 @@ def run_ours(args):
         line["sweep"] = sweep_bench(stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["configs"] = oracle_configs()
     print(json.dumps(line))
     sim.close()
     return 0
