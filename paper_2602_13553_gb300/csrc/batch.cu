@@ -2,13 +2,16 @@
 // size advanced together in split precision, and the serving layer on top.
 //
 // Every replica's state lives in its own device arena and is described by a
-// RepDesc in a device table.  Each MD step is four launches over all
-// replicas -- control, step, neighbour list, forces -- each a persistent grid
-// of fixed size that walks a device-resident work list (step tiles, force
-// clusters, neighbour blocks) whose length it reads from device memory.
-// Because neither grid sizes nor pointers change when replicas join or leave,
-// one CUDA graph of G steps is captured once per batch and replayed for the
-// batch's lifetime: continuous batching without re-capture.  Per-replica
+// RepDesc in a device table.  Each MD step is five or six launches over all
+// replicas -- control, step (warp items, and block items when some replica's
+// bead count needs them), rebuild decision, rebuilds, forces -- each a
+// persistent grid of fixed size that walks a device-resident work list (step
+// tiles, force clusters, neighbour blocks) whose length it reads from device
+// memory.  Because neither grid sizes nor pointers change when replicas join
+// or leave, one CUDA graph of G steps is captured once per batch and replayed
+// for the batch's lifetime: continuous batching without re-capture (a graph
+// is captured again only when block items appear or disappear, or when the
+// warp-item shared-memory slot grows).  Per-replica
 // step counters, step budgets and the "at integer time" flag live on the
 // device, so every replica runs exactly its own number of steps.
 //
@@ -1671,6 +1674,7 @@ struct pimd_batch {
   int h_counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int wslot = 0;          // floats of shared memory per warp of the warp-item step kernel
   int grid_w = 0;         // its blocks (persistent grid)
+  bool block_items = true;   // some replica has a bead count outside the warp-item classes
   int wblocks_sm = 0;     // blocks per SM in use
   int wtuned = 0;         // blocks per SM chosen by the autotuner (0: the occupancy limit)
   int nsm = 152;
@@ -1774,6 +1778,14 @@ pimd_status upload(pimd_batch *b) {
   b->h_counts[4] = nw;
   b->h_counts[5] = 0;
   b->h_counts[6] = 0;
+  const bool blk = b->h_counts[0] > nw;
+  if (blk != b->block_items) {
+    b->block_items = blk;
+    if (b->graph) {   // the captured step launches k_bstep or not
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
   const int slot = pmax_w ? wslot_floats(pmax_w) : wslot_floats(8);
   if (slot != b->wslot) {
     b->wslot = slot;
@@ -1808,7 +1820,7 @@ pimd_status upload(pimd_batch *b) {
 void launch_step_kernels(pimd_batch *b) {
   k_bstep_w<<<b->grid_w, kWWarps * 32, (size_t)kWWarps * b->wslot * sizeof(float), b->stream>>>(
       b->d_reps, b->d_step, b->d_counts, b->d_counts + 5, b->wslot);
-  k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts);
+  if (b->block_items) k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts);
 }
 
 // The rebuild decision over all neighbour items, then the rebuilds listed.
@@ -1816,6 +1828,10 @@ void launch_nbr_kernels(pimd_batch *b) {
   k_bdecide<<<b->nsm, 256, 0, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, b->d_nbr_go, b->d_counts + 6);
   k_bnbr<<<b->grid_nbr, 128, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr_go, b->d_counts + 6);
 }
+
+// Kernels launched per MD step: control, warp-item step, block-item step
+// (when some replica needs it), rebuild decision, rebuilds, forces.
+int step_launches(const pimd_batch *b) { return b->block_items ? 6 : 5; }
 
 // One MD step of every active replica.
 cudaError_t launch_one_step(pimd_batch *b, cudaEvent_t e0, cudaEvent_t e1) {
@@ -2258,13 +2274,13 @@ extern "C" pimd_status pimd_batch_run(pimd_batch *b, int64_t nsteps) {
     if (!b->graph && (st = capture(b)) != PIMD_OK) return st;
     while (left >= b->graph_steps) {
       BK(cudaGraphLaunch(b->graph, b->stream));
-      b->launches += 6 * b->graph_steps;
+      b->launches += (int64_t)step_launches(b) * b->graph_steps;
       left -= b->graph_steps;
     }
   }
   for (; left > 0; --left) {
     BK(launch_one_step(b, nullptr, nullptr));
-    b->launches += 6;
+    b->launches += step_launches(b);
   }
   const int cg = (b->capacity + 127) / 128;
   k_bctl<<<cg, 128, 0, b->stream>>>(b->d_reps, b->capacity, 1, nullptr);
@@ -2383,7 +2399,7 @@ extern "C" pimd_status pimd_batch_time_kernels(pimd_batch *b, int32_t nsteps, do
       BK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
       acc[k] += t;
     }
-    b->launches += 6;
+    b->launches += step_launches(b);
   }
   for (auto &e : ev) cudaEventDestroy(e);
   for (int k = 0; k < 4; ++k) ms[k] = acc[k];
