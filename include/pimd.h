@@ -373,8 +373,10 @@ pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double *x, double 
 /* Pick the step-kernel tile (atoms per block) for every bead count in the
  * batch by timing candidates with CUDA events while the replicas step
  * (steps_per_trial steps per candidate; they count toward the replicas'
- * budgets; trajectories do not depend on the tile).  tiles_out, if not NULL,
- * receives PIMD_MAX_BEADS + 1 entries: the chosen tile per P (0 = unused). */
+ * budgets; trajectories do not depend on the tile), and the blocks per SM of
+ * the warp-item step kernel (bead counts 8, 16, 32, 64).  tiles_out, if not
+ * NULL, receives PIMD_MAX_BEADS + 1 entries: [0] the warp-item blocks per SM,
+ * [P] the chosen tile for bead count P (0 = unused). */
 pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t *tiles_out);
 
 /* Kernel accounting: kernels enqueued so far (graph nodes included), and

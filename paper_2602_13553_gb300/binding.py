@@ -449,7 +449,9 @@ class Batch:
     def autotune(self, steps_per_trial: int = 2):
         tiles = (ctypes.c_int32 * (MAX_BEADS + 1))()
         check(_batch_lib().pimd_batch_autotune(self._h, steps_per_trial, tiles))
-        return {P: tiles[P] for P in range(MAX_BEADS + 1) if tiles[P] > 0}
+        out = {P: tiles[P] for P in range(1, MAX_BEADS + 1) if tiles[P] > 0}
+        out["warp_blocks_per_sm"] = tiles[0]
+        return out
 
     def kernel_launches(self) -> int:
         return int(_batch_lib().pimd_batch_kernel_launches(self._h))

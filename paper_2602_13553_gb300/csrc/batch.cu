@@ -2434,7 +2434,7 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
       BK(cudaEventElapsedTime(&ms, e0, e1));
       total += ms;
     }
-    b->launches += 6 * steps_per_trial;
+    b->launches += (int64_t)step_launches(b) * steps_per_trial;
     *ms_out = total;
     return PIMD_OK;
   };
@@ -2453,7 +2453,7 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
       b->grid_w = b->nsm * nb;
       // one untimed step first (caches and clocks settle), then the trial
       if (launch_one_step(b, nullptr, nullptr) != cudaSuccess) return fail(PIMD_ECUDA, "autotune step failed");
-      b->launches += 6;
+      b->launches += step_launches(b);
       float ms = 0.f;
       st = time_step(&ms);
       if (st == PIMD_OK && ms < best_ms) {
@@ -2508,8 +2508,10 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (tiles_out)
+  if (tiles_out) {
     for (int P = 0; P <= PIMD_MAX_BEADS; ++P) tiles_out[P] = b->tileA[P];
+    tiles_out[0] = b->wblocks_sm;   // blocks per SM of the warp-item step kernel
+  }
   return st;
 }
 
