@@ -57,6 +57,7 @@ constexpr int kMmaTile = 2304;      // max padded rows x (P + 4) over P % 8 == 0
 constexpr int kStepSmem = 3 * kMmaTile;   // floats; >= 4 * kTileMax
 constexpr int kBatchMaxMol = 4096;   // molecules per replica (centroids staged in shared memory)
 constexpr int kNbrMolPerItem = 8;    // molecules per neighbour-list work item
+constexpr int kNbrThreads = 32 * kNbrMolPerItem;   // one warp per molecule
 constexpr size_t kNbrSmem = 3 * kBatchMaxMol * sizeof(float);
 constexpr int kOutStride = 3 * kMaxBeads + 10;  // pimd_estimates layout from K_mode on
 constexpr int kEstItems = 64;        // estimator work items (e-blocks) per replica, at most
@@ -1189,6 +1190,7 @@ __global__ void k_bnbr(const RepDesc *reps, const int2 *items, const int *count)
     {
       // the replica's oxygen centroids (wrapped, FP32) into shared memory
       extern __shared__ float s_cw[];
+#pragma unroll 4
       for (int t = threadIdx.x; t < 3 * R.nmol; t += blockDim.x) s_cw[t] = R.xcw[9 * (t / 3) + t % 3];
       __syncthreads();
       // One warp per molecule of this item's 8: the warp walks the buckets
@@ -1212,21 +1214,40 @@ __global__ void k_bnbr(const RepDesc *reps, const int2 *items, const int *count)
         int *off = R.nbr_off + (size_t)m * (NS + 1);
         int *nl = R.nbr + (size_t)m * kMaxNeighbours;
         int total = 0;
-        for (int b = 0; b < NS; ++b) {
-          if (lane == 0) off[b] = total;
-          for (int j0 = b; j0 < nmol; j0 += 32 * NS) {
-            const int j = j0 + lane * NS;
-            bool hit = false;
-            if (j < nmol && j != m) {
-              const float d0 = micb(cw[3 * j] - c0, L0, i0);
-              const float d1 = micb(cw[3 * j + 1] - c1, L1, i1);
-              const float d2 = micb(cw[3 * j + 2] - c2, L2, i2);
-              hit = d0 * d0 + d1 * d1 + d2 * d2 < rl2;
-            }
+        auto near = [&](int j) {
+          const float d0 = micb(cw[3 * j] - c0, L0, i0);
+          const float d1 = micb(cw[3 * j + 1] - c1, L1, i1);
+          const float d2 = micb(cw[3 * j + 2] - c2, L2, i2);
+          return d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+        };
+        const int n0 = (nmol + NS - 1) / NS;   // candidates of bucket 0, the longest
+        if (n0 <= 16) {
+          // short buckets: 32 / seg consecutive buckets per ballot, seg lanes
+          // each in bucket order, so the lane prefix count is the list order
+          int seg = 1;
+          while (seg < n0) seg <<= 1;
+          const int kb = 32 / seg;
+          const int sg = lane / seg, tl = lane - sg * seg;
+          for (int b = 0; b < NS; b += kb) {
+            const int bb = b + sg, j = bb + tl * NS;
+            const bool hit = bb < NS && j < nmol && j != m && near(j);
             const unsigned mask = __ballot_sync(0xffffffffu, hit);
             const int pos = total + __popc(mask & ((1u << lane) - 1u));
+            if (tl == 0 && bb < NS) off[bb] = pos;
             if (hit && pos < kMaxNeighbours) nl[pos] = j;
             total += __popc(mask);
+          }
+        } else {
+          for (int b = 0; b < NS; ++b) {
+            if (lane == 0) off[b] = total;
+            for (int j0 = b; j0 < nmol; j0 += 32 * NS) {
+              const int j = j0 + lane * NS;
+              const bool hit = j < nmol && j != m && near(j);
+              const unsigned mask = __ballot_sync(0xffffffffu, hit);
+              const int pos = total + __popc(mask & ((1u << lane) - 1u));
+              if (hit && pos < kMaxNeighbours) nl[pos] = j;
+              total += __popc(mask);
+            }
           }
         }
         if (lane == 0) {
@@ -1826,7 +1847,7 @@ void launch_step_kernels(pimd_batch *b) {
 // The rebuild decision over all neighbour items, then the rebuilds listed.
 void launch_nbr_kernels(pimd_batch *b) {
   k_bdecide<<<b->nsm, 256, 0, b->stream>>>(b->d_reps, b->d_nbr, b->d_counts + 2, b->d_nbr_go, b->d_counts + 6);
-  k_bnbr<<<b->grid_nbr, 128, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr_go, b->d_counts + 6);
+  k_bnbr<<<b->grid_nbr, kNbrThreads, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr_go, b->d_counts + 6);
 }
 
 // Kernels launched per MD step: control, warp-item step, block-item step
@@ -1988,14 +2009,14 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
   }
   b->nsm = nsm;
   // persistent grids: every SM filled to the kernel's occupancy limit
-  auto occ = [&](const void *fn, size_t smem = 0) {
+  auto occ = [&](const void *fn, size_t smem = 0, int threads = 128) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, smem) != cudaSuccess || n < 1) n = 2;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess || n < 1) n = 2;
     return nsm * n;
   };
   b->grid_step = occ((const void *)k_bstep);
   b->grid_clu = occ((const void *)k_bforce);
-  b->grid_nbr = occ((const void *)k_bnbr, kNbrSmem);
+  b->grid_nbr = occ((const void *)k_bnbr, kNbrSmem, kNbrThreads);
   b->grid_est = 8 * nsm;
   auto fail_free = [&](pimd_status st) {
     pimd_batch_destroy(b);
@@ -2227,7 +2248,7 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   // initial neighbour list and forces of this replica only
   if (e == cudaSuccess) {
     k_bpos<<<std::min(1024, (r.nmol * 3 * P + 255) / 256), 256, 0, b->stream>>>(b->d_reps, slot);
-    k_bnbr<<<std::max(1, (int)r.items_nbr.size()), 128, kNbrSmem, b->stream>>>(b->d_reps, r.d_items_nbr,
+    k_bnbr<<<std::max(1, (int)r.items_nbr.size()), kNbrThreads, kNbrSmem, b->stream>>>(b->d_reps, r.d_items_nbr,
                                                                         r.d_counts + 2);
     k_bforce<<<std::max(1, (int)std::min<size_t>((r.items_clu.size() + 3) / 4, b->grid_clu)), 128, 0,
                b->stream>>>(b->d_reps, r.d_items_clu, r.d_counts + 1, 1);
