@@ -72,6 +72,8 @@ CASES = [
     (1, 5, 0, 1), (2, 37, 0, 1), (3, 37, 1, 1), (5, 300, 0, 0), (7, 1, 1, 1),
     (8, 700, 1, 1), (16, 131, 0, 1), (32, 70, 1, 0), (64, 19, 0, 1), (100, 9, 1, 1),
     (128, 11, 0, 1), (128, 3, 1, 1),
+    # grids of >= 4 x 152 blocks: one Philox draw per (atom, mode) in a pre-pass
+    (8, 6500, 0, 1), (8, 6500, 1, 1),
 ]
 
 
