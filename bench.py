@@ -223,8 +223,8 @@ def sweep_bench(stream, steps=4, warmup=2):
     64, 128, in FP64 and in split precision.  Per point: bead-atom-steps/s
     over `steps` calls of 10 MD steps (CUDA events on the library's stream)
     and the roofline of the step kernel, from its own CUDA-event time per
-    launch: FP64 against the FP64 pipe (18 P + 51 flops per bead-atom), split
-    against HBM (60 B + 96 B / P per bead-atom)."""
+    launch: FP64 against the FP64 pipe (step_flops_per_bead_atom: folded
+    transforms), split against HBM (60 B + 96 B / P per bead-atom)."""
     import torch
     from paper_2602_13553_gb300 import binding, inputs
     hbar = 4.135667403e-3 / (2 * math.pi)
@@ -256,7 +256,7 @@ def sweep_bench(stream, steps=4, warmup=2):
             pt = {"N": N, "P": P, "precision": name, "value": units * 10 * steps / (ms / 1e3),
                   "step_kernel_ms": step_ms}
             if prec == 0:
-                ach = (18 * P + 51) * units / (step_ms / 1e3) / 1e12
+                ach = step_flops_per_bead_atom(P) * units / (step_ms / 1e3) / 1e12
                 pt["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK / 1e12,
                                   "unit": "TFLOP/s", "frac": ach / (FP64_PEAK / 1e12)}
             else:
