@@ -151,3 +151,21 @@ def test_full_replica_mix_sampled_against_oracle(orc, pimd):
         for k in ("K_CV", "T_ring"):
             assert abs(est[s][k] - ec[k]) < 1e-3 * abs(ec[k]), (s, k)
     b.close()
+
+
+def test_batch_obabo_agrees_with_oracle(orc, pimd):
+    """OBABO replicas (the merged closing B O / opening O B of the warp-item
+    and block-item kernels, bead counts 8, 32 and 100) against the oracle."""
+    b = pimd.Batch(4)
+    reps = [MIX[0], MIX[2], rep(24, 100, 17, 250.0)]
+    slots = [add(b, r, 40, integrator=1) for r in reps]
+    b.run(25)
+    b.run(15)
+    for s, r in zip(slots, reps):
+        c = orc.Sim(r["x0"], r["mass"], T=r["T"], dt=r["dt"], potential=1, ff=r["ff"], box=r["box"],
+                    seed=r["seed"], integrator=1)
+        c.run(40)
+        x, v, st = b.get_state(s)
+        assert st == 40
+        assert np.max(np.abs(x - c.x)) < 1e-4
+    b.close()

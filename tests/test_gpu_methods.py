@@ -175,3 +175,18 @@ def test_bzp_aniso_checkpoint_resume_is_bitwise(pimd):
     assert np.array_equal(a.get_barostat()[0], b.get_barostat()[0])
     with pytest.raises(pimd.PimdError):
         b.set_barostat(np.array([0.0, 1.0, 0.0]), box)      # y is outside the mask
+
+
+@pytest.mark.parametrize("barostat,integrator", [(1, 0), (2, 1)])
+def test_bzp_barostat_with_fixcom(orc, pimd, barostat, integrator):
+    """The barostat and fixcom together: the centroid momentum removal at the
+    end of each step composes with the barostat's centroid scaling."""
+    x0, mass, kw = _water(32, 4, 11)
+    probe = orc.Sim(x0, mass, T=300.0, dt=2.5e-4, thermostat=0, **kw)
+    pext = probe.estimators()["P_CV"] * 0.9
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, barostat=barostat, pext=pext, taup=0.05,
+                 integrator=integrator, fixcom=1, **kw)
+    _run_both(c, g, 50, 1e-8)
+    _, vg, _ = g.get_state()
+    scale = (mass[:, None] * np.abs(vg[0])).sum()
+    assert np.abs((mass[:, None] * vg[0]).sum(axis=0)).max() < 1e-11 * scale
