@@ -162,6 +162,7 @@ struct pimd_handle {
   double *xc = nullptr, *v0 = nullptr;
   float *dev = nullptr, *vk = nullptr, *F32 = nullptr, *xcw = nullptr;
   float *Mf = nullptr, *Mtf = nullptr, *cAf = nullptr, *sAf = nullptr, *wsAf = nullptr;
+  float *Tff = nullptr, *Tif = nullptr;   // split: FP32 folded transforms
   float *c1f = nullptr, *c2f = nullptr;
   double tA = 0.0, c1_0 = 0.0, c2_0 = 0.0;
   double *inv_mm = nullptr, *sigv = nullptr, *mass_mm = nullptr, *kspring = nullptr;
@@ -406,6 +407,8 @@ static SplitStepArgs split_args(pimd_handle *h) {
   a.A = h->A_step;
   a.Mf = h->Mf;
   a.Mtf = h->Mtf;
+  a.Tff = h->Tff;
+  a.Tif = h->Tif;
   a.cAf = h->cAf;
   a.sAf = h->sAf;
   a.wsAf = h->wsAf;
@@ -760,6 +763,8 @@ static void carve(pimd_handle *h, Carver &c) {
     h->xcw = c.take<float>((size_t)N * 3);
     h->Mf = c.take<float>((size_t)P * P);
     h->Mtf = c.take<float>((size_t)P * P);
+    h->Tff = c.take<float>((size_t)(P / 2 + 1) * P);
+    h->Tif = c.take<float>((size_t)(P / 2 + 1) * P);
     h->cAf = c.take<float>(P);
     h->sAf = c.take<float>(P);
     h->wsAf = c.take<float>(P);
@@ -1024,7 +1029,8 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
       CK(cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
       return PIMD_OK;
     };
-    if ((st = upf(h->Mf, M)) || (st = upf(h->Mtf, Mt)) || (st = upf(h->cAf, cA)) ||
+    if ((st = upf(h->Mf, M)) || (st = upf(h->Mtf, Mt)) || (st = upf(h->Tff, tb.Tf)) ||
+        (st = upf(h->Tif, tb.Ti)) || (st = upf(h->cAf, cA)) ||
         (st = upf(h->sAf, sA)) || (st = upf(h->wsAf, wsA)) || (st = upf(h->c1f, c1v)) ||
         (st = upf(h->c2f, c2v))) {
       release(h);

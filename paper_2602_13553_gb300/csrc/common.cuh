@@ -250,6 +250,7 @@ struct NbrArgs {
 struct SplitStepArgs {
   int N, P, A;
   const float *Mf, *Mtf;       // [P][P] FP32 copies of M and M^T
+  const float *Tff, *Tif;      // [P/2 + 1][P] FP32 folded forward / inverse tables (as ModeTables::Tf, Ti)
   const float *cAf, *sAf, *wsAf, *c1f, *c2f;   // FP32 mode coefficients (k >= 1)
   double tA, c1_0, c2_0;       // centroid: drift time of one A, O coefficients
   const double *inv_mm, *sigv; // [N]

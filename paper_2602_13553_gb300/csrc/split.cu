@@ -38,6 +38,30 @@ __device__ __forceinline__ float gauss1f(uint64_t seed, uint32_t atom, uint32_t 
   return r * (d == 1 ? sn : cs);
 }
 
+// The three deviates of gauss1f for d = 0, 1, 2 from one Philox draw (the
+// same words and the same FP32 arithmetic, so the same values).
+__device__ __forceinline__ void gauss3f(uint64_t seed, uint32_t atom, uint32_t mode, uint32_t stream,
+                                        uint64_t step, float &e0, float &e1, float &e2) {
+  const uint4 w = philox4x32_10(
+      make_uint4(atom, (mode & 0xffffu) | (stream << 16), (uint32_t)step, (uint32_t)(step >> 32)),
+      make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const float s = 5.9604644775390625e-8f;  // 2^-24
+  const float r0 = sqrtf(-2.0f * __logf(((float)(w.x >> 8) + 0.5f) * s));
+  const float r1 = sqrtf(-2.0f * __logf(((float)(w.z >> 8) + 0.5f) * s));
+  float sn, cs, sn2, cs2;
+  sincospif(2.0f * (((float)(w.y >> 8) + 0.5f) * s), &sn, &cs);
+  sincospif(2.0f * (((float)(w.w >> 8) + 0.5f) * s), &sn2, &cs2);
+  e0 = r0 * cs;
+  e1 = r0 * sn;
+  e2 = r1 * cs2;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __device__ __forceinline__ void rotatef(float &q, float &v, float c, float s_over_w, float w_s) {
   const float qn = fmaf(c, q, s_over_w * v);
   const float vn = fmaf(-w_s, q, c * v);
@@ -45,11 +69,6 @@ __device__ __forceinline__ void rotatef(float &q, float &v, float c, float s_ove
   v = vn;
 }
 
-__device__ __forceinline__ double warp_maxd(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-  return v;
-}
 
 __device__ __forceinline__ float wrapf(double x, double L, double invL) {
   return L > 0.0 ? (float)(x - L * floor(x * invL)) : (float)x;
@@ -68,38 +87,68 @@ __global__ void __launch_bounds__(256) k_step_split(SplitStepArgs a) {
   float *sV = sD + tileLen;
   float *sF = sV + tileLen;
   float *sQ = sF + tileLen;
-  __shared__ double sred[2][8];
+  float *sE = sQ + tileLen;      // PILE_L deviates of this step (stream O1), per element
+  float *sE2 = sE + tileLen;     // OBABO: stream O2 of the previous step
+  __shared__ float sred[2][8];
   const int tile0 = blockIdx.x * a.A;
   const int na = min(a.A, a.N - tile0);
   const int len = na * 3 * P;
   const size_t base = (size_t)tile0 * 3 * P;
+  // d and F staged folded (u_j = x_j + x_{P-j}, u_{P-j} = x_j - x_{P-j}):
+  // the forward transforms then sum one half of a row (rows of M are even
+  // for modes k <= H = P/2, odd above), as in the FP64 step kernel
+  const int H = P >> 1;
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
-    sD[t] = a.d[base + t];
-    sV[t] = a.vk[base + t];
-    sF[t] = a.F[base + t];
+    const int j = t % P, pj = j == 0 ? 0 : P - j;
+    const size_t g = base + t, gp = g - j + pj;
+    const float da = a.d[g], fa = a.F[g];
+    float du = da, fu = fa;
+    if (pj != j) {
+      const float db = a.d[gp], fb = a.F[gp];
+      du = j < pj ? da + db : db - da;
+      fu = j < pj ? fa + fb : fb - fa;
+    }
+    sD[t] = du;
+    sV[t] = a.vk[g];
+    sF[t] = fu;
+  }
+  const uint64_t step = (uint64_t)(*a.step + a.step_off);
+  // one Philox draw per (atom, mode) serves the three components
+  const bool o2 = a.integrator == 1 && !a.first;
+  if (a.thermo) {
+    for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
+      const int al = t / P, k = t - al * P;
+      const int e = al * 3 * P + k;
+      gauss3f(a.seed, (uint32_t)(tile0 + al), (uint32_t)k, kStreamO1, step, sE[e], sE[e + P], sE[e + 2 * P]);
+      if (o2)
+        gauss3f(a.seed, (uint32_t)(tile0 + al), (uint32_t)k, kStreamO2, step - 1, sE2[e], sE2[e + P],
+                sE2[e + 2 * P]);
+    }
   }
   __syncthreads();
-  const uint64_t step = (uint64_t)(*a.step + a.step_off);
-  const float *__restrict__ Mt = a.Mtf;
+  const float *__restrict__ Tf = a.Tff;
   const float kick = (float)a.kick, half = (float)a.half;
   for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int k = task % P;
     const int r = task / P;
     const int c = r % 3;
     const int i = tile0 + r / 3;
-    const float *fx = sF + r * P;
-    const float *xx = sD + r * P;
+    const bool even = k <= H;
+    const int n = even ? H + 1 : P - H - 1;
+    const float *fx = sF + r * P + (even ? 0 : H + 1);
+    const float *xx = sD + r * P + (even ? 0 : H + 1);
+    const float *tf = Tf + k;
     float fa = 0.f, fb = 0.f, qa = 0.f, qb = 0.f;
     int j = 0;
-    for (; j + 1 < P; j += 2) {
-      const float m0 = __ldg(Mt + j * P + k), m1 = __ldg(Mt + (j + 1) * P + k);
+    for (; j + 1 < n; j += 2) {
+      const float m0 = __ldg(tf + j * P), m1 = __ldg(tf + (j + 1) * P);
       fa = fmaf(m0, fx[j], fa);
       fb = fmaf(m1, fx[j + 1], fb);
       qa = fmaf(m0, xx[j], qa);
       qb = fmaf(m1, xx[j + 1], qb);
     }
-    if (j < P) {
-      const float m0 = __ldg(Mt + j * P + k);
+    if (j < n) {
+      const float m0 = __ldg(tf + j * P);
       fa = fmaf(m0, fx[j], fa);
       qa = fmaf(m0, xx[j], qa);
     }
@@ -116,16 +165,15 @@ __global__ void __launch_bounds__(256) k_step_split(SplitStepArgs a) {
     if (a.integrator == 0) {
       v = fmaf(kick * im, f, v);
       rotatef(q, v, cA, sA, wsA);
-      if (a.thermo) v = fmaf(c1, v, c2s * gauss1f(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
+      if (a.thermo) v = fmaf(c1, v, c2s * sE[task]);
       rotatef(q, v, cA, sA, wsA);
     } else {
       const float kb = half * im;
       if (!a.first) {
         v = fmaf(kb, f, v);
-        if (a.thermo)
-          v = fmaf(c1, v, c2s * gauss1f(a.seed, (uint32_t)i, (uint32_t)k, kStreamO2, step - 1, c));
+        if (a.thermo) v = fmaf(c1, v, c2s * sE2[task]);
       }
-      if (a.thermo) v = fmaf(c1, v, c2s * gauss1f(a.seed, (uint32_t)i, (uint32_t)k, kStreamO1, step, c));
+      if (a.thermo) v = fmaf(c1, v, c2s * sE[task]);
       v = fmaf(kb, f, v);
       rotatef(q, v, cA, sA, wsA);
     }
@@ -146,21 +194,15 @@ __global__ void __launch_bounds__(256) k_step_split(SplitStepArgs a) {
     if (a.integrator == 0) {
       v = fma(a.kick * im, f0, v);
       x = fma(dr, v, x);
-      if (a.thermo)
-        v = fma(a.c1_0, v, a.c2_0 * __ldg(a.sigv + i) *
-                               (double)gauss1f(a.seed, (uint32_t)i, 0u, kStreamO1, step, c));
+      if (a.thermo) v = fma(a.c1_0, v, a.c2_0 * __ldg(a.sigv + i) * (double)sE[t * P]);
       x = fma(dr, v, x);
     } else {
       const double kb = a.half * im;
       if (!a.first) {
         v = fma(kb, f0, v);
-        if (a.thermo)
-          v = fma(a.c1_0, v, a.c2_0 * __ldg(a.sigv + i) *
-                                 (double)gauss1f(a.seed, (uint32_t)i, 0u, kStreamO2, step - 1, c));
+        if (a.thermo) v = fma(a.c1_0, v, a.c2_0 * __ldg(a.sigv + i) * (double)sE2[t * P]);
       }
-      if (a.thermo)
-        v = fma(a.c1_0, v, a.c2_0 * __ldg(a.sigv + i) *
-                               (double)gauss1f(a.seed, (uint32_t)i, 0u, kStreamO1, step, c));
+      if (a.thermo) v = fma(a.c1_0, v, a.c2_0 * __ldg(a.sigv + i) * (double)sE[t * P]);
       v = fma(kb, f0, v);
       x = fma(dr, v, x);
     }
@@ -170,54 +212,72 @@ __global__ void __launch_bounds__(256) k_step_split(SplitStepArgs a) {
     sQ[t * P] = 0.f;   // the deviations carry no centroid mode
   }
   __syncthreads();
-  const float *__restrict__ M = a.Mf;
+  // inverse, first half: C_j (bead j <= H, even modes) or S_{P-j} (bead
+  // j > H, odd modes) into sF, free since the forward pass
+  const float *__restrict__ Ti = a.Tif;
   for (int task = threadIdx.x; task < len; task += blockDim.x) {
     const int j = task % P;
-    const float *qq = sQ + (task / P) * P;
+    const bool even = j <= H;
+    const int n = even ? H + 1 : P - H - 1;
+    const float *qq = sQ + (task - j) + (even ? 0 : H + 1);
+    const float *ti = Ti + j;
     float xa = 0.f, xb = 0.f;
-    int k = 1;
-    for (; k + 1 < P; k += 2) {
-      xa = fmaf(__ldg(M + k * P + j), qq[k], xa);
-      xb = fmaf(__ldg(M + (k + 1) * P + j), qq[k + 1], xb);
+    int k = 0;
+    for (; k + 1 < n; k += 2) {
+      xa = fmaf(__ldg(ti + k * P), qq[k], xa);
+      xb = fmaf(__ldg(ti + (k + 1) * P), qq[k + 1], xb);
     }
-    if (k < P) xa = fmaf(__ldg(M + k * P + j), qq[k], xa);
-    const float dn = xa + xb;
+    if (k < n) xa = fmaf(__ldg(ti + k * P), qq[k], xa);
+    sF[task] = xa + xb;
+  }
+  __syncthreads();
+  // second half: d'_j = C_j + S_j (j <= H), d'_{P-j} = C_j - S_j
+  for (int task = threadIdx.x; task < len; task += blockDim.x) {
+    const int j = task % P, pj = j == 0 ? 0 : P - j;
+    const int row0 = task - j;
+    const float dn = j <= H ? sF[task] + (pj > H ? sF[row0 + pj] : 0.f) : sF[row0 + pj] - sF[task];
     a.d[base + task] = dn;
     sD[task] = dn;
   }
   if (!a.blkmax) return;
   __syncthreads();
-  // neighbour-list skin check of the oxygens: bead spread |d^k| and centroid drift
-  double vdisp = 0.0, vdev = 0.0;
+  // neighbour-list skin check of the oxygens: bead spread |d^k| and centroid
+  // drift, squared and reduced in FP32 (the FP64 pipe is the scarce one; a
+  // relative margin below keeps the bound conservative)
+  float vdisp = 0.f, vdev = 0.f;
   for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
     const int al = t / P, k = t % P;
     const int i = tile0 + al;
     if (i % 3) continue;
     const float *ds = sD + al * 3 * P;
     const float e0 = ds[k], e1 = ds[P + k], e2 = ds[2 * P + k];
-    vdev = fmax(vdev, (double)(e0 * e0 + e1 * e1 + e2 * e2));
+    vdev = fmaxf(vdev, e0 * e0 + e1 * e1 + e2 * e2);
     if (k == 0) {
       const int m = i / 3;
       const double c0 = a.xc[3 * (size_t)i], c1 = a.xc[3 * (size_t)i + 1], c2 = a.xc[3 * (size_t)i + 2];
-      const double g0 = c0 - a.cref[3 * m], g1 = c1 - a.cref[3 * m + 1], g2 = c2 - a.cref[3 * m + 2];
-      vdisp = fmax(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
+      const float g0 = (float)(c0 - a.cref[3 * m]), g1 = (float)(c1 - a.cref[3 * m + 1]);
+      const float g2 = (float)(c2 - a.cref[3 * m + 2]);
+      vdisp = fmaxf(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
       a.ccur[3 * m] = c0;
       a.ccur[3 * m + 1] = c1;
       a.ccur[3 * m + 2] = c2;
     }
   }
-  vdisp = warp_maxd(vdisp);
-  vdev = warp_maxd(vdev);
+  // NaN positions force a rebuild
+  if (vdisp != vdisp) vdisp = __int_as_float(0x7f800000);
+  if (vdev != vdev) vdev = __int_as_float(0x7f800000);
+  vdisp = warp_maxf(vdisp);
+  vdev = warp_maxf(vdev);
   if ((threadIdx.x & 31) == 0) {
     sred[0][threadIdx.x >> 5] = vdisp;
     sred[1][threadIdx.x >> 5] = vdev;
   }
   __syncthreads();
   if (threadIdx.x < 2) {
-    double mx = 0.0;
-    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) mx = fmax(mx, sred[threadIdx.x][w]);
-    // a margin for FP32 rounding of the deviations; NaN forces a rebuild
-    a.blkmax[2 * blockIdx.x + threadIdx.x] = (mx == mx) ? sqrt(mx) + 1e-4 : 1e300;
+    float mx = 0.f;
+    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) mx = fmaxf(mx, sred[threadIdx.x][w]);
+    // margins for FP32 rounding of the deviations and of the squares
+    a.blkmax[2 * blockIdx.x + threadIdx.x] = mx <= 3.0e38f ? sqrt((double)mx) * (1.0 + 1e-6) + 1e-4 : 1e300;
   }
 }
 
@@ -503,7 +563,7 @@ __global__ void k_compress_split(SplitStepArgs a, const double *x, const double 
 }
 
 // --- host launchers ----------------------------------------------------------
-size_t split_step_smem_bytes(int A, int P) { return (size_t)4 * A * 3 * P * sizeof(float); }
+size_t split_step_smem_bytes(int A, int P) { return (size_t)6 * A * 3 * P * sizeof(float); }
 
 cudaError_t launch_step_split(const SplitStepArgs &a, int threads, cudaStream_t s) {
   const int grid = (a.N + a.A - 1) / a.A;
