@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   double *sQ = sF + tileLen;
   double *sE = sQ + tileLen;     // PILE_L deviates of this step, stream O1, per element
   double *sE2 = sE + tileLen;    // OBABO: stream O2 of the previous step
-  __shared__ double sred[2][8];
+  __shared__ float sred[2][8];
   const int tile0 = blockIdx.x * a.A;
   const int na = min(a.A, a.N - tile0);
   const int len = na * 3 * P;
@@ -204,8 +204,15 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   if (!a.blkmax) return;
   // Neighbour-list skin check for the oxygens of this tile: centroid
   // c = q~_0 / sqrt(P), its drift since the last build and the bead spread.
+  // Tiles without an oxygen report zero at once.  The differences are taken
+  // in FP64, their squares and the maxima in FP32 (the FP64 pipe is the
+  // scarce unit; a relative margin keeps the reported bound conservative).
+  if ((tile0 + 2) / 3 * 3 >= tile0 + na) {
+    if (threadIdx.x < 2) a.blkmax[2 * blockIdx.x + threadIdx.x] = 0.0;
+    return;
+  }
   __syncthreads();
-  double vdisp = 0.0, vdev = 0.0;
+  float vdisp = 0.f, vdev = 0.f;
   const double rsp = rsqrt((double)P);
   for (int t = threadIdx.x; t < na * P; t += blockDim.x) {
     const int al = t / P, k = t % P;
@@ -214,29 +221,35 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
     const double *xq = sQ + al * 3 * P;
     const double c0 = xq[0] * rsp, c1 = xq[P] * rsp, c2 = xq[2 * P] * rsp;
     const double *xs = sX + al * 3 * P;
-    const double e0 = xs[k] - c0, e1 = xs[P + k] - c1, e2 = xs[2 * P + k] - c2;
-    vdev = fmax(vdev, e0 * e0 + e1 * e1 + e2 * e2);
+    const float e0 = (float)(xs[k] - c0), e1 = (float)(xs[P + k] - c1), e2 = (float)(xs[2 * P + k] - c2);
+    vdev = fmaxf(vdev, e0 * e0 + e1 * e1 + e2 * e2);
     if (k == 0) {
       const int m = i / 3;
-      const double g0 = c0 - a.cref[3 * m], g1 = c1 - a.cref[3 * m + 1], g2 = c2 - a.cref[3 * m + 2];
-      vdisp = fmax(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
+      const float g0 = (float)(c0 - a.cref[3 * m]), g1 = (float)(c1 - a.cref[3 * m + 1]);
+      const float g2 = (float)(c2 - a.cref[3 * m + 2]);
+      vdisp = fmaxf(vdisp, g0 * g0 + g1 * g1 + g2 * g2);
       a.ccur[3 * m] = c0;
       a.ccur[3 * m + 1] = c1;
       a.ccur[3 * m + 2] = c2;
     }
   }
-  vdisp = warp_max(vdisp);
-  vdev = warp_max(vdev);
+  // NaN positions force a rebuild (and fail later at a synchronising call)
+  if (vdisp != vdisp) vdisp = __int_as_float(0x7f800000);
+  if (vdev != vdev) vdev = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    vdisp = fmaxf(vdisp, __shfl_down_sync(0xffffffffu, vdisp, o));
+    vdev = fmaxf(vdev, __shfl_down_sync(0xffffffffu, vdev, o));
+  }
   if ((threadIdx.x & 31) == 0) {
     sred[0][threadIdx.x >> 5] = vdisp;
     sred[1][threadIdx.x >> 5] = vdev;
   }
   __syncthreads();
   if (threadIdx.x < 2) {
-    double mx = 0.0;
-    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) mx = fmax(mx, sred[threadIdx.x][w]);
-    // NaN positions force a rebuild (and fail later at a synchronising call)
-    a.blkmax[2 * blockIdx.x + threadIdx.x] = (mx == mx) ? sqrt(mx) : 1e300;
+    float mx = 0.f;
+    for (int w = 0; w < (int)((blockDim.x + 31) / 32); ++w) mx = fmaxf(mx, sred[threadIdx.x][w]);
+    a.blkmax[2 * blockIdx.x + threadIdx.x] = mx <= 3.0e38f ? sqrt((double)mx) * (1.0 + 1e-6) : 1e300;
   }
 }
 
