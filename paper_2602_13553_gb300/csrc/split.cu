@@ -79,9 +79,13 @@ __device__ __forceinline__ float wrapf(double x, double L, double invL) {
 // slot keeps F~_0 for phase 2.  Phase 2: centroid tasks (al, c) in FP64 --
 // kick, drift, O with an FP32 deviate, drift -- packed one per lane; and
 // the inverse transform of the internal modes into new deviations.
+// PT > 0 fixes the bead count at compile time (the index arithmetic of every
+// element -- divisions by P and by 3 -- then reduces to shifts and multiplies,
+// which matter in this issue-bound kernel); PT = 0 reads it from the arguments.
+template <int PT>
 __global__ void __launch_bounds__(256) k_step_split(SplitStepArgs a) {
   extern __shared__ float smf[];
-  const int P = a.P;
+  const int P = PT > 0 ? PT : a.P;
   const int tileLen = a.A * 3 * P;
   float *sD = smf;
   float *sV = sD + tileLen;
@@ -567,7 +571,15 @@ size_t split_step_smem_bytes(int A, int P) { return (size_t)6 * A * 3 * P * size
 
 cudaError_t launch_step_split(const SplitStepArgs &a, int threads, cudaStream_t s) {
   const int grid = (a.N + a.A - 1) / a.A;
-  k_step_split<<<grid, threads, split_step_smem_bytes(a.A, a.P), s>>>(a);
+  const size_t smem = split_step_smem_bytes(a.A, a.P);
+  switch (a.P) {
+    case 8: k_step_split<8><<<grid, threads, smem, s>>>(a); break;
+    case 16: k_step_split<16><<<grid, threads, smem, s>>>(a); break;
+    case 32: k_step_split<32><<<grid, threads, smem, s>>>(a); break;
+    case 64: k_step_split<64><<<grid, threads, smem, s>>>(a); break;
+    case 128: k_step_split<128><<<grid, threads, smem, s>>>(a); break;
+    default: k_step_split<0><<<grid, threads, smem, s>>>(a); break;
+  }
   return cudaGetLastError();
 }
 
