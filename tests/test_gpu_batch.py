@@ -169,3 +169,20 @@ def test_batch_obabo_agrees_with_oracle(orc, pimd):
         assert st == 40
         assert np.max(np.abs(x - c.x)) < 1e-4
     b.close()
+
+
+@pytest.mark.parametrize("kw", [dict(sp=0.5), dict(thermostat=0), dict(tau=0.2, scale=0.5)])
+def test_batch_keywords_agree_with_oracle(orc, pimd, kw):
+    """Keywords that change only the mode tables or switch the thermostat
+    (sp, NVE, tau and scale) in the batch engine, against the oracle."""
+    b = pimd.Batch(2)
+    r = MIX[1]
+    s = add(b, r, 30, **kw)
+    b.run(30)
+    c = orc.Sim(r["x0"], r["mass"], T=r["T"], dt=r["dt"], potential=1, ff=r["ff"], box=r["box"],
+                seed=r["seed"], **kw)
+    c.run(30)
+    x, _, st = b.get_state(s)
+    assert st == 30
+    assert np.max(np.abs(x - c.x)) < 1e-4
+    b.close()
