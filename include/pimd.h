@@ -324,6 +324,20 @@ pimd_status pimd_kernel_times(pimd_handle *h, double *ms, int64_t *launches);
  * replayed CUDA graphs included); -1 for a NULL handle. */
 int64_t pimd_kernel_launches(const pimd_handle *h);
 
+/* The PILE_L noise of App. D (eta ~ N(0, 1), independent per mode, atom and
+ * step) exactly as the FP64 step kernels draw it, for checking a trajectory's
+ * noise: for mode k < n_modes and atom i < n_atoms, the four Philox-4x32-10
+ * words of counter (i, (k & 0xffff) | (stream << 16), step low 32, step high
+ * 32) under key (seed low 32, seed high 32), and the three Box-Muller
+ * deviates made from them (the keying and map described at pimd_create).
+ *   words  host [n_modes][n_atoms][4] uint32, or NULL
+ *   eta    host [n_modes][n_atoms][3] double, or NULL
+ * EINVAL unless 1 <= n_atoms, 1 <= n_modes <= 65536, n_atoms n_modes <= 2^24
+ * and stream < 65536.  Allocates and frees its own device buffers and
+ * synchronises the device. */
+pimd_status pimd_noise_sample(uint64_t seed, uint32_t stream, uint64_t step, int32_t n_atoms, int32_t n_modes,
+                              uint32_t *words, double *eta);
+
 /* ---- batches of independent systems --------------------------------------
  * A batch advances many independent water-like ring-polymer systems
  * ("replicas": their own N, P, T, masses, seed and step count) together in

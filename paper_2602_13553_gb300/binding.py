@@ -103,7 +103,7 @@ EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "p
            "pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
            "pimd_set_state", "pimd_get_barostat", "pimd_set_barostat", "pimd_destroy",
            "pimd_set_kernel_timing", "pimd_kernel_times",
-           "pimd_kernel_launches", "pimd_estimators_noalloc",
+           "pimd_kernel_launches", "pimd_noise_sample", "pimd_estimators_noalloc",
            "pimd_batch_replica_bytes", "pimd_batch_create", "pimd_batch_add", "pimd_batch_remove",
            "pimd_batch_run", "pimd_batch_sync", "pimd_batch_status", "pimd_batch_estimators",
            "pimd_batch_get_state", "pimd_batch_autotune", "pimd_batch_kernel_launches",
@@ -156,6 +156,9 @@ def lib():
         L.pimd_kernel_times.restype = ctypes.c_int
         L.pimd_kernel_launches.argtypes = [vp]
         L.pimd_kernel_launches.restype = ctypes.c_int64
+        L.pimd_noise_sample.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32), dp]
+        L.pimd_noise_sample.restype = ctypes.c_int
         for f in ("pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
                   "pimd_set_state", "pimd_get_barostat", "pimd_set_barostat"):
             getattr(L, f).restype = ctypes.c_int
@@ -174,6 +177,16 @@ def _dp(a):
         return None
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def noise_sample(seed: int, stream: int, step: int, n_atoms: int, n_modes: int):
+    """Philox words [n_modes][n_atoms][4] (uint32) and FP64 deviates
+    [n_modes][n_atoms][3] of one (seed, stream, step), from the device."""
+    words = np.zeros((n_modes, n_atoms, 4), dtype=np.uint32)
+    eta = np.zeros((n_modes, n_atoms, 3))
+    check(lib().pimd_noise_sample(seed, stream, step, n_atoms, n_modes,
+                                  words.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _dp(eta)))
+    return words, eta
 
 
 def default_params(**kw) -> Params:

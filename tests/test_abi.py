@@ -133,3 +133,13 @@ def test_null_handle_calls(L):
     e = b.Estimates()
     assert L.pimd_estimators(None, ctypes.byref(e)) == 1
     L.pimd_destroy(None)
+
+
+def test_noise_sample_rejects_bad_sizes(L):
+    """Argument checks come before any CUDA call, so they run without a GPU."""
+    w = (ctypes.c_uint32 * 16)()
+    e = (ctypes.c_double * 12)()
+    assert L.pimd_noise_sample(1, 0, 0, 0, 4, w, e) == 1          # n_atoms < 1
+    assert L.pimd_noise_sample(1, 0, 0, 4, 0, w, e) == 1          # n_modes < 1
+    assert L.pimd_noise_sample(1, 70000, 0, 4, 4, w, e) == 1      # stream >= 2^16
+    assert L.pimd_noise_sample(1, 0, 0, 1 << 20, 32, w, e) == 1   # more than 2^24 draws

@@ -29,8 +29,8 @@ def test_philox_weyl_constants_from_definition(orc):
         one = 1 << w
         phi_frac = (math.isqrt(5 * one * one) - one) // 2      # floor(2^w (sqrt5 - 1)/2)
         s3 = math.isqrt(3 * one * one) - one                     # floor(2^w (sqrt3 - 1))
-        # round 1 with ctr = 0: hi/lo of products are 0 -> c = (k0, 0, k1, 0)
-        # round 2 (key bumped): products of (k0) and (k1) ... check via 1-round identity instead
+        # first Philox round with ctr = 0: hi/lo of products are 0 -> c = (k0, 0, k1, 0)
+        # second Philox round (key bumped): checked through the one-round identity instead
         out1 = orc.philox4(w, 1, [0, 0, 0, 0], [0, 0])
         assert list(map(int, out1)) == [0, 0, 0, 0]
         # with ctr zero and key K, one round gives (k0, 0, k1, 0)
