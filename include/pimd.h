@@ -338,13 +338,24 @@ int64_t pimd_kernel_launches(const pimd_handle *h);
 pimd_status pimd_noise_sample(uint64_t seed, uint32_t stream, uint64_t step, int32_t n_atoms, int32_t n_modes,
                               uint32_t *words, double *eta);
 
+/* FP64 fused multiply-add throughput of the current device in TFLOP/s (2
+ * flops per FMA), measured with CUDA events over one launch of 4 blocks of
+ * 256 threads per SM, each thread running eight independent chains of iters
+ * FMAs (after one untimed launch): the FP64 peak the step and force kernels'
+ * arithmetic is compared with.  Allocates a small device buffer and
+ * synchronises the device.  EINVAL for iters < 1 or a NULL output. */
+pimd_status pimd_fp64_fma_rate(int32_t iters, double *tflops);
+
 /* ---- batches of independent systems --------------------------------------
  * A batch advances many independent water-like ring-polymer systems
  * ("replicas": their own N, P, T, masses, seed and step count) together in
  * split precision (PIMD_PREC_SPLIT arithmetic).  Each MD step of the batch
- * is four kernel launches covering every replica; they are captured once in a
- * CUDA graph and replayed, and replicas can be added and removed between
- * calls without re-capture.  Each replica stops after its own step count;
+ * is five kernel launches covering every replica -- control, fused step
+ * (warp items for bead counts 8, 16, 32, 64), rebuild decision, neighbour-list
+ * rebuilds, forces -- and a sixth, the block-item step, while some replica's
+ * bead count is outside {8, 16, 32, 64}; they are captured once in a CUDA
+ * graph and replayed, and replicas can be added and removed between calls
+ * without re-capture.  Each replica stops after its own step count;
  * a replica's trajectory does not depend on which other replicas share the
  * batch.  Same units, layouts and error rules as the single-system calls. */
 typedef struct pimd_batch pimd_batch;
@@ -395,20 +406,26 @@ pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t 
 
 /* Kernel accounting: kernels enqueued so far (graph nodes included), and
  * nsteps real steps launched one kernel at a time with CUDA events around
- * each of the step's four kernels: ms[0..3] receive the summed device
- * milliseconds of the control, fused-step, neighbour-list and force kernels.
+ * four groups of the step's kernels: ms[0..3] receive the summed device
+ * milliseconds of the control kernel, the fused-step kernels (warp items and,
+ * when launched, block items), the neighbour-list kernels (rebuild decision
+ * and rebuilds) and the force kernel.
  * The timed steps leave the replicas at integer time, like pimd_batch_run. */
 int64_t pimd_batch_kernel_launches(const pimd_batch *b);
 pimd_status pimd_batch_time_kernels(pimd_batch *b, int32_t nsteps, double *ms);
 void pimd_batch_destroy(pimd_batch *b);
 
 /* ---- serving -----------------------------------------------------------------
- * A server owns one batch and a worker thread.  Submitted jobs wait in a FIFO
+ * A server owns one batch and a worker thread.  Submitted jobs wait in a
  * queue; between chunks of chunk_steps MD steps the worker admits queued jobs
  * while their device memory (pimd_batch_replica_bytes) fits the HBM budget
  * and a slot is free, so jobs that arrive while others run join the running
  * batch (continuous batching); finished jobs leave it and free their memory.
- * All server calls are thread-safe. */
+ * Admission scans the queue in submission order and admits the first job
+ * that fits; a job at the head that does not fit can be passed by at most 32
+ * later jobs, after which admission waits until it fits.  The worker never
+ * holds the server's lock during device work, so submit, poll and cancel do
+ * not wait for the GPU.  All server calls are thread-safe. */
 typedef struct pimd_server pimd_server;
 
 pimd_status pimd_server_create(size_t hbm_budget_bytes, int32_t max_replicas, int64_t chunk_steps,
@@ -442,37 +459,59 @@ typedef struct {
 } pimd_server_stats;
 pimd_status pimd_server_stats_get(pimd_server *s, pimd_server_stats *out);
 
+/* Keep (enable = 1) or stop keeping (0) a host copy of every job's final
+ * state as it finishes, for pimd_server_get_state.  Off by default: a copy
+ * costs 48 P N bytes of host memory until it is fetched. */
+pimd_status pimd_server_keep_state(pimd_server *s, int enable);
+
+/* The final state of a finished job, as pimd_batch_get_state: x [P][N][3]
+ * (A), v_nm [P][N][3] (A/ps), *step; any pointer may be NULL.  The copy is
+ * released once fetched.  EPENDING while the job is queued or running;
+ * ENOTFOUND for unknown or cancelled jobs and for jobs that finished while
+ * keeping was off (or whose copy was already fetched). */
+pimd_status pimd_server_get_state(pimd_server *s, uint64_t job, double *x, double *v_nm, int64_t *step);
+
 /* Stop the worker (queued and running jobs are dropped) and free everything. */
 void pimd_server_destroy(pimd_server *s);
 
 /* ---- estimators without any allocation -----------------------------------
- * The paper has no counterpart to this entry point.  It computes the same
- * App. A outputs as pimd_estimators, but for a state held in the caller's
- * own device buffers and without allocating any memory: no cudaMalloc, no
- * cudaFree, no pinned or host heap allocation.  It exists for callers that
- * cannot let a library allocate device memory: a host application that owns
- * a fixed device pool reserved at start-up, or a time-stepping loop in which
- * an allocation would synchronise the device and stall its other streams.
- * Every intermediate lives in one statically sized device array of 1 MiB
- * inside this library; every GPU that loads the library holds it until the
- * process exits.
- *   x, v_nm, F  device arrays [P][N][3]: Cartesian positions (A), normal-mode
- *               velocities at integer time (A/ps), Cartesian forces (eV/A)
+ * The paper has no counterpart to this entry point.  It computes the
+ * estimators that pimd_estimators reports (K_mode through vir_sum), but for a
+ * state held in the caller's own device buffers, and it allocates no memory
+ * at all: no cudaMalloc, no cudaFree, no pinned or host heap allocation.  It
+ * exists for callers that cannot let a library allocate: a host application
+ * that owns a fixed device pool reserved at start-up, or a time-stepping loop
+ * in which an allocation would synchronise the device and stall its other
+ * streams.  Every intermediate lives in one statically sized device array of
+ * 1 MiB inside this library; every GPU that loads the library holds it until
+ * the process exits.
+ *   x, v_nm, F  device arrays [P][N][3]: Cartesian positions (A), velocities
+ *               at integer time (A/ps; normal-mode velocities for method
+ *               nmpimd, bead velocities for method pimd), Cartesian forces
+ *               (eV/A)
  *   mass        device [N] (amu);  U_bead device [P] (eV), bead energies
  *   vir_sum     sum_k Tr Xi^(k) (eV);  volume in A^3, 0 for no box (NaN
- *               pressures);  T (K) and sp as at pimd_create
- *   stream      cudaStream_t the kernels run on; the call synchronises it
- *   out         host struct; step is set to 0
+ *               pressures);  T (K) as at pimd_create
+ *   params      the keywords the estimators depend on -- sp, method, fmmode,
+ *               fmass, read as pimd_create reads them -- or NULL for the
+ *               defaults (sp 1, nmpimd, fmmode physical, fmass 1); the
+ *               other fields are ignored
+ *   stream      cudaStream_t the kernels run on; the call waits for it
+ *   out         host struct; step is set to 0; outputs 11-15, box and vWa
+ *               are set to 0 (no barostat or box edges reach this call)
  * Limits: 1 <= P <= 128 and 1 <= N with 3 N P < 2^31; other sizes are
- * EINVAL.  The array is shared by every call on a device and keeps the last
- * call's contents; each call rewrites all it reads, but calls whose kernels
- * overlap on one GPU race and must be serialised by the caller.  The first
- * call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. */
-pimd_status pimd_estimators_noalloc(int32_t N, int32_t P, double T, double sp, double volume,
-                                    const double *x, const double *v_nm, const double *F,
-                                    const double *mass, const double *U_bead, double vir_sum,
+ * EINVAL, as are T <= 0, volume < 0, sp <= 0, fmass <= 0 and fmmode normal
+ * with method pimd.  The call synchronises the stream and copies the result
+ * into *out before it returns.  The array is shared by every call on a
+ * device and keeps the last call's contents; each call rewrites all it
+ * reads, but calls whose kernels overlap on one GPU race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current),
+ * which loads the library's device code there if nothing has yet; make that
+ * first call before any stream capture begins on the device. */
+pimd_status pimd_estimators_noalloc(int32_t N, int32_t P, double T, double volume, const double *x,
+                                    const double *v_nm, const double *F, const double *mass,
+                                    const double *U_bead, double vir_sum, const pimd_params *params,
                                     void *stream, pimd_estimates *out);
 
 #ifdef __cplusplus

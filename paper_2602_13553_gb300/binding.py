@@ -103,13 +103,14 @@ EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "p
            "pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
            "pimd_set_state", "pimd_get_barostat", "pimd_set_barostat", "pimd_destroy",
            "pimd_set_kernel_timing", "pimd_kernel_times",
-           "pimd_kernel_launches", "pimd_noise_sample", "pimd_estimators_noalloc",
+           "pimd_kernel_launches", "pimd_noise_sample", "pimd_fp64_fma_rate", "pimd_estimators_noalloc",
            "pimd_batch_replica_bytes", "pimd_batch_create", "pimd_batch_add", "pimd_batch_remove",
            "pimd_batch_run", "pimd_batch_sync", "pimd_batch_status", "pimd_batch_estimators",
            "pimd_batch_get_state", "pimd_batch_autotune", "pimd_batch_kernel_launches",
            "pimd_batch_time_kernels",
            "pimd_batch_destroy", "pimd_server_create", "pimd_batch_submit", "pimd_batch_poll",
-           "pimd_batch_cancel", "pimd_server_job_times", "pimd_server_stats_get", "pimd_server_destroy")
+           "pimd_batch_cancel", "pimd_server_job_times", "pimd_server_stats_get", "pimd_server_keep_state",
+           "pimd_server_get_state", "pimd_server_destroy")
 KINDS = ("step", "force", "nbr", "close", "est", "other")
 
 _lock = threading.Lock()
@@ -159,6 +160,8 @@ def lib():
         L.pimd_noise_sample.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32), dp]
         L.pimd_noise_sample.restype = ctypes.c_int
+        L.pimd_fp64_fma_rate.argtypes = [ctypes.c_int32, dp]
+        L.pimd_fp64_fma_rate.restype = ctypes.c_int
         for f in ("pimd_create", "pimd_step", "pimd_sync", "pimd_estimators", "pimd_get_state",
                   "pimd_set_state", "pimd_get_barostat", "pimd_set_barostat"):
             getattr(L, f).restype = ctypes.c_int
@@ -177,6 +180,13 @@ def _dp(a):
         return None
     assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def fp64_fma_rate(iters: int = 20000) -> float:
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    out = ctypes.c_double()
+    check(lib().pimd_fp64_fma_rate(int(iters), ctypes.byref(out)))
+    return out.value
 
 
 def noise_sample(seed: int, stream: int, step: int, n_atoms: int, n_modes: int):
@@ -375,6 +385,8 @@ def _batch_lib():
         "pimd_batch_cancel": ([vp, ctypes.c_uint64], ctypes.c_int),
         "pimd_server_job_times": ([vp, ctypes.c_uint64, dp, dp, dp], ctypes.c_int),
         "pimd_server_stats_get": ([vp, ctypes.POINTER(ServerStats)], ctypes.c_int),
+        "pimd_server_keep_state": ([vp, ctypes.c_int], ctypes.c_int),
+        "pimd_server_get_state": ([vp, ctypes.c_uint64, dp, dp, i64], ctypes.c_int),
         "pimd_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -489,12 +501,16 @@ class Batch:
 class Server:
     """Continuous-batching PIMD job server (pimd_server)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_replicas: int = 256, chunk_steps: int = 100, stream=None):
+    def __init__(self, hbm_budget_bytes: int, max_replicas: int = 256, chunk_steps: int = 100, stream=None,
+                 keep_state: bool = False):
         L = _batch_lib()
         h = ctypes.c_void_p()
         check(L.pimd_server_create(int(hbm_budget_bytes), max_replicas, chunk_steps,
                                    ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
         self._h = h
+        self.shapes = {}
+        if keep_state:
+            check(L.pimd_server_keep_state(h, 1))
 
     def submit(self, x0, mass, *, T, dt, nsteps, ff, box, v0=None, gamma0=0.0, **params) -> int:
         s = make_system(x0, mass, ff=ff, box=box, v0=v0)
@@ -502,7 +518,17 @@ class Server:
         job = ctypes.c_uint64()
         check(_batch_lib().pimd_batch_submit(self._h, ctypes.byref(s), x0.shape[0], T, dt, gamma0,
                                              ctypes.byref(prm), int(nsteps), ctypes.byref(job)))
+        self.shapes[job.value] = (x0.shape[0], x0.shape[1])
         return job.value
+
+    def get_state(self, job: int):
+        """(x, v_nm, step) of a finished job (the server must keep states)."""
+        P, N = self.shapes[job]
+        x = np.zeros((P, N, 3))
+        v = np.zeros((P, N, 3))
+        st = ctypes.c_int64()
+        check(_batch_lib().pimd_server_get_state(self._h, job, _dp(x), _dp(v), ctypes.byref(st)))
+        return x, v, st.value
 
     def poll(self, job: int):
         """None while pending; the estimator dict once done; raises on failure."""

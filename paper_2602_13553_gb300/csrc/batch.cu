@@ -2561,7 +2561,14 @@ struct Job {
   int64_t steps_seen = 0;
   pimd_estimates result{};
   double t_submit = -1, t_start = -1, t_end = -1;
+  int bypassed = 0;                 // admissions of later jobs while this one waited at the head
+  std::vector<double> final_x, final_v;   // kept final state (pimd_server_keep_state)
+  int64_t final_step = -1;
 };
+
+// A job at the head of the queue that does not fit lets later jobs that fit
+// go first, at most this many times; then admission waits for it.
+constexpr int kMaxBypass = 32;
 
 }  // namespace serving
 }  // namespace pimd
@@ -2581,6 +2588,7 @@ struct pimd_server {
   pimd_server_stats stats{};
   std::vector<int64_t> st_step, st_left;
   std::vector<pimd_estimates> est;
+  bool keep_state = false;
 };
 
 namespace {
@@ -2589,44 +2597,88 @@ double now_s(pimd_server *s) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
 }
 
+// Admit queued jobs while one fits the budget and a slot is free.  The queue
+// is scanned in FIFO order and the first job that fits is admitted (a head
+// job that does not fit can be passed kMaxBypass times).  Called with the
+// lock held; the lock is released around pimd_batch_add, which computes the
+// job's initial forces on the GPU, so submissions and polls never wait for
+// device work.
+void admit(pimd_server *s, std::unique_lock<std::mutex> &lk) {
+  using namespace pimd::serving;
+  for (;;) {
+    uint64_t id = 0;
+    bool found = false, head = true, head_blocked = false;
+    for (auto it = s->queue.begin(); it != s->queue.end();) {
+      Job &q = s->jobs[*it];
+      if (q.cancel) {
+        q.state = kCancelled;
+        it = s->queue.erase(it);
+        continue;
+      }
+      if (s->used + q.bytes <= s->budget) {
+        id = *it;
+        s->queue.erase(it);
+        found = true;
+        break;
+      }
+      if (head) {
+        if (q.bypassed >= kMaxBypass) break;   // the head waits for memory; nothing passes it
+        head_blocked = true;
+      }
+      head = false;
+      ++it;
+    }
+    if (!found) return;
+    if (head_blocked) s->jobs[s->queue.front()].bypassed++;
+    Job &j = s->jobs[id];
+    s->used += j.bytes;   // reserved while the job is added
+    pimd_system sys;
+    sys.n_atoms = j.n_atoms;
+    sys.potential = j.potential;
+    sys.mass = j.mass.data();
+    sys.pos = j.pos.data();
+    sys.vel = j.vel.empty() ? nullptr : j.vel.data();
+    std::memcpy(sys.box, j.box, sizeof(sys.box));
+    std::memcpy(sys.ff, j.ff, sizeof(sys.ff));
+    const int32_t P = j.P;
+    const double T = j.T, dt = j.dt, gamma0 = j.gamma0;
+    const pimd_params prm = j.params;
+    const int64_t nsteps = j.nsteps;
+    int32_t slot = -1;
+    lk.unlock();   // the job's arrays are only read by this thread meanwhile
+    const pimd_status st = pimd_batch_add(s->batch, &sys, P, T, dt, gamma0, &prm, nsteps, &slot);
+    lk.lock();
+    if (st == PIMD_EBUDGET) {   // no free slot: back to the head, wait for a job to leave
+      s->used -= j.bytes;
+      s->queue.push_front(id);
+      return;
+    }
+    if (st != PIMD_OK) {
+      s->used -= j.bytes;
+      j.state = kFailed;
+      j.status = st;
+      j.t_end = now_s(s);
+      s->stats.failed++;
+      continue;
+    }
+    j.state = kRunning;
+    j.slot = slot;
+    j.t_start = now_s(s);
+  }
+}
+
 void server_loop(pimd_server *s) {
   using namespace pimd::serving;
+  struct Leaving {
+    uint64_t id;
+    int slot;
+    bool keep;
+    std::vector<double> x, v;
+    int64_t step;
+  };
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stop) {
-    // admission: FIFO while the head fits the budget and a slot is free
-    while (!s->queue.empty()) {
-      const uint64_t id = s->queue.front();
-      Job &j = s->jobs[id];
-      if (j.cancel) {
-        s->queue.pop_front();
-        j.state = kCancelled;
-        continue;
-      }
-      if (s->used + j.bytes > s->budget) break;
-      pimd_system sys;
-      sys.n_atoms = j.n_atoms;
-      sys.potential = j.potential;
-      sys.mass = j.mass.data();
-      sys.pos = j.pos.data();
-      sys.vel = j.vel.empty() ? nullptr : j.vel.data();
-      std::memcpy(sys.box, j.box, sizeof(sys.box));
-      std::memcpy(sys.ff, j.ff, sizeof(sys.ff));
-      int32_t slot = -1;
-      const pimd_status st = pimd_batch_add(s->batch, &sys, j.P, j.T, j.dt, j.gamma0, &j.params, j.nsteps, &slot);
-      if (st == PIMD_EBUDGET) break;   // no free slot: wait for a job to leave
-      s->queue.pop_front();
-      if (st != PIMD_OK) {
-        j.state = kFailed;
-        j.status = st;
-        j.t_end = now_s(s);
-        s->stats.failed++;
-        continue;
-      }
-      j.state = kRunning;
-      j.slot = slot;
-      j.t_start = now_s(s);
-      s->used += j.bytes;
-    }
+    admit(s, lk);
     int running = 0;
     for (auto &kv : s->jobs)
       if (kv.second.state == kRunning) ++running;
@@ -2650,6 +2702,8 @@ void server_loop(pimd_server *s) {
     lk.lock();
     s->stats.chunks++;
     s->stats.gpu_busy_s += t_after - t_run;
+    std::vector<Leaving> leaving;
+    const bool keep = s->keep_state;
     for (auto &kv : s->jobs) {
       Job &j = kv.second;
       if (j.state != kRunning) continue;
@@ -2660,21 +2714,55 @@ void server_loop(pimd_server *s) {
       }
       const bool finished = st == PIMD_OK && s->st_left[j.slot] == 0;
       if (st != PIMD_OK || finished || j.cancel) {
+        Leaving l;
+        l.id = kv.first;
+        l.slot = j.slot;
+        l.keep = keep && st == PIMD_OK && finished && !j.cancel;
+        l.step = -1;
+        if (l.keep) {
+          l.x.resize((size_t)j.P * j.n_atoms * 3);
+          l.v.resize(l.x.size());
+        }
         if (st != PIMD_OK) {
           j.state = kFailed;
           j.status = st;
           s->stats.failed++;
+          j.t_end = t_after;
         } else if (j.cancel) {
           j.state = kCancelled;
+          j.t_end = t_after;
         } else {
-          j.state = kDone;
-          j.result = s->est[j.slot];
-          s->stats.completed++;
+          j.result = s->est[j.slot];   // marked done once its memory is released
         }
-        j.t_end = t_after;
-        pimd_batch_remove(s->batch, j.slot);
-        s->used -= j.bytes;
-        j.slot = -1;
+        leaving.push_back(std::move(l));
+      }
+    }
+    if (leaving.empty()) continue;
+    // copies of kept states and removals outside the lock
+    lk.unlock();
+    for (Leaving &l : leaving) {
+      if (l.keep && pimd_batch_get_state(s->batch, l.slot, l.x.data(), l.v.data(), &l.step) != PIMD_OK) {
+        l.x.clear();
+        l.v.clear();
+        l.step = -1;
+      }
+      pimd_batch_remove(s->batch, l.slot);
+    }
+    const double t_left = now_s(s);
+    lk.lock();
+    for (Leaving &l : leaving) {
+      Job &j = s->jobs[l.id];
+      s->used -= j.bytes;
+      j.slot = -1;
+      if (j.state == kRunning) {
+        j.state = kDone;
+        j.t_end = t_left;
+        s->stats.completed++;
+        if (l.keep) {
+          j.final_x = std::move(l.x);
+          j.final_v = std::move(l.v);
+          j.final_step = l.step;
+        }
       }
     }
   }
@@ -2796,5 +2884,34 @@ extern "C" pimd_status pimd_server_stats_get(pimd_server *s, pimd_server_stats *
   if (!s || !out) return fail(PIMD_EINVAL, "NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
   *out = s->stats;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_server_keep_state(pimd_server *s, int enable) {
+  if (!s) return fail(PIMD_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->keep_state = enable != 0;
+  return PIMD_OK;
+}
+
+extern "C" pimd_status pimd_server_get_state(pimd_server *s, uint64_t job, double *x, double *v_nm,
+                                             int64_t *step) {
+  using namespace pimd::serving;
+  if (!s) return fail(PIMD_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->jobs.find(job);
+  if (it == s->jobs.end() || it->second.state == kCancelled)
+    return fail(PIMD_ENOTFOUND, "unknown job %llu", (unsigned long long)job);
+  Job &j = it->second;
+  if (j.state == kQueued || j.state == kRunning) return PIMD_EPENDING;
+  if (j.state == kFailed) return fail(j.status, "job %llu failed", (unsigned long long)job);
+  if (j.final_step < 0) return fail(PIMD_ENOTFOUND, "no final state kept for job %llu", (unsigned long long)job);
+  const size_t n = (size_t)j.P * j.n_atoms * 3;
+  if (x) std::memcpy(x, j.final_x.data(), n * sizeof(double));
+  if (v_nm) std::memcpy(v_nm, j.final_v.data(), n * sizeof(double));
+  if (step) *step = j.final_step;
+  std::vector<double>().swap(j.final_x);
+  std::vector<double>().swap(j.final_v);
+  j.final_step = -1;
   return PIMD_OK;
 }

@@ -1,6 +1,6 @@
 """GPU path (FP64, through the C ABI) against the FP64 CPU oracle for the
 method keywords of Sec. III.C: method pimd (Cartesian beads), fmmode normal,
-fmass and fixcom.  Same bars as the normal-mode parity tests: 1e-10 after 100
+fmass, sp and fixcom.  Same bars as the normal-mode parity tests: 1e-10 after 100
 steps (harmonic), 1e-8 after 50 steps (water-like), estimators within them."""
 import math
 
@@ -56,6 +56,22 @@ def test_fictitious_masses_harmonic(orc, pimd, fmmode, fmass):
     c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, potential=0, ff=(OMEGA_HO,),
                  fmmode=fmmode, fmass=fmass, tau=0.05)
     _run_both(c, g, 100, 1e-10)
+
+
+@pytest.mark.parametrize("method,integrator,sp", [(0, 0, 0.5), (0, 1, 2.0), (1, 0, 0.7), (1, 1, 1.5)])
+def test_scaled_hbar_harmonic(orc, pimd, method, integrator, sp):
+    """Keyword sp (hbar -> sp hbar, only omega_n changes, Eq. 2) on the FP64
+    handle, normal modes and Cartesian beads, BAOAB and OBABO."""
+    x0, mass = inputs.harmonic(64, 8, seed=5, std=0.1)
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, potential=0, ff=(OMEGA_HO,),
+                 integrator=integrator, method=method, sp=sp)
+    _run_both(c, g, 100, 1e-10)
+
+
+def test_scaled_hbar_water(orc, pimd):
+    x0, mass, kw = _water(16, 8, 6)
+    c, g = _pair(orc, pimd, x0, mass, T=300.0, dt=2.5e-4, sp=0.6, **kw)
+    _run_both(c, g, 50, 1e-8)
 
 
 def test_fictitious_masses_water_obabo(orc, pimd):

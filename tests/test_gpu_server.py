@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2602_13553_gb300 import inputs
-from tests._gpu import pimd  # noqa: F401
+from tests._gpu import assert_split_close, pimd  # noqa: F401
 from tests.test_gpu_batch import MIX
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +49,46 @@ def test_result_same_alone_and_in_mix(pimd):
         assert abs(mixed[k] - alone[k]) <= 1e-12 * abs(alone[k]), k
     st = srv.stats()
     assert st["completed"] == 2 + 1 + len(late) and st["failed"] == 0
+    srv.close()
+
+
+def test_served_job_agrees_with_oracle(orc, pimd):
+    """A job submitted into a running mix is served to completion; its final
+    state and every estimator are compared with the oracle run of the same
+    inputs for the same number of steps, at the split-precision bars."""
+    srv = pimd.Server(8 << 30, max_replicas=16, chunk_steps=25, keep_state=True)
+    early = [submit(srv, MIX[0], 300), submit(srv, MIX[5], 200)]
+    time.sleep(0.05)
+    jobs = {submit(srv, MIX[2], 60): MIX[2], submit(srv, MIX[3], 45): MIX[3]}
+    res = wait(srv, early + list(jobs))
+    for j, r in jobs.items():
+        x, v, st = srv.get_state(j)
+        n = 60 if r is MIX[2] else 45
+        assert st == n and res[j]["step"] == n
+        c = orc.Sim(r["x0"], r["mass"], T=r["T"], dt=r["dt"], potential=1, ff=r["ff"], box=r["box"],
+                    seed=r["seed"])
+        c.run(n)
+        assert_split_close(x, v, res[j], c, c.estimators(), "served job %d" % j)
+        with pytest.raises(pimd.PimdError) as ei:   # the kept copy is released once fetched
+            srv.get_state(j)
+        assert ei.value.status == 7
+    srv.close()
+
+
+def test_small_jobs_pass_a_head_job_that_does_not_fit(pimd):
+    """A head job that must wait for memory does not idle the budget: a later
+    job that fits is admitted while the head waits."""
+    big, small = MIX[2], MIX[0]
+    nb = pimd.replica_bytes(big["x0"].shape[1], big["x0"].shape[0])
+    ns = pimd.replica_bytes(small["x0"].shape[1], small["x0"].shape[0])
+    assert ns < nb
+    srv = pimd.Server(nb + ns, max_replicas=8, chunk_steps=20)
+    first = submit(srv, big, 2000)      # holds nb of the budget for a while
+    head = submit(srv, big, 20)         # cannot fit until the first finishes
+    later = submit(srv, small, 20)      # fits beside the first
+    wait(srv, [first, head, later])
+    t_first, t_head, t_later = srv.times(first), srv.times(head), srv.times(later)
+    assert t_later[1] < t_first[2] <= t_head[1] + 1e-9
     srv.close()
 
 
