@@ -100,6 +100,7 @@ struct RepDesc {
   double *cref, *ccur;
   int *nbr, *nbr_off;
   double *Upart, *Wpart, *epart;
+  const int *mperm;           // [nmol] molecules in space-filling-curve order (force work order)
 };
 
 // ---------------------------------------------------------------------------
@@ -1288,9 +1289,10 @@ __device__ __forceinline__ void bforce_item(const RepDesc &R, const int4 w, int 
     const int Bk = P < 32 ? P : 32;
     const int G = 32 / Bk;
     const int u = lane / Bk, kl = lane % Bk;
-    const int m = w.y + u;
+    const int pos = w.y + u;
     const int k = w.z * Bk + kl;
-    if (u >= G || m >= R.nmol || k >= P) return;
+    if (u >= G || pos >= R.nmol || k >= P) return;
+    const int m = __ldg(R.mperm + pos);
     const int o = 3 * m;
     const float L0 = R.boxf[0], L1 = R.boxf[1], L2 = R.boxf[2];
     const float i0 = R.invboxf[0], i1 = R.invboxf[1], i2 = R.invboxf[2];
@@ -1388,10 +1390,182 @@ __device__ __forceinline__ void bforce_item(const RepDesc &R, const int4 w, int 
   }
 }
 
+// Bonded terms (two O-H bonds, the H-O-H angle) of molecule m at bead k:
+// forces on O and the two H, and the bead's bonded energy and virial.  Same
+// arithmetic as the scalar item above.
+__device__ __forceinline__ void bonded_bead(const RepDesc &R, int P, int m, int k, float (&fO)[3],
+                                            float (&fH)[2][3], float &ub, float &wb) {
+  const int o = 3 * m;
+  const float L0 = R.boxf[0], L1 = R.boxf[1], L2 = R.boxf[2];
+  const float i0 = R.invboxf[0], i1 = R.invboxf[1], i2 = R.invboxf[2];
+  const size_t so = (size_t)o * 3 * P + k;
+  const float co0 = R.xcw[3 * o], co1 = R.xcw[3 * o + 1], co2 = R.xcw[3 * o + 2];
+  const float do0 = R.d[so], do1 = R.d[so + P], do2 = R.d[so + 2 * P];
+  float dv[2][3], r[2], ir[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int hh = o + 1 + h;
+    const size_t sh = (size_t)hh * 3 * P + k;
+    dv[h][0] = micb(R.xcw[3 * hh] - co0, L0, i0) + (R.d[sh] - do0);
+    dv[h][1] = micb(R.xcw[3 * hh + 1] - co1, L1, i1) + (R.d[sh + P] - do1);
+    dv[h][2] = micb(R.xcw[3 * hh + 2] - co2, L2, i2) + (R.d[sh + 2 * P] - do2);
+    r[h] = sqrtf(dv[h][0] * dv[h][0] + dv[h][1] * dv[h][1] + dv[h][2] * dv[h][2]);
+    ir[h] = 1.f / r[h];
+  }
+  ub = 0.f;
+  wb = 0.f;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float dr = r[h] - R.r0f;
+    ub = fmaf(0.5f * R.kbf * dr, dr, ub);
+    const float g = -R.kbf * dr * ir[h];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      fH[h][c] = g * dv[h][c];
+      wb = fmaf(dv[h][c], fH[h][c], wb);
+    }
+  }
+  {
+    const float ir01 = ir[0] * ir[1];
+    const float dot = dv[0][0] * dv[1][0] + dv[0][1] * dv[1][1] + dv[0][2] * dv[1][2];
+    const float cth = fminf(1.f, fmaxf(-1.f, dot * ir01));
+    const float th = acosf(cth);
+    const float dth = th - R.th0f;
+    const float pref = R.kthf * dth / sinf(th);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = 1 - h;
+      const float ch = cth * ir[h] * ir[h];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float fa = pref * fmaf(dv[g][c], ir01, -ch * dv[h][c]);
+        fH[h][c] += fa;
+        wb = fmaf(dv[h][c], fa, wb);
+      }
+    }
+    ub = fmaf(0.5f * R.kthf * dth, dth, ub);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) fO[c] = -(fH[0][c] + fH[1][c]);
+}
+
+__device__ __forceinline__ float2 ldg2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+
+// Minimum image of a pair of components: d - L rint(d / L), elementwise.
+__device__ __forceinline__ float2 micb2(float2 d, float2 invL, float2 nL) {
+  float2 t = __fmul2_rn(d, invL);
+  t.x = rintf(t.x);
+  t.y = rintf(t.y);
+  return __ffma2_rn(t, nL, d);
+}
+
+// The work item of k_bforce for an even bead count, two adjacent beads
+// (k, k + 1) per lane: lane = (group u, bead pair kl) with Bk = min(P, 64)
+// beads per group and G = 32 / (Bk / 2) molecules per warp.  The pair loop
+// runs on packed FP32 pairs (Blackwell's two-wide FP32 add, multiply and
+// fused multiply-add), each element rounded exactly as the scalar item
+// rounds it, so the forces, energies and virials are the scalar item's; a
+// bead of the pair outside the cutoff adds exact zeros.  The neighbour
+// index and the list bounds serve both beads.
+template <int PT>
+__device__ __forceinline__ void bforce_item2(const RepDesc &R, const int4 w, int lane) {
+  const int P = PT > 0 ? PT : R.P;
+  const int Bk = P < 64 ? P : 64;
+  const int Lg = Bk >> 1;
+  const int G = 32 / Lg;
+  const int u = lane / Lg, kl = lane - u * Lg;
+  const int pos = w.y + u;
+  const int k = w.z * Bk + 2 * kl;
+  if (u >= G || pos >= R.nmol || k >= P) return;
+  const int m = __ldg(R.mperm + pos);
+  float fO[2][3], fH[2][2][3], ub[2], wb[2];
+  bonded_bead(R, P, m, k, fO[0], fH[0], ub[0], wb[0]);
+  bonded_bead(R, P, m, k + 1, fO[1], fH[1], ub[1], wb[1]);
+  const float2 iL0 = make_float2(R.invboxf[0], R.invboxf[0]), nL0 = make_float2(-R.boxf[0], -R.boxf[0]);
+  const float2 iL1 = make_float2(R.invboxf[1], R.invboxf[1]), nL1 = make_float2(-R.boxf[1], -R.boxf[1]);
+  const float2 iL2 = make_float2(R.invboxf[2], R.invboxf[2]), nL2 = make_float2(-R.boxf[2], -R.boxf[2]);
+  const int NS = kLJWarps * R.G;
+  const int *off = R.nbr_off + (size_t)m * (NS + 1);
+  const int q1 = __ldg(off + NS);
+  const int *__restrict__ nl = R.nbr + (size_t)m * kMaxNeighbours;
+  const float rc2 = R.rc2f;
+  const float2 sig2 = make_float2(R.sig2f, R.sig2f), e4 = make_float2(R.e4f, R.e4f);
+  const float2 ne4 = make_float2(-R.e4f, -R.e4f), ne24 = make_float2(-R.e24f, -R.e24f);
+  const float2 e48 = make_float2(2.0f * R.e24f, 2.0f * R.e24f);
+  const float *__restrict__ pO = R.pO;
+  const float *__restrict__ pm = pO + (size_t)m * 3 * P + k;
+  const float2 p0 = ldg2(pm), p1 = ldg2(pm + P), p2 = ldg2(pm + 2 * P);
+  const float2 np0 = make_float2(-p0.x, -p0.y), np1 = make_float2(-p1.x, -p1.y), np2 = make_float2(-p2.x, -p2.y);
+  float2 f0 = make_float2(fO[0][0], fO[1][0]), f1 = make_float2(fO[0][1], fO[1][1]);
+  float2 f2 = make_float2(fO[0][2], fO[1][2]);
+  float2 ulj = make_float2(0.f, 0.f), wlj = make_float2(0.f, 0.f);
+  // one candidate: the pair's minimum-image separation for both beads and,
+  // inside the cutoff, the Lennard-Jones force, energy and virial
+  auto pair = [&](float2 a0, float2 a1, float2 a2) {
+    const float2 d0 = micb2(__fadd2_rn(a0, np0), iL0, nL0);
+    const float2 d1 = micb2(__fadd2_rn(a1, np1), iL1, nL1);
+    const float2 d2 = micb2(__fadd2_rn(a2, np2), iL2, nL2);
+    const float2 r2 = __ffma2_rn(d2, d2, __ffma2_rn(d1, d1, __fmul2_rn(d0, d0)));
+    const bool in0 = r2.x < rc2, in1 = r2.y < rc2;
+    if (in0 || in1) {
+      // a bead outside the cutoff gets 1/r^2 = 0: every term it adds is an exact zero
+      const float2 inv = make_float2(in0 ? __fdividef(1.0f, r2.x) : 0.f, in1 ? __fdividef(1.0f, r2.y) : 0.f);
+      const float2 s2 = __fmul2_rn(sig2, inv);
+      const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+      ulj = __ffma2_rn(s6, __ffma2_rn(e4, s6, ne4), ulj);
+      const float2 fr = __fmul2_rn(__fmul2_rn(__ffma2_rn(e48, s6, ne24), s6), inv);
+      const float2 nfr = make_float2(-fr.x, -fr.y);
+      f0 = __ffma2_rn(nfr, d0, f0);
+      f1 = __ffma2_rn(nfr, d1, f1);
+      f2 = __ffma2_rn(nfr, d2, f2);
+      wlj = __ffma2_rn(fr, r2, wlj);
+    }
+  };
+  // four candidates per round: their indices, then their twelve rows, are
+  // requested before any arithmetic, so the gathers overlap; the candidates
+  // are then summed in list order
+  int q = __ldg(off);
+  for (; q + 4 <= q1; q += 4) {
+    int jj[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) jj[v] = __ldg(nl + q + v);
+    float2 a[4][3];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const float *__restrict__ pj = pO + (size_t)jj[v] * 3 * P + k;
+      a[v][0] = ldg2(pj);
+      a[v][1] = ldg2(pj + P);
+      a[v][2] = ldg2(pj + 2 * P);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) pair(a[v][0], a[v][1], a[v][2]);
+  }
+  for (; q < q1; ++q) {
+    const float *__restrict__ pj = pO + (size_t)__ldg(nl + q) * 3 * P + k;
+    pair(ldg2(pj), ldg2(pj + P), ldg2(pj + 2 * P));
+  }
+  const size_t so = (size_t)(3 * m) * 3 * P + k;
+  float *__restrict__ F = R.F;
+  const float2 fo[3] = {f0, f1, f2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    *reinterpret_cast<float2 *>(F + so + c * P) = fo[c];
+    *reinterpret_cast<float2 *>(F + so + 3 * P + c * P) = make_float2(fH[0][0][c], fH[1][0][c]);
+    *reinterpret_cast<float2 *>(F + so + 6 * P + c * P) = make_float2(fH[0][1][c], fH[1][1][c]);
+  }
+  double *up = R.Upart + (size_t)m * P + k, *wp = R.Wpart + (size_t)m * P + k;
+  up[0] = (double)fmaf(0.5f, ulj.x, ub[0]);
+  up[1] = (double)fmaf(0.5f, ulj.y, ub[1]);
+  wp[0] = (double)fmaf(0.5f, wlj.x, wb[0]);
+  wp[1] = (double)fmaf(0.5f, wlj.y, wb[1]);
+}
+
 __global__ void __launch_bounds__(128, 6) k_bforce(const RepDesc *__restrict__ reps, const int4 *__restrict__ items,
                                                 const int *__restrict__ count, int force_all) {
   const int n = *count;
   const int lane = threadIdx.x & 31;
+  // the warps of a block take consecutive items (molecules in
+  // space-filling-curve order, so they share neighbour rows in L1)
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int it = gw; it < n; it += nw) {
@@ -1399,11 +1573,16 @@ __global__ void __launch_bounds__(128, 6) k_bforce(const RepDesc *__restrict__ r
     const RepDesc *__restrict__ Rp = reps + w.x;
     if (!force_all && !Rp->ctl[kCtlActive]) continue;
     switch (Rp->P) {
-      case 8: bforce_item<8>(*Rp, w, lane); break;
-      case 16: bforce_item<16>(*Rp, w, lane); break;
-      case 32: bforce_item<32>(*Rp, w, lane); break;
-      case 64: bforce_item<64>(*Rp, w, lane); break;
-      default: bforce_item<0>(*Rp, w, lane); break;
+      case 8: bforce_item2<8>(*Rp, w, lane); break;
+      case 16: bforce_item2<16>(*Rp, w, lane); break;
+      case 32: bforce_item2<32>(*Rp, w, lane); break;
+      case 64: bforce_item2<64>(*Rp, w, lane); break;
+      default:
+        if (Rp->P & 1)
+          bforce_item<0>(*Rp, w, lane);
+        else
+          bforce_item2<0>(*Rp, w, lane);
+        break;
     }
   }
 }
@@ -1413,8 +1592,8 @@ __global__ void __launch_bounds__(128, 6) k_bforce(const RepDesc *__restrict__ r
 // bead mean of d in FP32 from the FP32 deviations, relative error ~P 2^-24;
 // r - r_c = d - mean_j d_j); products and sums in FP64.
 __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *items, const int *count) {
-  __shared__ double sK[128], sS[128];
-  __shared__ double sred[3][4];
+  __shared__ CSum sK[128], sS[128];
+  __shared__ CSum sred[3][4];
   const int n = *count;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = items[it];
@@ -1423,7 +1602,7 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
     const int A = P >= 128 ? 1 : 128 / P;       // estimator tile: A P <= 128 tasks
     const int ntiles = (N + A - 1) / A;
     const int ntask = A * P;
-    double kk = 0.0, ss = 0.0, rF = 0.0, rcF = 0.0, mv0 = 0.0;
+    CSum kk{0.0, 0.0}, ss{0.0, 0.0}, rF{0.0, 0.0}, rcF{0.0, 0.0}, mv0{0.0, 0.0};
     for (int tile = w.y; tile < ntiles; tile += R.ne) {
       const int tile0 = tile * A;
       for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
@@ -1457,12 +1636,12 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
           const float dk = dr[k];
           const double xk = R.xc[(size_t)i * 3 + c] + (double)dk;
           const double fk = (double)R.F[row + k];
-          rF += xk * fk;
-          rcF += (double)(dk - (dma + dmb) * invP) * fk;
+          rF.add(xk * fk);
+          rcF.add((double)(dk - (dma + dmb) * invP) * fk);
         }
-        kk += 0.5 * mm * v2;
-        ss += 0.5 * mm * R.wn2 * __ldg(R.lam + k) * q2;
-        if (k == 0) mv0 += mm * v2;
+        kk.add(0.5 * mm * v2);
+        ss.add(0.5 * mm * R.wn2 * __ldg(R.lam + k) * q2);
+        if (k == 0) mv0.add(mm * v2);
       }
     }
     // per-mode sums: tile tasks never exceed the 128 threads, so thread t
@@ -1472,20 +1651,17 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
     sS[threadIdx.x] = ss;
     __syncthreads();
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
-      double a = 0.0, b2 = 0.0;
+      CSum a{0.0, 0.0}, b2{0.0, 0.0};
       for (int t = k; t < ntask; t += P) {
-        a += sK[t];
-        b2 += sS[t];
+        a.add(sK[t]);
+        b2.add(sS[t]);
       }
-      out[k] = a;
-      out[P + k] = b2;
+      out[k] = a.value();
+      out[P + k] = b2.value();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      rF += __shfl_down_sync(0xffffffffu, rF, o);
-      rcF += __shfl_down_sync(0xffffffffu, rcF, o);
-      mv0 += __shfl_down_sync(0xffffffffu, mv0, o);
-    }
+    rF = warp_csum(rF);
+    rcF = warp_csum(rcF);
+    mv0 = warp_csum(mv0);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) {
       sred[0][threadIdx.x >> 5] = rF;
@@ -1494,9 +1670,9 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-      double sum = 0.0;
-      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) sum += sred[threadIdx.x][ww];
-      out[2 * P + threadIdx.x] = sum;
+      CSum sum{0.0, 0.0};
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) sum.add(sred[threadIdx.x][ww]);
+      out[2 * P + threadIdx.x] = sum.value();
     }
     if (threadIdx.x == 3) out[2 * P + 3] = 0.0;
     __syncthreads();
@@ -1643,6 +1819,7 @@ size_t layout_replica(Replica &r, char *base) {
   d.Upart = carve_ptr<double>(base, off, nmol * P);
   d.Wpart = carve_ptr<double>(base, off, nmol * P);
   d.epart = carve_ptr<double>(base, off, kEstItems * (2 * P + 4));
+  d.mperm = carve_ptr<int>(base, off, nmol);
   r.d_items_step = carve_ptr<int2>(base, off, N);
   r.d_items_nbr = carve_ptr<int2>(base, off, (nmol + kNbrMolPerItem - 1) / kNbrMolPerItem);
   r.d_items_clu = carve_ptr<int4>(base, off, nmol * ((P + 31) / 32));
@@ -1737,8 +1914,11 @@ void replica_items(pimd_batch *b, int slot, Replica &r) {
   for (int mb = 0; mb < (r.nmol + kNbrMolPerItem - 1) / kNbrMolPerItem; ++mb)
     r.items_nbr.push_back(make_int2(slot, mb));
   r.items_clu.clear();
-  const int nchunk = (r.P + 31) / 32;
-  const int per = r.P < 32 ? 32 / r.P : 1;   // molecules per warp
+  // force items (molecules per warp, bead chunks): even bead counts take two
+  // beads per lane in chunks of 64, odd ones one bead per lane in chunks of 32
+  const int cb = r.P % 2 == 0 ? 64 : 32;
+  const int nchunk = (r.P + cb - 1) / cb;
+  const int per = r.P < cb ? 32 / ((r.P % 2 == 0) ? r.P / 2 : r.P) : 1;   // molecules per warp
   for (int m = 0; m < r.nmol; m += per)
     for (int c = 0; c < nchunk; ++c) r.items_clu.push_back(make_int4(slot, m, c, 0));
   r.items_est.clear();
@@ -2154,6 +2334,37 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
     inv_mmf[i] = (float)inv_mm[i];
     sigvf[i] = (float)sigv[i];
   }
+  // force work order: molecules sorted along a Morton curve of their initial
+  // oxygen bead-mean positions (wrapped into the box, 10 bits per axis), so
+  // consecutive items are near each other in space and share neighbours
+  const int nmol = N / 3;
+  std::vector<int> mperm(nmol);
+  {
+    std::vector<std::pair<uint64_t, int>> key(nmol);
+    auto spread = [](uint64_t v) {   // bits of v at every third position
+      uint64_t x = v & 0x3ff;
+      x = (x | (x << 16)) & 0x30000ff;
+      x = (x | (x << 8)) & 0x300f00f;
+      x = (x | (x << 4)) & 0x30c30c3;
+      x = (x | (x << 2)) & 0x9249249;
+      return x;
+    };
+    for (int m = 0; m < nmol; ++m) {
+      uint64_t code = 0;
+      for (int c = 0; c < 3; ++c) {
+        double a = 0.0;
+        for (int k = 0; k < P; ++k) a += sys->pos[((size_t)k * N + 3 * m) * 3 + c];
+        a /= P;
+        const double L = sys->box[c];
+        double f = a / L - std::floor(a / L);
+        if (!(f >= 0.0 && f < 1.0)) f = 0.0;
+        code |= spread((uint64_t)(f * 1024.0)) << c;
+      }
+      key[m] = {code, m};
+    }
+    std::sort(key.begin(), key.end());
+    for (int m = 0; m < nmol; ++m) mperm[m] = key[m].second;
+  }
   std::vector<float> Mf(tb.M.begin(), tb.M.end()), Mtf(tb.Mt.begin(), tb.Mt.end());
   if (!b->ptab[P]) {
     float *t = (float *)dev_alloc(b->alloc, 2 * (size_t)P * P * sizeof(float), b->stream);
@@ -2218,6 +2429,7 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
       {r.d_items_step, r.items_step.data(), r.items_step.size() * sizeof(int2)},
       {r.d_items_nbr, r.items_nbr.data(), r.items_nbr.size() * sizeof(int2)},
       {r.d_items_clu, r.items_clu.data(), r.items_clu.size() * sizeof(int4)},
+      {(void *)d.mperm, mperm.data(), nmol * sizeof(int)},
       {r.d_counts, counts, sizeof(counts)},
       {b->d_reps + slot, &d, sizeof(RepDesc)},
   };

@@ -91,6 +91,34 @@ __device__ __forceinline__ double gauss1(uint64_t seed, uint32_t atom, uint32_t 
   return r * (d == 1 ? sinpi(ang) : cospi(ang));
 }
 
+// Compensated running sum: (s, c) holds s + c, every addition keeping its
+// rounding error in c (Neumaier's variant of Kahan summation), so a sum of
+// many terms carries about one rounding of the total.  Plain aggregate
+// (usable in shared memory); start from CSum{0.0, 0.0}.
+struct CSum {
+  double s, c;
+  __device__ __forceinline__ void add(double x) {
+    const double t = s + x;
+    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ void add(const CSum &o) {
+    add(o.s);
+    c += o.c;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+// Warp-wide compensated sum (fixed shuffle tree); lane 0 holds the total.
+__device__ __forceinline__ CSum warp_csum(CSum v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    CSum w{__shfl_down_sync(0xffffffffu, v.s, o), __shfl_down_sync(0xffffffffu, v.c, o)};
+    v.add(w);
+  }
+  return v;
+}
+
 // Minimum-image component (box edge L > 0; round half to even like rint).
 __device__ __forceinline__ double mic(double d, double L, double invL) {
   return d - L * rint(d * invL);

@@ -7,19 +7,14 @@
 //                                          ring's spring energy)
 // and, as bead j = k, r^j . F^j and (r^j - r_c) . F^j (r_c = bead average).
 // Per-mode sums over the tile's atoms are taken in a fixed order in shared
-// memory; scalars go through warp shuffles.  One row of partials per block.
+// memory, the scalars through a fixed shuffle tree, all compensated (CSum).
+// One row of partials per block.
 // Pass 2 (k_est_final): one block sums the rows in block order with
 // Neumaier compensation, adds the per-bead U^(k) and Tr Xi^(k) rows of the
 // force kernel and assembles the outputs; a NaN/Inf sets the error word.
 #include "common.cuh"
 
 namespace pimd {
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
 
 __global__ void __launch_bounds__(256) k_est_f64(EstArgs a) {
   extern __shared__ double sm[];
@@ -31,7 +26,7 @@ __global__ void __launch_bounds__(256) k_est_f64(EstArgs a) {
   double *sK = sF + tileLen;          // [A*P]
   double *sS = sK + a.A * P;          // [A*P]
   double *sC = sS + a.A * P;          // [A*3] centroids
-  __shared__ double sred[3][8];
+  __shared__ CSum sred[3][8];
   const int tile0 = blockIdx.x * a.A;
   const int na = min(a.A, a.N - tile0);
   const int len = na * 3 * P;
@@ -49,7 +44,7 @@ __global__ void __launch_bounds__(256) k_est_f64(EstArgs a) {
     sC[t] = s / P;
   }
   __syncthreads();
-  double rF = 0.0, rcF = 0.0, mv0 = 0.0;
+  CSum rF{0.0, 0.0}, rcF{0.0, 0.0}, mv0{0.0, 0.0};
   const double *__restrict__ Mt = a.mt.Mt;
   for (int task = threadIdx.x; task < a.A * P; task += blockDim.x) {
     const int k = task % P;
@@ -73,7 +68,7 @@ __global__ void __launch_bounds__(256) k_est_f64(EstArgs a) {
       kk = 0.5 * mm * __ldg(a.mt.mu + k) * v2s;   // fictitious mass m^(k)
       if (a.method == 0) {
         ss = 0.5 * mm * a.wn2 * __ldg(a.mt.lam + k) * (q0 * q0 + q1 * q1 + q2 * q2);
-        if (k == 0) mv0 += mm * __ldg(a.mt.mu) * v2s;
+        if (k == 0) mv0.add(mm * __ldg(a.mt.mu) * v2s);
       } else {
         // Cartesian bead form of output 2, and v~^(0) = sum_k v^(k) / sqrt(P)
         const int km = k == 0 ? P - 1 : k - 1, kp = k == P - 1 ? 0 : k + 1;
@@ -91,21 +86,25 @@ __global__ void __launch_bounds__(256) k_est_f64(EstArgs a) {
             for (int j = 0; j < P; ++j) sv += vv[d * P + j];
             w2 += sv * sv;
           }
-          mv0 += mm * __ldg(a.mt.mu) * w2 / P;
+          mv0.add(mm * __ldg(a.mt.mu) * w2 / P);
         }
       }
       // bead j = k
       const double x0 = xx[k], x1 = xx[P + k], x2 = xx[2 * P + k];
       const double f0 = ff[k], f1 = ff[P + k], f2 = ff[2 * P + k];
-      rF += x0 * f0 + x1 * f1 + x2 * f2;
-      rcF += (x0 - sC[al * 3]) * f0 + (x1 - sC[al * 3 + 1]) * f1 + (x2 - sC[al * 3 + 2]) * f2;
+      rF.add(x0 * f0);
+      rF.add(x1 * f1);
+      rF.add(x2 * f2);
+      rcF.add((x0 - sC[al * 3]) * f0);
+      rcF.add((x1 - sC[al * 3 + 1]) * f1);
+      rcF.add((x2 - sC[al * 3 + 2]) * f2);
     }
     sK[task] = kk;
     sS[task] = ss;
   }
-  rF = warp_sum(rF);
-  rcF = warp_sum(rcF);
-  mv0 = warp_sum(mv0);
+  rF = warp_csum(rF);
+  rcF = warp_csum(rcF);
+  mv0 = warp_csum(mv0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
     sred[0][warp] = rF;
@@ -116,19 +115,19 @@ __global__ void __launch_bounds__(256) k_est_f64(EstArgs a) {
   const int W = 2 * P + 4;
   double *out = a.part + (size_t)blockIdx.x * W;
   for (int k = threadIdx.x; k < P; k += blockDim.x) {
-    double sk = 0.0, sss = 0.0;
+    CSum sk{0.0, 0.0}, sss{0.0, 0.0};
     for (int al = 0; al < na; ++al) {
-      sk += sK[al * P + k];
-      sss += sS[al * P + k];
+      sk.add(sK[al * P + k]);
+      sss.add(sS[al * P + k]);
     }
-    out[k] = sk;
-    out[P + k] = sss;
+    out[k] = sk.value();
+    out[P + k] = sss.value();
   }
   if (threadIdx.x < 3) {
     const int nw = (blockDim.x + 31) / 32;
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += sred[threadIdx.x][w];
-    out[2 * P + threadIdx.x] = s;
+    CSum s{0.0, 0.0};
+    for (int w = 0; w < nw; ++w) s.add(sred[threadIdx.x][w]);
+    out[2 * P + threadIdx.x] = s.value();
   }
   if (threadIdx.x == 3) out[2 * P + 3] = 0.0;
 }

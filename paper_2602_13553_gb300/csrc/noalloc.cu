@@ -64,34 +64,6 @@ __global__ void k_nm_tables_static(int P, int normal_masses, double fmass, doubl
   }
 }
 
-// Compensated running sums: (s, c) holds s + c; every addition keeps its
-// rounding error in c (Neumaier's TwoSum variant), so a block's partial sums
-// carry no more than one rounding of the total.
-struct CSum {
-  double s, c;
-  __device__ __forceinline__ void add(double x) {
-    const double t = s + x;
-    c += (fabs(s) >= fabs(x)) ? (s - t) + x : (x - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ void add(const CSum &o) {
-    add(o.s);
-    c += o.c;
-  }
-  __device__ __forceinline__ double value() const { return s + c; }
-};
-
-__device__ __forceinline__ CSum warp_csum(CSum v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    CSum w{0.0, 0.0};
-    w.s = __shfl_down_sync(0xffffffffu, v.s, o);
-    w.c = __shfl_down_sync(0xffffffffu, v.c, o);
-    v.add(w);
-  }
-  return v;
-}
-
 // Pass 1: persistent blocks walk atom tiles (stride gridDim.x); thread task
 // (atom al, mode k) adds 1/2 m^(k) |v~_k|^2 to K^(k) and the ring's spring
 // energy of mode k (normal modes: 1/2 m w_n^2 lambda_k |q~_k|^2 with q~ = M x;

@@ -72,20 +72,47 @@ __global__ void __launch_bounds__(256) k_step_f64(StepArgs a) {
   const int len = na * 3 * P;
   const size_t base = (size_t)tile0 * 3 * P;
   const int H = P >> 1;
-  for (int t = threadIdx.x; t < len; t += blockDim.x) {
-    // folded staging of x and F: the partner bead P - j of bead j
-    const int j = t % P, pj = j == 0 ? 0 : P - j;
-    const size_t g = base + t, gp = g - j + pj;
-    const double xa = a.x[g], fa = a.F[g];
-    double xu = xa, fu = fa;
-    if (pj != j) {
-      const double xb = a.x[gp], fb = a.F[gp];
-      xu = j < pj ? xa + xb : xb - xa;
-      fu = j < pj ? fa + fb : fb - fa;
+  // stage the tile's x, F and v~ once each (16-byte loads where the tile
+  // starts on an even element: it is contiguous in [N][3][P])
+  if ((base & 1) == 0) {
+    const double2 *__restrict__ x2 = reinterpret_cast<const double2 *>(a.x + base);
+    const double2 *__restrict__ f2 = reinterpret_cast<const double2 *>(a.F + base);
+    const double2 *__restrict__ v2 = reinterpret_cast<const double2 *>(a.v + base);
+    for (int t = threadIdx.x; t < (len >> 1); t += blockDim.x) {
+      const double2 xv = x2[t], fv = f2[t], vv = v2[t];
+      sX[2 * t] = xv.x;
+      sX[2 * t + 1] = xv.y;
+      sF[2 * t] = fv.x;
+      sF[2 * t + 1] = fv.y;
+      sV[2 * t] = vv.x;
+      sV[2 * t + 1] = vv.y;
     }
-    sX[t] = xu;
-    sF[t] = fu;
-    sV[t] = a.v[g];
+    if ((len & 1) && threadIdx.x == 0) {
+      sX[len - 1] = a.x[base + len - 1];
+      sF[len - 1] = a.F[base + len - 1];
+      sV[len - 1] = a.v[base + len - 1];
+    }
+  } else {
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+      sX[t] = a.x[base + t];
+      sF[t] = a.F[base + t];
+      sV[t] = a.v[base + t];
+    }
+  }
+  __syncthreads();
+  // fold each staged row in place: (x_j, x_{P-j}) -> (x_j + x_{P-j}, x_j - x_{P-j})
+  // for 0 < j < P - j, one thread per pair
+  {
+    const int hp = (P - 1) >> 1;   // pairs per row
+    for (int t = threadIdx.x; t < na * 3 * hp; t += blockDim.x) {
+      const int r = t / hp, j = t - r * hp + 1;
+      double *xr = sX + r * P, *fr = sF + r * P;
+      const double xa = xr[j], xb = xr[P - j], fa = fr[j], fb = fr[P - j];
+      xr[j] = xa + xb;
+      xr[P - j] = xa - xb;
+      fr[j] = fa + fb;
+      fr[P - j] = fa - fb;
+    }
   }
   const uint64_t step = (uint64_t)(*a.step + a.step_off);
   // Large grids: one Philox draw and Box-Muller per (atom, mode) serve the
