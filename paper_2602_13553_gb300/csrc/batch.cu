@@ -753,6 +753,8 @@ __device__ void bstep_warp(const RepDesc *__restrict__ Rp, int tile, float *__re
   }
   __syncwarp();   // the centroids in sxc are visible to every lane
   // new deviations, and the skin criterion: bead spread of the oxygens
+  // (water-like systems, which carry reference centroids)
+  const bool water = Rp->cref != nullptr;
   float *__restrict__ dg = Rp->d + base;
   float vdev = 0.f;
 #pragma unroll
@@ -764,10 +766,12 @@ __device__ void bstep_warp(const RepDesc *__restrict__ Rp, int tile, float *__re
       if (bead < P && a < na) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) __stcs(dg + (a * 3 + c) * P + bead, D[bt][c][q]);
-        if ((tile0 + a) % 3 == 0) {
-          float *po = Rp->pO + (size_t)(tile0 + a) * P + bead;   // molecule (tile0 + a) / 3, row 3 m + c
+        if (water && (tile0 + a) % 3 == 0) {
+          if (Rp->pO) {
+            float *po = Rp->pO + (size_t)(tile0 + a) * P + bead;   // molecule (tile0 + a) / 3, row 3 m + c
 #pragma unroll
-          for (int c = 0; c < 3; ++c) po[c * P] = sf0[a * 3 + c] + D[bt][c][q];
+            for (int c = 0; c < 3; ++c) po[c * P] = sf0[a * 3 + c] + D[bt][c][q];
+          }
           const float s2 = D[bt][0][q] * D[bt][0][q] + D[bt][1][q] * D[bt][1][q] + D[bt][2][q] * D[bt][2][q];
           vdev = fmaxf(vdev, s2 == s2 ? s2 : __int_as_float(0x7f800000));   // NaN forces a rebuild
         }
@@ -775,7 +779,7 @@ __device__ void bstep_warp(const RepDesc *__restrict__ Rp, int tile, float *__re
     }
   // centroid drift of the oxygens since the last rebuild
   float vdisp = 0.f;
-  if (lane < na && (tile0 + lane) % 3 == 0) {
+  if (water && lane < na && (tile0 + lane) % 3 == 0) {
     const int m = (tile0 + lane) / 3;
     double s2 = 0.0;
 #pragma unroll
@@ -792,7 +796,7 @@ __device__ void bstep_warp(const RepDesc *__restrict__ Rp, int tile, float *__re
     vdisp = fmaxf(vdisp, __shfl_xor_sync(0xffffffffu, vdisp, o));
     vdev = fmaxf(vdev, __shfl_xor_sync(0xffffffffu, vdev, o));
   }
-  if (lane < 2) skin_max(Rp->ctl, lane, lane == 0 ? vdisp : vdev);
+  if (water && lane < 2) skin_max(Rp->ctl, lane, lane == 0 ? vdisp : vdev);
   __syncwarp();   // the slot is free for the next item
 }
 
@@ -824,6 +828,49 @@ __global__ void __launch_bounds__(kWWarps * 32, 3) k_bstep_w(const RepDesc *__re
       case 32: bstep_warp<32>(Rp, w.y, slot, step, first); break;
       case 64: bstep_warp<64>(Rp, w.y, slot, step, first); break;
       default: break;
+    }
+  }
+}
+
+// The warp-item step of one system (a single-system handle in split
+// precision, bead counts 8, 16, 32, 64): the same per-item arithmetic as
+// k_bstep_w, with the step index read from the handle's counter.  Warps take
+// the 8-atom tiles in turn.  For water-like systems the last warp to finish
+// turns the step's skin maxima (squared FP32 bit patterns in ctl) into the
+// one conservative (drift, spread) pair that the neighbour-list check reads,
+// and clears them for the next step (threadfence-and-count, no waiting).
+__global__ void __launch_bounds__(kWWarps * 32, 3) k_sstep_w(const RepDesc *__restrict__ Rp,
+                                                            const int64_t *__restrict__ stepp, int step_off,
+                                                            int first, int slot_floats, double *blkmax,
+                                                            unsigned *done) {
+  extern __shared__ __align__(16) float wsm[];
+  float *slot = wsm + (threadIdx.x >> 5) * slot_floats;
+  const int lane = threadIdx.x & 31;
+  const int ntiles = (Rp->N + kWAtoms - 1) / kWAtoms;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const uint64_t step = (uint64_t)(*stepp + step_off);
+  for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += nw) {
+    switch (Rp->P) {
+      case 8: bstep_warp<8>(Rp, tile, slot, step, first); break;
+      case 16: bstep_warp<16>(Rp, tile, slot, step, first); break;
+      case 32: bstep_warp<32>(Rp, tile, slot, step, first); break;
+      case 64: bstep_warp<64>(Rp, tile, slot, step, first); break;
+      default: break;
+    }
+  }
+  if (!blkmax) return;
+  __threadfence();
+  if (lane == 0) {
+    const unsigned t = atomicAdd(done, 1u);
+    if (t == (unsigned)nw - 1) {
+      __threadfence();
+      const unsigned *w = reinterpret_cast<const unsigned *>(Rp->ctl + kCtlSkin);
+      const float d2 = __uint_as_float(atomicOr(const_cast<unsigned *>(w), 0u));
+      const float s2 = __uint_as_float(atomicOr(const_cast<unsigned *>(w) + 1, 0u));
+      blkmax[0] = d2 <= 3.0e38f ? sqrt((double)d2) * (1.0 + 1e-6) : 1e300;
+      blkmax[1] = s2 <= 3.0e38f ? sqrt((double)s2) * (1.0 + 1e-6) : 1e300;
+      atomicExch(reinterpret_cast<unsigned long long *>(Rp->ctl + kCtlSkin), 0ull);
+      atomicExch(done, 0u);
     }
   }
 }
@@ -2138,6 +2185,131 @@ SplitStepArgs replica_split_args(const Replica &r) {
 
 }  // namespace hostside
 using namespace hostside;
+
+namespace pimd {
+
+// ---- the warp-item step for a single-system handle (split precision) ------
+size_t split_warp_desc_bytes() { return sizeof(RepDesc); }
+size_t split_warp_frag_float4(int P) { return 4 * (size_t)((P + 15) / 16) * (P / 8) * 32; }
+bool split_warp_class(int P) { return warp_class(P); }
+
+// Fill a descriptor for the handle's own arrays and upload it with the FP32
+// per-atom constants and the TF32 fragment tables of M and M^T into the
+// device buffers the handle carved for them.
+namespace {
+int g_sw_nsm = 0;   // SM count of the device, read at set-up (one GPU per process)
+
+cudaError_t split_warp_prepare() {
+  if (g_sw_nsm) return cudaSuccess;
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void *)k_sstep_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float)));
+  if (e == cudaSuccess) g_sw_nsm = nsm > 0 ? nsm : 152;
+  return e;
+}
+}  // namespace
+
+cudaError_t split_warp_setup(const SplitWarpSetup &w, cudaStream_t st) {
+  const cudaError_t pe = split_warp_prepare();   // outside any stream capture
+  if (pe != cudaSuccess) return pe;
+  const int N = w.N, P = w.P;
+  RepDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.live = 1;
+  d.N = N;
+  d.P = P;
+  d.nmol = w.cref ? N / 3 : 0;
+  d.integrator = w.integrator;
+  d.thermo = w.thermo;
+  d.seed = w.seed;
+  d.dt = w.dt;
+  d.tA = w.tA;
+  d.dr0 = w.tA / std::sqrt((double)P);
+  d.c1_0 = w.c1_0;
+  d.c2_0 = w.c2_0;
+  for (int c = 0; c < 3; ++c) {
+    d.box[c] = w.box[c];
+    d.invbox[c] = w.box[c] > 0 ? 1.0 / w.box[c] : 0.0;
+  }
+  d.ctl = w.ctl;
+  d.xc = w.xc;
+  d.v0 = w.v0;
+  d.d = w.d;
+  d.vk = w.vk;
+  d.F = w.F;
+  d.xcw = w.xcw;
+  d.pO = nullptr;
+  d.inv_mm = w.inv_mm;
+  d.sigv = w.sigv;
+  d.inv_mmf = w.inv_mmf;
+  d.sigvf = w.sigvf;
+  d.cAf = w.cAf;
+  d.sAf = w.sAf;
+  d.wsAf = w.wsAf;
+  d.c1f = w.c1f;
+  d.c2f = w.c2f;
+  d.cref = w.cref;
+  d.ccur = w.ccur;
+  const size_t one = split_warp_frag_float4(P) / 4;
+  d.mfa_hi = w.frag;
+  d.mfa_lo = w.frag + one;
+  d.mia_hi = w.frag + 2 * one;
+  d.mia_lo = w.frag + 3 * one;
+  std::vector<double> Mt((size_t)P * P);
+  std::vector<double> M(w.M_host, w.M_host + (size_t)P * P);
+  for (int k = 0; k < P; ++k)
+    for (int j = 0; j < P; ++j) Mt[(size_t)j * P + k] = M[(size_t)k * P + j];
+  std::vector<float> fh, fl, ih, il;
+  fragment_tables(M, P, fh, fl);
+  fragment_tables(Mt, P, ih, il);
+  std::vector<float> imf(N), sgf(N);
+  for (int i = 0; i < N; ++i) {
+    imf[i] = (float)w.inv_mm_host[i];
+    sgf[i] = (float)w.sigv_host[i];
+  }
+  long long ctl[kCtlWords] = {0};
+  const struct {
+    void *dst;
+    const void *src;
+    size_t bytes;
+  } ups[] = {
+      {w.desc, &d, sizeof(RepDesc)},
+      {w.frag, fh.data(), one * sizeof(float4)},
+      {w.frag + one, fl.data(), one * sizeof(float4)},
+      {w.frag + 2 * one, ih.data(), one * sizeof(float4)},
+      {w.frag + 3 * one, il.data(), one * sizeof(float4)},
+      {w.inv_mmf, imf.data(), N * sizeof(float)},
+      {w.sigvf, sgf.data(), N * sizeof(float)},
+      {w.ctl, ctl, sizeof(ctl)},
+  };
+  for (const auto &u : ups) {
+    // pageable sources: the copy completes before the call returns
+    const cudaError_t e = cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaError_t e = cudaMemsetAsync(w.done, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);
+}
+
+cudaError_t launch_step_split_warp(const void *desc, int N, const int64_t *step, int step_off, int first,
+                                   double *blkmax, unsigned *done, cudaStream_t s) {
+  const cudaError_t pe = split_warp_prepare();
+  if (pe != cudaSuccess) return pe;
+  const int nsm = g_sw_nsm;
+  const int smem = (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float));
+  const int ntiles = (N + kWAtoms - 1) / kWAtoms;
+  const int warps = std::min(ntiles, nsm * 3 * kWWarps);
+  const int grid = std::max(1, (warps + kWWarps - 1) / kWWarps);
+  k_sstep_w<<<grid, kWWarps * 32, smem, s>>>(reinterpret_cast<const RepDesc *>(desc), step, step_off, first,
+                                            wslot_floats(kWMaxP), blkmax, done);
+  return cudaGetLastError();
+}
+
+}  // namespace pimd
 
 size_t batch_replica_bytes(int N, int P) {
   Replica r;

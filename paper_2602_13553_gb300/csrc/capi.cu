@@ -165,6 +165,14 @@ struct pimd_handle {
   float *Tff = nullptr, *Tif = nullptr;   // split: FP32 folded transforms
   float *c1f = nullptr, *c2f = nullptr;
   double tA = 0.0, c1_0 = 0.0, c2_0 = 0.0;
+  // split precision with 8, 16, 32 or 64 beads: the warp-item step kernel
+  // (tensor-core transforms) and its descriptor, tables and control words
+  bool split_warp = false;
+  char *sw_desc = nullptr;
+  float4 *sw_frag = nullptr;
+  float *sw_imf = nullptr, *sw_sgf = nullptr;
+  long long *sw_ctl = nullptr;
+  unsigned *sw_done = nullptr;
   double *inv_mm = nullptr, *sigv = nullptr, *mass_mm = nullptr, *kspring = nullptr;
   double *M = nullptr, *Mt = nullptr, *cA = nullptr, *sA = nullptr, *wsA = nullptr;
   double *c1 = nullptr, *c2 = nullptr, *lam = nullptr, *mu = nullptr, *imu = nullptr;
@@ -364,7 +372,8 @@ static ForceArgs force_args(pimd_handle *h) {
   a.nbr_groups = h->nbr_groups;
   a.check_nbr = 0;
   a.blkmax = h->blkmax;
-  a.nblk_check = (h->N + h->A_step - 1) / h->A_step;
+  // the warp-item split step reports one (drift, spread) pair for the system
+  a.nblk_check = h->split_warp ? 1 : (h->N + h->A_step - 1) / h->A_step;
   a.skin = h->skin;
   a.rlist = h->rlist;
   a.ccur = h->ccur;
@@ -380,7 +389,8 @@ static NbrArgs nbr_args(pimd_handle *h, bool force) {
   a.x = h->x;
   a.cref = h->cref;
   a.blkmax = h->blkmax;
-  a.nblk_check = (h->N + h->A_step - 1) / h->A_step;
+  // the warp-item split step reports one (drift, spread) pair for the system
+  a.nblk_check = h->split_warp ? 1 : (h->N + h->A_step - 1) / h->A_step;
   a.nbr = h->nbr;
   a.nbr_off = h->nbr_off;
   a.nbr_groups = h->nbr_groups;
@@ -568,11 +578,19 @@ static pimd_status enqueue_baro(pimd_handle *h, double t0, double tB, bool step_
 // positions, and the step counter.
 static pimd_status enqueue_step(pimd_handle *h, bool first) {
   if (h->precision == PIMD_PREC_SPLIT) {
-    SplitStepArgs a = split_args(h);
-    a.first = first ? 1 : 0;
-    a.kick = first ? 0.5 * h->dt : h->dt;
-    pimd_status st =
-        enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step_split(a, h->threads_step, h->stream); });
+    pimd_status st;
+    if (h->split_warp) {
+      const bool water = h->potential == PIMD_POT_WATERLIKE;
+      st = enqueue(h, PIMD_KIND_STEP, 1, [&] {
+        return launch_step_split_warp(h->sw_desc, h->N, h->d_step, 0, first ? 1 : 0, water ? h->blkmax : nullptr,
+                                      h->sw_done, h->stream);
+      });
+    } else {
+      SplitStepArgs a = split_args(h);
+      a.first = first ? 1 : 0;
+      a.kick = first ? 0.5 * h->dt : h->dt;
+      st = enqueue(h, PIMD_KIND_STEP, 1, [&] { return launch_step_split(a, h->threads_step, h->stream); });
+    }
     if (st != PIMD_OK) return st;
     return enqueue_forces(h, false, true);
   }
@@ -770,6 +788,14 @@ static void carve(pimd_handle *h, Carver &c) {
     h->wsAf = c.take<float>(P);
     h->c1f = c.take<float>(P);
     h->c2f = c.take<float>(P);
+    if (h->split_warp) {
+      h->sw_desc = c.take<char>(split_warp_desc_bytes());
+      h->sw_frag = c.take<float4>(split_warp_frag_float4(P));
+      h->sw_imf = c.take<float>(N);
+      h->sw_sgf = c.take<float>(N);
+      h->sw_ctl = c.take<long long>(8);
+      h->sw_done = c.take<unsigned>(1);
+    }
   }
 }
 
@@ -973,6 +999,7 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
   }
   h->A_step = tile_atoms(N, P);
   h->threads_step = tile_threads(h->A_step, P);
+  h->split_warp = prm.precision == PIMD_PREC_SPLIT && split_warp_class(P);
   h->A_est = std::max(1, 256 / P);
   h->threads_est = est_threads(h->A_est, P);
   const char *ng = getenv("PIMD_NO_GRAPH");
@@ -1039,6 +1066,49 @@ extern "C" pimd_status pimd_create(const pimd_system *sys, int32_t P, double T, 
     h->tA = tA;
     h->c1_0 = c1v[0];
     h->c2_0 = c2v[0];
+    if (h->split_warp) {
+      SplitWarpSetup w{};
+      w.N = N;
+      w.P = P;
+      w.integrator = h->integrator;
+      w.thermo = h->thermostat == PIMD_THERMO_PILE_L;
+      w.seed = h->seed;
+      w.dt = h->dt;
+      w.tA = tA;
+      w.c1_0 = c1v[0];
+      w.c2_0 = c2v[0];
+      for (int c = 0; c < 3; ++c) w.box[c] = h->potential == PIMD_POT_WATERLIKE ? h->box[c] : 0.0;
+      w.xc = h->xc;
+      w.v0 = h->v0;
+      w.d = h->dev;
+      w.vk = h->vk;
+      w.F = h->F32;
+      w.xcw = h->xcw;
+      w.inv_mm = h->inv_mm;
+      w.sigv = h->sigv;
+      w.cAf = h->cAf;
+      w.sAf = h->sAf;
+      w.wsAf = h->wsAf;
+      w.c1f = h->c1f;
+      w.c2f = h->c2f;
+      const bool water = h->potential == PIMD_POT_WATERLIKE;
+      w.cref = water ? h->cref : nullptr;
+      w.ccur = water ? h->ccur : nullptr;
+      w.M_host = M.data();
+      w.inv_mm_host = inv_mm.data();
+      w.sigv_host = sigv.data();
+      w.desc = h->sw_desc;
+      w.frag = h->sw_frag;
+      w.inv_mmf = h->sw_imf;
+      w.sigvf = h->sw_sgf;
+      w.ctl = h->sw_ctl;
+      w.done = h->sw_done;
+      const cudaError_t e = split_warp_setup(w, h->stream);
+      if (e != cudaSuccess) {
+        release(h);
+        return fail(PIMD_ECUDA, "split step set-up failed: %s", cudaGetErrorString(e));
+      }
+    }
   }
   auto init = [&]() -> pimd_status {
     CK(cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));

@@ -17,8 +17,14 @@ constexpr double kPi = 3.14159265358979323846;
 
 constexpr int kMaxBeads = 128;
 constexpr int kMaxNeighbours = 192;     // per molecule, O-O list with skin
-constexpr int kLJWarps = 14;            // warps sharing one molecule's O-O neighbour list
-constexpr int kMaxBuckets = 112;        // kLJWarps * max lane groups (8)
+// The single-system water force kernels run one cluster of kForceBlocks
+// blocks x 4 warps per (molecule, bead chunk): kLJWarps warps share the
+// molecule's O-O neighbour list, one takes the two bonds, one the angle.
+// (Two blocks per cluster -- one block per SM for a 64-molecule box, six
+// list warps -- measured slower: 25.1 against 21.5 us per FP64 launch.)
+constexpr int kForceBlocks = 4;
+constexpr int kLJWarps = 4 * kForceBlocks - 2;   // warps sharing one molecule's O-O neighbour list
+constexpr int kMaxBuckets = kLJWarps * 8;        // kLJWarps * max lane groups (8)
 
 // Bits of the device error word (read back at synchronising calls).
 enum : unsigned { kErrNbrOverflow = 1u, kErrNonFinite = 2u, kErrBoxSmall = 4u };

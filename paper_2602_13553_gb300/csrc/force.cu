@@ -61,28 +61,28 @@ __global__ void __launch_bounds__(256) k_force_harmonic_f64(ForceArgs a) {
   if (a.step_inc && blockIdx.x == 0 && threadIdx.x == 0) *a.step_inc += 1;
 }
 
-// Water-like model, FP64.  A cluster of 4 blocks x 4 warps serves one
-// (molecule m, chunk of Bk = min(P, 32) beads).  Lane = (group u, bead kl):
-// beads of the chunk in adjacent lanes (coalesced gathers of a neighbour's
-// bead row), G = 32 / Bk groups when P < 32.  Warps s = 0..13 split the
-// molecule's O-O neighbour list: warp s, group u owns bucket b = s G + u,
-// the neighbours j with j mod (14 G) = b, in index order -- every lane of a
-// warp runs the same loop (no divergent filtering), and because a pair's
-// bucket depends on j alone, every sum depends only on the set of
-// interacting pairs: a rebuilt list cannot change a bit.  Warp 14 evaluates
-// the two O-H bonds, warp 15 the H-O-H angle.
+// Water-like model, FP64.  A cluster of kForceBlocks (2) blocks x 4 warps
+// serves one (molecule m, chunk of Bk = min(P, 32) beads).  Lane = (group u,
+// bead kl): beads of the chunk in adjacent lanes (coalesced gathers of a
+// neighbour's bead row), G = 32 / Bk groups when P < 32.  Warps s = 0 ..
+// kLJWarps - 1 split the molecule's O-O neighbour list: warp s, group u owns
+// bucket b = s G + u, the neighbours j with j mod (kLJWarps G) = b, in index
+// order -- every lane of a warp runs the same loop (no divergent filtering),
+// and because a pair's bucket depends on j alone, every sum depends only on
+// the set of interacting pairs: a rebuilt list cannot change a bit.  Warp
+// kLJWarps evaluates the two O-H bonds, warp kLJWarps + 1 the H-O-H angle.
 // A neighbour is first tested in FP32 against (rc + 0.05 A)^2 -- a
 // conservative bound, FP32 rounding of a <100 A coordinate being ~1e-5 A --
 // and only survivors are evaluated in FP64 with the exact r < rc test, so the
 // FP64 result is that of an all-FP64 loop; the FP32 image shift is exact for
 // every pair that can be inside rc (their |d| is well below L/2).
-// Reduction: warps and groups in shared memory, then the 4 blocks of the
+// Reduction: warps and groups in shared memory, then the blocks of the
 // cluster through distributed shared memory in rank order -- deterministic,
 // no atomics, no global scratch.
 // kDiag (anisotropic barostat) also accumulates the diagonal of the virial
 // tensor, Xi_aa = sum d_a f_a, into W3part.
 template <bool kDiag>
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f64(ForceArgs a) {
+__global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_force_water_f64(ForceArgs a) {
   constexpr int NC = kDiag ? 14 : 11;   // F (9), U, Tr Xi, then Xi_xx, Xi_yy, Xi_zz
   __shared__ double sacc[NC][128];
   __shared__ double red[NC][32];
@@ -93,7 +93,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
   const int G = a.nbr_groups;
   const int NS = kLJWarps * G;
   const int nchunk = (P + Bk - 1) / Bk;
-  const int cid = blockIdx.x / 4;
+  const int cid = blockIdx.x / kForceBlocks;
   const int m = cid / nchunk, chunk = cid % nchunk;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = rank * 4 + warp;     // 0..kLJWarps-1: LJ buckets; then bonds, angle
@@ -225,7 +225,9 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
           const double cth = fmin(1.0, fmax(-1.0, dot * ir01));
           const double th = acos(cth);
           const double dth = th - a.th0;
-          const double pref = a.kth * dth / sin(th);
+          // sin(acos c) = sqrt(1 - c^2): one square root on the FP64 pipe
+          // in place of a sine (the H-O-H angle stays far from 0 and pi)
+          const double pref = a.kth * dth / sqrt(fma(-cth, cth, 1.0));
           double w = 0.0;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -327,7 +329,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_f
       const int k2 = chunk * Bk + kk;
       if (k2 >= P) continue;
       double sum = 0.0;
-      for (int r = 0; r < 4; ++r) sum += cluster.map_shared_rank(&red[0][0], r)[comp * 32 + kk];
+      for (int r = 0; r < kForceBlocks; ++r) sum += cluster.map_shared_rank(&red[0][0], r)[comp * 32 + kk];
       if (comp < 9)
         a.F[(size_t)(3 * m + comp / 3) * 3 * P + (comp % 3) * P + k2] = sum;
       else if (comp == 9)
@@ -456,7 +458,7 @@ int force_blocks(int n_groups, int P) {
 
 int water_force_blocks(int nmol, int P) {
   const int Bk = P < 32 ? P : 32;
-  return 4 * nmol * ((P + Bk - 1) / Bk);
+  return kForceBlocks * nmol * ((P + Bk - 1) / Bk);
 }
 
 // lane groups per warp of the water force kernel: the largest power of two

@@ -370,12 +370,13 @@ __global__ void __launch_bounds__(256) k_force_harmonic_split(SplitForceArgs a) 
 __device__ __forceinline__ float micf(float d, float L, float invL) { return fmaf(-rintf(d * invL), L, d); }
 
 // Water-like model in FP32, same decomposition as the FP64 kernel: a
-// 4-block cluster per (molecule, bead chunk), warps 0..13 own buckets of the
-// O-O neighbour list, warp 14 the bonds, warp 15 the angle; partials are
+// kForceBlocks-block cluster per (molecule, bead chunk), warps 0 ..
+// kLJWarps - 1 own buckets of the O-O neighbour list, warp kLJWarps the
+// bonds, warp kLJWarps + 1 the angle; partials are
 // reduced through distributed shared memory in rank order.  A pair vector is
 // the minimum-image difference of the wrapped FP32 centroids plus the
 // difference of the FP32 deviations.
-__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_split(SplitForceArgs a) {
+__global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_force_water_split(SplitForceArgs a) {
   __shared__ float sacc[9][128];
   __shared__ double saccd[2][128];
   __shared__ float red[9][32];
@@ -387,7 +388,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_s
   const int G = a.nbr_groups;
   const int NS = kLJWarps * G;
   const int nchunk = (P + Bk - 1) / Bk;
-  const int cid = blockIdx.x / 4;
+  const int cid = blockIdx.x / kForceBlocks;
   const int m = cid / nchunk, chunk = cid % nchunk;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = rank * 4 + warp;
@@ -518,11 +519,11 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(128) k_force_water_s
       if (k2 >= P) continue;
       if (comp < 9) {
         float sum = 0.f;
-        for (int r = 0; r < 4; ++r) sum += cluster.map_shared_rank(&red[0][0], r)[comp * 32 + kk];
+        for (int r = 0; r < kForceBlocks; ++r) sum += cluster.map_shared_rank(&red[0][0], r)[comp * 32 + kk];
         a.F[(size_t)(3 * m + comp / 3) * 3 * P + (comp % 3) * P + k2] = sum;
       } else {
         double sum = 0.0;
-        for (int r = 0; r < 4; ++r) sum += cluster.map_shared_rank(&redd[0][0], r)[(comp - 9) * 32 + kk];
+        for (int r = 0; r < kForceBlocks; ++r) sum += cluster.map_shared_rank(&redd[0][0], r)[(comp - 9) * 32 + kk];
         if (comp == 9)
           a.Upart[(size_t)m * P + k2] = sum;
         else
