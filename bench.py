@@ -323,6 +323,12 @@ def batched_bench(stream, steps, warmup):
     live = stp >= 0
     rebuild_rate = float(rb[live].sum() / max(1, stp[live].sum()))
     kt = b.time_kernels(10)
+    # the transform A/B: the same replicas on the block-item kernel with FP32
+    # FMA transforms (default tiles), step kernels timed the same way
+    b.set_transforms("ffma")
+    b.run(20)
+    kt_ffma = b.time_kernels(10)
+    b.set_transforms("tensor")
     dom = "step" if kt["step"] >= kt["force"] else "force"
     per_ms = kt[dom] / 10.0
     bytes_ = step_bytes if dom == "step" else force_bytes
@@ -345,6 +351,9 @@ def batched_bench(stream, steps, warmup):
                      "avg_launch_ms": per_ms,
                      "traffic": traffic_for("k_bstep_w" if dom == "step" else "k_bforce"),
                      "kernel_time_share": {k: round(v / tot, 4) for k, v in kt.items()}},
+        "transform_ab": {"tensor_core_step_ms": kt["step"] / 10.0, "ffma_step_ms": kt_ffma["step"] / 10.0,
+                         "basis": "per-MD-step device time of the step kernels over the mix: warp items with "
+                                  "3xTF32 mma.sync transforms against block items with FP32 FMA transforms"},
         "whole_step": {"bound": "hbm", "achieved": md_bytes / (md_ms / 1e3) / 1e9, "peak": peak,
                        "unit": "GB/s", "frac": md_bytes / (md_ms / 1e3) / 1e9 / peak, "peak_source": src,
                        "algorithmic_bytes_per_md_step": md_bytes, "ms_per_md_step": md_ms,

@@ -404,7 +404,18 @@ pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double *x, double 
  * [P] the chosen tile for bead count P (0 = unused). */
 pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t *tiles_out);
 
-/* Kernel accounting: kernels enqueued so far (graph nodes included), and
+/* Normal-mode transforms of the batch's step: PIMD_TRANSFORMS_TENSOR (the
+ * default) runs bead counts 8, 16, 32, 64 and 128 as warp items whose
+ * transforms are 3xTF32 tensor-core products; PIMD_TRANSFORMS_FFMA runs every
+ * replica on the block-item kernel with FP32 fused-multiply-add transforms,
+ * the comparison path for that choice.  Both compute the same split-precision
+ * step (FP32-level transforms); trajectories differ by FP32 rounding.
+ * Waits for queued work; step tiles return to their defaults (run
+ * pimd_batch_autotune again to tune them).  EINVAL for another kind. */
+enum { PIMD_TRANSFORMS_TENSOR = 0, PIMD_TRANSFORMS_FFMA = 1 };
+pimd_status pimd_batch_set_transforms(pimd_batch *b, int32_t kind);
+
+/* Kernel accounting: kernels enqueued so far (graph nodes included), and/* Kernel accounting: kernels enqueued so far (graph nodes included), and
  * nsteps real steps launched one kernel at a time with CUDA events around
  * four groups of the step's kernels: ms[0..3] receive the summed device
  * milliseconds of the control kernel, the fused-step kernels (warp items and,

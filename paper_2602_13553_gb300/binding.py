@@ -107,7 +107,7 @@ EXPORTS = ("pimd_set_allocator", "pimd_params_default", "pimd_status_string", "p
            "pimd_batch_replica_bytes", "pimd_batch_create", "pimd_batch_add", "pimd_batch_remove",
            "pimd_batch_run", "pimd_batch_sync", "pimd_batch_status", "pimd_batch_estimators",
            "pimd_batch_get_state", "pimd_batch_autotune", "pimd_batch_kernel_launches",
-           "pimd_batch_time_kernels",
+           "pimd_batch_time_kernels", "pimd_batch_set_transforms",
            "pimd_batch_destroy", "pimd_server_create", "pimd_batch_submit", "pimd_batch_poll",
            "pimd_batch_cancel", "pimd_server_job_times", "pimd_server_stats_get", "pimd_server_keep_state",
            "pimd_server_get_state", "pimd_server_destroy")
@@ -376,6 +376,7 @@ def _batch_lib():
         "pimd_batch_autotune": ([vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "pimd_batch_kernel_launches": ([vp], ctypes.c_int64),
         "pimd_batch_time_kernels": ([vp, ctypes.c_int32, dp], ctypes.c_int),
+        "pimd_batch_set_transforms": ([vp, ctypes.c_int32], ctypes.c_int),
         "pimd_batch_destroy": ([vp], None),
         "pimd_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.c_int64, vp, ctypes.POINTER(vp)],
                                ctypes.c_int),
@@ -477,6 +478,11 @@ class Batch:
         out = {P: tiles[P] for P in range(1, MAX_BEADS + 1) if tiles[P] > 0}
         out["warp_blocks_per_sm"] = tiles[0]
         return out
+
+    def set_transforms(self, kind: str) -> None:
+        """'tensor' (warp items, 3xTF32 tensor cores) or 'ffma' (block items,
+        FP32 FMA transforms)."""
+        check(_batch_lib().pimd_batch_set_transforms(self._h, {"tensor": 0, "ffma": 1}[kind]))
 
     def kernel_launches(self) -> int:
         return int(_batch_lib().pimd_batch_kernel_launches(self._h))

@@ -77,7 +77,9 @@ __device__ __forceinline__ void skin_max(long long *ctl, int which, float v2) {
 
 struct RepDesc {
   int live, N, P, nmol, A, G, integrator, thermo;
-  int nstep_items, ne, pad0, pad1;
+  int nstep_items, ne;
+  int ffma;                   // 1: block-item step with FP32 FMA transforms (comparison path)
+  int pad1;
   uint64_t seed;
   double dt, tA, c1_0, c2_0, kT, volume, wn2;
   double dr0;                 // tA / sqrt(P): centroid drift per unit v~_0
@@ -120,6 +122,7 @@ __global__ void k_bctl(const RepDesc *reps, int nslots, int mode, int *wnext) {
   if (mode == 0 && r == 0 && wnext) {
     wnext[0] = 0;   // warp-item counter of the step kernel
     wnext[1] = 0;   // length of this step's rebuild list
+    wnext[3] = 0;   // warp-item counter of the 128-bead step kernel
   }
   if (r >= nslots || !reps[r].live) return;
   long long *c = reps[r].ctl;
@@ -832,17 +835,45 @@ __global__ void __launch_bounds__(kWWarps * 32, 3) k_bstep_w(const RepDesc *__re
   }
 }
 
+// Warp items of bead count 128, the range [counts[4], counts[7]) of the step
+// list: the same per-item arithmetic as k_bstep_w in a kernel of its own,
+// whose larger accumulator tiles (eight mode tiles) and 26 KB warp slots
+// would otherwise set the register and shared-memory budget of the smaller
+// bead counts; claimed from the counter *next (reset by k_bctl).
+__global__ void __launch_bounds__(kWWarps * 32, 1) k_bstep_w128(const RepDesc *__restrict__ reps,
+                                                               const int2 *__restrict__ items,
+                                                               const int *__restrict__ counts, int *next) {
+  extern __shared__ __align__(16) float wsm[];
+  float *slot = wsm + (threadIdx.x >> 5) * wslot_floats(128);
+  const int lo = counts[4], hi = counts[7];
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = lo + atomicAdd(next, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= hi) break;
+    const int2 w = items[it];
+    const RepDesc *__restrict__ Rp = reps + w.x;
+    const long long *ctl = Rp->ctl;
+    if (!ctl[kCtlActive] || Rp->P != 128) continue;
+    bstep_warp<128>(Rp, w.y, slot, (uint64_t)ctl[kCtlStep], (int)ctl[kCtlFirst]);
+  }
+}
+
 // The warp-item step of one system (a single-system handle in split
-// precision, bead counts 8, 16, 32, 64): the same per-item arithmetic as
+// precision, bead counts 8, 16, 32, 64, 128): the same per-item arithmetic as
 // k_bstep_w, with the step index read from the handle's counter.  Warps take
 // the 8-atom tiles in turn.  For water-like systems the last warp to finish
 // turns the step's skin maxima (squared FP32 bit patterns in ctl) into the
 // one conservative (drift, spread) pair that the neighbour-list check reads,
 // and clears them for the next step (threadfence-and-count, no waiting).
-__global__ void __launch_bounds__(kWWarps * 32, 3) k_sstep_w(const RepDesc *__restrict__ Rp,
-                                                            const int64_t *__restrict__ stepp, int step_off,
-                                                            int first, int slot_floats, double *blkmax,
-                                                            unsigned *done) {
+// kBig: the 128-bead instance (eight mode tiles, one block per SM's share of
+// registers), as k_bstep_w128 is for the batch.
+template <bool kBig>
+__global__ void __launch_bounds__(kWWarps * 32, kBig ? 1 : 3) k_sstep_w(const RepDesc *__restrict__ Rp,
+                                                                       const int64_t *__restrict__ stepp,
+                                                                       int step_off, int first, int slot_floats,
+                                                                       double *blkmax, unsigned *done) {
   extern __shared__ __align__(16) float wsm[];
   float *slot = wsm + (threadIdx.x >> 5) * slot_floats;
   const int lane = threadIdx.x & 31;
@@ -850,6 +881,10 @@ __global__ void __launch_bounds__(kWWarps * 32, 3) k_sstep_w(const RepDesc *__re
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const uint64_t step = (uint64_t)(*stepp + step_off);
   for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += nw) {
+    if (kBig) {
+      if (Rp->P == 128) bstep_warp<128>(Rp, tile, slot, step, first);
+      continue;
+    }
     switch (Rp->P) {
       case 8: bstep_warp<8>(Rp, tile, slot, step, first); break;
       case 16: bstep_warp<16>(Rp, tile, slot, step, first); break;
@@ -877,7 +912,7 @@ __global__ void __launch_bounds__(kWWarps * 32, 3) k_sstep_w(const RepDesc *__re
 
 // The split-precision fused step (same arithmetic as the single-system split
 // kernel) over the block items (replica, tile) of the bead counts outside the
-// warp-item classes: the suffix [counts[4], counts[0]) of the step list.
+// warp-item classes: the suffix [counts[7], counts[0]) of the step list.
 // Every descriptor field an item
 // needs is read once into registers (restrict-qualified), and the task index
 // split (mode, row) uses shifts when P is a power of two.
@@ -887,12 +922,12 @@ __global__ void __launch_bounds__(128, 4) k_bstep(const RepDesc *__restrict__ re
   float *sD = sbuf, *sV = sbuf + kTileMax, *sF = sbuf + 2 * kTileMax, *sQ = sbuf + 3 * kTileMax;
   __shared__ double sred[2][4];
   const int n = counts[0];
-  for (int it = counts[4] + blockIdx.x; it < n; it += gridDim.x) {
+  for (int it = counts[7] + blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = items[it];
     const RepDesc *__restrict__ Rp = reps + w.x;
     long long *__restrict__ ctl = Rp->ctl;
     if (!ctl[kCtlActive]) continue;
-    if ((Rp->P & 7) == 0) {
+    if ((Rp->P & 7) == 0 && !Rp->ffma) {
       // tensor-core path: tiles with padded rows in sF (forces), sX
       // (deviations), sV (velocities)
       const int P = Rp->P, A = Rp->A, N = Rp->N, PS = P + 4;
@@ -1163,8 +1198,14 @@ __global__ void __launch_bounds__(128) k_bclose(const RepDesc *reps, const int2 
     const RepDesc &R = reps[w.x];
     if (!R.ctl[kCtlClose]) continue;
     const int P = R.P, A = R.A;
-    const int tile0 = w.y * A;
-    const int na = min(A, R.N - tile0);
+    const int item0 = w.y * A;
+    const int nitem = min(A, R.N - item0);
+    // the item's atoms in sub-tiles that fit the shared tile (a 128-bead
+    // warp item spans twice kTileMax)
+    const int sub = max(1, kTileMax / (3 * P));
+    for (int a0 = 0; a0 < nitem; a0 += sub) {
+    const int tile0 = item0 + a0;
+    const int na = min(sub, nitem - a0);
     const int len = na * 3 * P;
     const size_t base = (size_t)tile0 * 3 * P;
     for (int t = threadIdx.x; t < len; t += blockDim.x) sF[t] = R.F[base + t];
@@ -1201,6 +1242,7 @@ __global__ void __launch_bounds__(128) k_bclose(const RepDesc *reps, const int2 
       R.vk[base + task] = v;
     }
     __syncthreads();
+    }
   }
 }
 
@@ -1916,10 +1958,16 @@ struct pimd_batch {
   float4 *mtab[PIMD_MAX_BEADS + 1] = {nullptr};
   std::vector<int2> h_step, h_nbr, h_est;
   std::vector<int4> h_clu;
-  int h_counts[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // [0] step items, [1] force, [2] nbr, [3] est, [4] end of the warp items,
+  // [5] their claim counter, [6] rebuild-list length, [7] end of the
+  // 128-bead warp items, [8] their claim counter
+  int h_counts[16] = {0};
   int wslot = 0;          // floats of shared memory per warp of the warp-item step kernel
   int grid_w = 0;         // its blocks (persistent grid)
+  int grid_w128 = 0;      // blocks of the 128-bead warp-item kernel
   bool block_items = true;   // some replica has a bead count outside the warp-item classes
+  bool w128_items = false;   // some replica has 128 beads
+  bool ffma = false;         // every step on the block-item kernel with FP32 FMA transforms
   int wblocks_sm = 0;     // blocks per SM in use
   int wtuned = 0;         // blocks per SM chosen by the autotuner (0: the occupancy limit)
   int nsm = 152;
@@ -1952,7 +2000,11 @@ pimd_status grow(pimd_batch *b, T **ptr, size_t *cap, size_t need) {
 }
 
 void replica_items(pimd_batch *b, int slot, Replica &r) {
-  r.A = warp_class(r.P) ? kWAtoms : (b->tileA[r.P] > 0 ? b->tileA[r.P] : default_tile(r.P));
+  if (b->ffma)
+    r.A = b->tileA[r.P] > 0 ? b->tileA[r.P] : std::max(1, 256 / (3 * r.P));
+  else
+    r.A = (warp_class(r.P) || r.P == 128) ? kWAtoms : (b->tileA[r.P] > 0 ? b->tileA[r.P] : default_tile(r.P));
+  r.desc.ffma = b->ffma ? 1 : 0;
   r.ntiles = (r.N + r.A - 1) / r.A;
   r.ne = std::min(r.ntiles, kEstItems);
   r.items_step.clear();
@@ -1989,7 +2041,7 @@ pimd_status upload(pimd_batch *b) {
   // claimed first), then the block items of the other bead counts
   int pmax_w = 0;
   for (int P : {64, 32, 16, 8})
-    for (int s = 0; s < b->capacity; ++s) {
+    for (int s = 0; s < b->capacity && !b->ffma; ++s) {
       Replica &r = b->reps[s];
       if (r.live && r.P == P) {
         b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
@@ -1997,9 +2049,15 @@ pimd_status upload(pimd_batch *b) {
       }
     }
   const int nw = (int)b->h_step.size();
-  for (int s = 0; s < b->capacity; ++s) {
+  for (int s = 0; s < b->capacity && !b->ffma; ++s) {   // then the 128-bead warp items
     Replica &r = b->reps[s];
-    if (r.live && !warp_class(r.P)) b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
+    if (r.live && r.P == 128) b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
+  }
+  const int nw128 = (int)b->h_step.size();
+  for (int s = 0; s < b->capacity; ++s) {   // block items: the other bead counts (all with FFMA transforms)
+    Replica &r = b->reps[s];
+    if (r.live && (b->ffma || (!warp_class(r.P) && r.P != 128)))
+      b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
   }
   for (int s = 0; s < b->capacity; ++s) {
     Replica &r = b->reps[s];
@@ -2026,10 +2084,13 @@ pimd_status upload(pimd_batch *b) {
   b->h_counts[4] = nw;
   b->h_counts[5] = 0;
   b->h_counts[6] = 0;
-  const bool blk = b->h_counts[0] > nw;
-  if (blk != b->block_items) {
+  b->h_counts[7] = nw128;
+  b->h_counts[8] = 0;
+  const bool blk = b->h_counts[0] > nw128, w128 = nw128 > nw;
+  if (blk != b->block_items || w128 != b->w128_items) {
     b->block_items = blk;
-    if (b->graph) {   // the captured step launches k_bstep or not
+    b->w128_items = w128;
+    if (b->graph) {   // the captured step launches k_bstep / k_bstep_w128 or not
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
@@ -2068,6 +2129,9 @@ pimd_status upload(pimd_batch *b) {
 void launch_step_kernels(pimd_batch *b) {
   k_bstep_w<<<b->grid_w, kWWarps * 32, (size_t)kWWarps * b->wslot * sizeof(float), b->stream>>>(
       b->d_reps, b->d_step, b->d_counts, b->d_counts + 5, b->wslot);
+  if (b->w128_items)
+    k_bstep_w128<<<b->grid_w128, kWWarps * 32, (size_t)kWWarps * wslot_floats(128) * sizeof(float), b->stream>>>(
+        b->d_reps, b->d_step, b->d_counts, b->d_counts + 8);
   if (b->block_items) k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts);
 }
 
@@ -2077,9 +2141,10 @@ void launch_nbr_kernels(pimd_batch *b) {
   k_bnbr<<<b->grid_nbr, kNbrThreads, kNbrSmem, b->stream>>>(b->d_reps, b->d_nbr_go, b->d_counts + 6);
 }
 
-// Kernels launched per MD step: control, warp-item step, block-item step
-// (when some replica needs it), rebuild decision, rebuilds, forces.
-int step_launches(const pimd_batch *b) { return b->block_items ? 6 : 5; }
+// Kernels launched per MD step: control, warp-item step, 128-bead warp-item
+// step and block-item step (each when some replica needs it), rebuild
+// decision, rebuilds, forces.
+int step_launches(const pimd_batch *b) { return 5 + (b->block_items ? 1 : 0) + (b->w128_items ? 1 : 0); }
 
 // One MD step of every active replica.
 cudaError_t launch_one_step(pimd_batch *b, cudaEvent_t e0, cudaEvent_t e1) {
@@ -2191,7 +2256,7 @@ namespace pimd {
 // ---- the warp-item step for a single-system handle (split precision) ------
 size_t split_warp_desc_bytes() { return sizeof(RepDesc); }
 size_t split_warp_frag_float4(int P) { return 4 * (size_t)((P + 15) / 16) * (P / 8) * 32; }
-bool split_warp_class(int P) { return warp_class(P); }
+bool split_warp_class(int P) { return warp_class(P) || P == 128; }
 
 // Fill a descriptor for the handle's own arrays and upload it with the FP32
 // per-atom constants and the TF32 fragment tables of M and M^T into the
@@ -2205,8 +2270,11 @@ cudaError_t split_warp_prepare() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void *)k_sstep_w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute((const void *)k_sstep_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void *)k_sstep_w<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kWWarps * wslot_floats(128) * sizeof(float)));
   if (e == cudaSuccess) g_sw_nsm = nsm > 0 ? nsm : 152;
   return e;
 }
@@ -2295,17 +2363,23 @@ cudaError_t split_warp_setup(const SplitWarpSetup &w, cudaStream_t st) {
   return cudaStreamSynchronize(st);
 }
 
-cudaError_t launch_step_split_warp(const void *desc, int N, const int64_t *step, int step_off, int first,
+cudaError_t launch_step_split_warp(const void *desc, int N, int P, const int64_t *step, int step_off, int first,
                                    double *blkmax, unsigned *done, cudaStream_t s) {
   const cudaError_t pe = split_warp_prepare();
   if (pe != cudaSuccess) return pe;
   const int nsm = g_sw_nsm;
-  const int smem = (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float));
+  const bool big = P == 128;
+  const int slot = big ? wslot_floats(128) : wslot_floats(kWMaxP);
+  const int smem = (int)(kWWarps * slot * sizeof(float));
   const int ntiles = (N + kWAtoms - 1) / kWAtoms;
-  const int warps = std::min(ntiles, nsm * 3 * kWWarps);
+  const int warps = std::min(ntiles, nsm * (big ? 2 : 3) * kWWarps);
   const int grid = std::max(1, (warps + kWWarps - 1) / kWWarps);
-  k_sstep_w<<<grid, kWWarps * 32, smem, s>>>(reinterpret_cast<const RepDesc *>(desc), step, step_off, first,
-                                            wslot_floats(kWMaxP), blkmax, done);
+  if (big)
+    k_sstep_w<true><<<grid, kWWarps * 32, smem, s>>>(reinterpret_cast<const RepDesc *>(desc), step, step_off, first,
+                                                     slot, blkmax, done);
+  else
+    k_sstep_w<false><<<grid, kWWarps * 32, smem, s>>>(reinterpret_cast<const RepDesc *>(desc), step, step_off,
+                                                      first, slot, blkmax, done);
   return cudaGetLastError();
 }
 
@@ -2353,11 +2427,14 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
     return fail(PIMD_ECUDA, "cannot enable %zu bytes of shared memory for the neighbour kernel", kNbrSmem);
   }
   const int wsmem = (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float));
+  const int wsmem128 = (int)(kWWarps * wslot_floats(128) * sizeof(float));
   if (cudaFuncSetAttribute((const void *)k_bstep_w, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaFuncSetAttribute((const void *)k_bstep_w128, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem128) !=
+          cudaSuccess) {
     cudaGetLastError();
     pimd_batch_destroy(b);
-    return fail(PIMD_ECUDA, "cannot enable %d bytes of shared memory for the step kernel", wsmem);
+    return fail(PIMD_ECUDA, "cannot enable %d bytes of shared memory for the step kernels", wsmem128);
   }
   b->nsm = nsm;
   // persistent grids: every SM filled to the kernel's occupancy limit
@@ -2367,6 +2444,7 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
     return nsm * n;
   };
   b->grid_step = occ((const void *)k_bstep);
+  b->grid_w128 = occ((const void *)k_bstep_w128, (size_t)kWWarps * wslot_floats(128) * sizeof(float));
   b->grid_clu = occ((const void *)k_bforce);
   b->grid_nbr = occ((const void *)k_bnbr, kNbrSmem, kNbrThreads);
   b->grid_est = 8 * nsm;
@@ -2375,7 +2453,7 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
     return st;
   };
   b->d_reps = (RepDesc *)dev_alloc(b->alloc, sizeof(RepDesc) * max_replicas, b->stream);
-  b->d_counts = (int *)dev_alloc(b->alloc, 8 * sizeof(int), b->stream);
+  b->d_counts = (int *)dev_alloc(b->alloc, sizeof(b->h_counts), b->stream);
   b->d_eout = (double *)dev_alloc(b->alloc, sizeof(double) * kOutStride * max_replicas, b->stream);
   b->d_ctl = (long long *)dev_alloc(b->alloc, sizeof(long long) * kCtlWords * max_replicas, b->stream);
   if (!b->d_reps || !b->d_counts || !b->d_eout || !b->d_ctl)
@@ -2776,6 +2854,21 @@ extern "C" pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double 
   return PIMD_OK;
 }
 
+extern "C" pimd_status pimd_batch_set_transforms(pimd_batch *b, int32_t kind) {
+  if (!b || (kind != PIMD_TRANSFORMS_TENSOR && kind != PIMD_TRANSFORMS_FFMA))
+    return fail(PIMD_EINVAL, "pimd_batch_set_transforms: unknown kind");
+  pimd_status st = pimd_batch_sync(b);
+  if (st != PIMD_OK) return st;
+  const bool f = kind == PIMD_TRANSFORMS_FFMA;
+  if (f == b->ffma) return PIMD_OK;
+  b->ffma = f;
+  for (int P = 0; P <= PIMD_MAX_BEADS; ++P) b->tileA[P] = 0;   // the tiles of the other path no longer apply
+  for (int s = 0; s < b->capacity; ++s)
+    if (b->reps[s].live) replica_items(b, s, b->reps[s]);
+  b->dirty = true;
+  return PIMD_OK;
+}
+
 extern "C" int64_t pimd_batch_kernel_launches(const pimd_batch *b) { return b ? b->launches : -1; }
 
 // nsteps steps launched one kernel at a time with CUDA events around each of
@@ -2844,7 +2937,7 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
     return PIMD_OK;
   };
   pimd_status st = PIMD_OK;
-  if (std::any_of(classes.begin(), classes.end(), [](int P) { return warp_class(P); })) {
+  if (!b->ffma && std::any_of(classes.begin(), classes.end(), [](int P) { return warp_class(P); })) {
     if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
     int nbmax = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbmax, (const void *)k_bstep_w, kWWarps * 32,
@@ -2876,11 +2969,11 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
   }
   for (int P : classes) {
     if (st != PIMD_OK) break;
-    if (warp_class(P)) {
+    if (!b->ffma && (warp_class(P) || P == 128)) {   // warp items: fixed 8-atom tiles
       b->tileA[P] = kWAtoms;
       continue;
     }
-    const int amax = default_tile(P);
+    const int amax = b->ffma ? std::max(1, 256 / (3 * P)) : default_tile(P);
     int best = amax;
     float best_ms = 1e30f;
     for (int A = amax; A >= 1; A = (A == 1) ? 0 : std::max(1, A / 2)) {

@@ -165,7 +165,7 @@ struct pimd_handle {
   float *Tff = nullptr, *Tif = nullptr;   // split: FP32 folded transforms
   float *c1f = nullptr, *c2f = nullptr;
   double tA = 0.0, c1_0 = 0.0, c2_0 = 0.0;
-  // split precision with 8, 16, 32 or 64 beads: the warp-item step kernel
+  // split precision with 8, 16, 32, 64 or 128 beads: the warp-item step kernel
   // (tensor-core transforms) and its descriptor, tables and control words
   bool split_warp = false;
   char *sw_desc = nullptr;
@@ -582,8 +582,8 @@ static pimd_status enqueue_step(pimd_handle *h, bool first) {
     if (h->split_warp) {
       const bool water = h->potential == PIMD_POT_WATERLIKE;
       st = enqueue(h, PIMD_KIND_STEP, 1, [&] {
-        return launch_step_split_warp(h->sw_desc, h->N, h->d_step, 0, first ? 1 : 0, water ? h->blkmax : nullptr,
-                                      h->sw_done, h->stream);
+        return launch_step_split_warp(h->sw_desc, h->N, h->P, h->d_step, 0, first ? 1 : 0,
+                                      water ? h->blkmax : nullptr, h->sw_done, h->stream);
       });
     } else {
       SplitStepArgs a = split_args(h);

@@ -44,7 +44,7 @@ void *dev_alloc(const DevAllocator &a, size_t bytes, cudaStream_t s);
 void dev_free(const DevAllocator &a, void *p, cudaStream_t s);
 
 // The warp-item split-precision step for a single-system handle (bead
-// counts 8, 16, 32, 64): the handle's device arrays and the device buffers
+// counts 8, 16, 32, 64, 128): the handle's device arrays and the device buffers
 // it carved for the step's descriptor, FP32 constants, TF32 fragment tables
 // (split_warp_frag_float4 float4s), control words and completion counter.
 struct SplitWarpSetup {
@@ -67,7 +67,7 @@ size_t split_warp_desc_bytes();
 size_t split_warp_frag_float4(int P);
 bool split_warp_class(int P);
 cudaError_t split_warp_setup(const SplitWarpSetup &w, cudaStream_t st);
-cudaError_t launch_step_split_warp(const void *desc, int N, const int64_t *step, int step_off, int first,
+cudaError_t launch_step_split_warp(const void *desc, int N, int P, const int64_t *step, int step_off, int first,
                                    double *blkmax, unsigned *done, cudaStream_t s);
 
 pimd_status fail(pimd_status s, const char *fmt, ...);

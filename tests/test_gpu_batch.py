@@ -179,3 +179,51 @@ def test_batch_keywords_agree_with_oracle(orc, pimd, kw):
     assert st == 30
     assert_split_close(x, v, b.estimators()[s], c, c.estimators(), str(kw))
     b.close()
+
+
+@pytest.mark.parametrize("integ", [0, 1])
+def test_batch_128_beads_agree_with_oracle(orc, pimd, integ):
+    """128-bead replicas (their own warp-item kernel, eight mode tiles) beside
+    a 32-bead one and a 100-bead block-item one, BAOAB and OBABO, against the
+    oracle; the 128-bead replica is bitwise the same alone."""
+    b = pimd.Batch(4)
+    reps = [rep(24, 128, 21, 280.0), rep(40, 32, 22), rep(20, 100, 23, 150.0, True), rep(33, 128, 24, 330.0, True)]
+    slots = [add(b, r, 30, integrator=integ) for r in reps]
+    b.run(18)
+    b.run(12)
+    est = b.estimators()
+    for s, r in zip(slots, reps):
+        c = orc.Sim(r["x0"], r["mass"], T=r["T"], dt=r["dt"], potential=1, ff=r["ff"], box=r["box"],
+                    seed=r["seed"], integrator=integ)
+        c.run(30)
+        x, v, st = b.get_state(s)
+        assert st == 30
+        assert_split_close(x, v, est[s], c, c.estimators(), "P = %d" % r["x0"].shape[0])
+    solo = pimd.Batch(1)
+    t = add(solo, reps[0], 30, integrator=integ)
+    solo.run(18)
+    solo.run(12)
+    xs, vs, _ = solo.get_state(t)
+    xb, vb, _ = b.get_state(slots[0])
+    assert np.array_equal(xs, xb) and np.array_equal(vs, vb)
+    b.close()
+
+
+def test_batch_ffma_transforms_agree_with_oracle(orc, pimd):
+    """The comparison path of the transforms (every replica on the block-item
+    kernel with FP32 FMA transforms) computes the same split-precision step:
+    against the oracle at the split bars, bead counts 8, 32, 64 and 128."""
+    b = pimd.Batch(4)
+    b.set_transforms("ffma")
+    reps = [MIX[0], MIX[2], MIX[3], rep(20, 128, 25)]
+    slots = [add(b, r, 30) for r in reps]
+    b.run(30)
+    est = b.estimators()
+    for s, r in zip(slots, reps):
+        c = orc.Sim(r["x0"], r["mass"], T=r["T"], dt=r["dt"], potential=1, ff=r["ff"], box=r["box"],
+                    seed=r["seed"])
+        c.run(30)
+        x, v, st = b.get_state(s)
+        assert st == 30
+        assert_split_close(x, v, est[s], c, c.estimators(), "FFMA P = %d" % r["x0"].shape[0])
+    b.close()
