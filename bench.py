@@ -54,8 +54,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=20)
-    ap.add_argument("--serve-jobs", type=int, default=200)
-    ap.add_argument("--serve-step-scale", type=float, default=0.1)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-step-scale", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -365,18 +365,19 @@ def batched_bench(stream, steps, warmup):
 def serve_bench(stream, n_jobs, step_scale):
     """The serving workload: a Poisson stream of water-like jobs at 50 jobs/s
     (96-12288 atoms, P 4-128, 1k-50k steps, all log-uniform) against a 150 GB
-    budget; the first n_jobs of the trace, step counts scaled by step_scale."""
+    budget; the first n_jobs of the trace (by default all 2000), step counts
+    scaled by step_scale (by default 1)."""
     from paper_2602_13553_gb300 import binding, inputs
     trace = inputs.serving_trace(n_jobs, 50.0, seed=1)
-    systems = []
-    for j in trace:
-        L = inputs.box_length(j.nmol)
-        x0, mass = inputs.water_box(j.nmol, L, j.P, j.seed % (2 ** 31), jitter=0.02)
-        systems.append((x0, mass, L, max(1, int(round(j.nsteps * step_scale)))))
     srv = binding.Server(150 * 10 ** 9, max_replicas=512, chunk_steps=100, stream=stream.cuda_stream)
     ids = []
     t0 = time.perf_counter()
-    for j, (x0, mass, L, n) in zip(trace, systems):
+    for j in trace:
+        # each job's box is drawn just before its arrival time (milliseconds),
+        # then submitted at that time
+        L = inputs.box_length(j.nmol)
+        x0, mass = inputs.water_lattice_box(j.nmol, L, j.P, j.seed % (2 ** 31), jitter=0.02)
+        n = max(1, int(round(j.nsteps * step_scale)))
         delay = j.arrival_s - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
@@ -398,7 +399,8 @@ def serve_bench(stream, n_jobs, step_scale):
     srv.close()
     lat = np.array(lat)
     return {
-        "workload": "Poisson water-like jobs at 50/s, first %d of the trace, steps x %g" % (n_jobs, step_scale),
+        "workload": ("Poisson water-like jobs at 50/s, 96-12288 atoms, P 4-128, 1k-50k steps (log-uniform), "
+                     "first %d jobs of the trace, steps x %g" % (n_jobs, step_scale)),
         "jobs": n_jobs, "completed": int(st["completed"]), "failed": int(st["failed"]),
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
         "aggregate": st["bead_atom_steps"] / (last - first), "unit": METRIC,

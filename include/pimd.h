@@ -350,12 +350,13 @@ pimd_status pimd_fp64_fma_rate(int32_t iters, double *tflops);
  * A batch advances many independent water-like ring-polymer systems
  * ("replicas": their own N, P, T, masses, seed and step count) together in
  * split precision (PIMD_PREC_SPLIT arithmetic).  Each MD step of the batch
- * is five kernel launches covering every replica -- control, fused step
- * (warp items for bead counts 8, 16, 32, 64), rebuild decision, neighbour-list
- * rebuilds, forces -- and a sixth, the block-item step, while some replica's
- * bead count is outside {8, 16, 32, 64}; they are captured once in a CUDA
- * graph and replayed, and replicas can be added and removed between calls
- * without re-capture.  Each replica stops after its own step count;
+ * is a sequence of kernel launches covering every replica -- control; the
+ * fused step, as one launch per class of bead count present (warp items of
+ * 64 beads; of 8, 16 or 32 beads; of 128 beads; block items of any other
+ * count); rebuild decision; neighbour-list rebuilds; forces -- captured once
+ * in a CUDA graph and replayed; replicas can be added and removed between
+ * calls, and the graph is captured again only when the set of classes
+ * present changes.  Each replica stops after its own step count;
  * a replica's trajectory does not depend on which other replicas share the
  * batch.  Same units, layouts and error rules as the single-system calls. */
 typedef struct pimd_batch pimd_batch;
@@ -399,9 +400,9 @@ pimd_status pimd_batch_get_state(pimd_batch *b, int32_t slot, double *x, double 
  * batch by timing candidates with CUDA events while the replicas step
  * (steps_per_trial steps per candidate; they count toward the replicas'
  * budgets; trajectories do not depend on the tile), and the blocks per SM of
- * the warp-item step kernel (bead counts 8, 16, 32, 64).  tiles_out, if not
- * NULL, receives PIMD_MAX_BEADS + 1 entries: [0] the warp-item blocks per SM,
- * [P] the chosen tile for bead count P (0 = unused). */
+ * the 64-bead warp-item step kernel.  tiles_out, if not NULL, receives
+ * PIMD_MAX_BEADS + 1 entries: [0] the 64-bead warp-item blocks per SM, [P]
+ * the tile for bead count P (0 = unused; 8 for the warp-item counts). */
 pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t *tiles_out);
 
 /* Normal-mode transforms of the batch's step: PIMD_TRANSFORMS_TENSOR (the

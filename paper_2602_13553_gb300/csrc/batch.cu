@@ -123,6 +123,7 @@ __global__ void k_bctl(const RepDesc *reps, int nslots, int mode, int *wnext) {
     wnext[0] = 0;   // warp-item counter of the step kernel
     wnext[1] = 0;   // length of this step's rebuild list
     wnext[3] = 0;   // warp-item counter of the 128-bead step kernel
+    wnext[5] = 0;   // warp-item counter of the 8-, 16-, 32-bead step kernel
   }
   if (r >= nslots || !reps[r].live) return;
   long long *c = reps[r].ctl;
@@ -803,34 +804,41 @@ __device__ void bstep_warp(const RepDesc *__restrict__ Rp, int tile, float *__re
   __syncwarp();   // the slot is free for the next item
 }
 
-// Warp items (replica, 8-atom tile) of the bead counts in {8, 16, 32, 64},
-// the prefix counts[4] of the step list, taken dynamically: lane 0 of each
-// warp claims the next item from the counter *next (reset by k_bctl).
-__global__ void __launch_bounds__(kWWarps * 32, 3) k_bstep_w(const RepDesc *__restrict__ reps,
-                                                            const int2 *__restrict__ items,
-                                                            const int *__restrict__ counts, int *next,
-                                                            int slot_floats) {
+// Warp items (replica, 8-atom tile) of the bead counts in {8, 16, 32, 64}:
+// the 64-bead items are the range [0, counts[9]) of the step list, claimed
+// from *next; the 8-, 16- and 32-bead items the range [counts[9], counts[4]),
+// run by the kSmall instance, whose smaller accumulator tiles fit four blocks
+// per SM (128 registers, 7.4 KB warp slots) where the 64-bead instance fits
+// three.  Lane 0 of each warp claims the next item (counters reset by k_bctl).
+template <bool kSmall>
+__global__ void __launch_bounds__(kWWarps * 32, kSmall ? 4 : 3) k_bstep_w(const RepDesc *__restrict__ reps,
+                                                                         const int2 *__restrict__ items,
+                                                                         const int *__restrict__ counts, int *next,
+                                                                         int slot_floats) {
   extern __shared__ __align__(16) float wsm[];
   float *slot = wsm + (threadIdx.x >> 5) * slot_floats;
-  const int n = counts[4];
+  const int lo = kSmall ? counts[9] : 0, hi = kSmall ? counts[4] : counts[9];
   const int lane = threadIdx.x & 31;
   for (;;) {
     int it = 0;
-    if (lane == 0) it = atomicAdd(next, 1);
+    if (lane == 0) it = lo + atomicAdd(next, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= n) break;
+    if (it >= hi) break;
     const int2 w = items[it];
     const RepDesc *__restrict__ Rp = reps + w.x;
     const long long *ctl = Rp->ctl;
     if (!ctl[kCtlActive]) continue;
     const uint64_t step = (uint64_t)ctl[kCtlStep];
     const int first = (int)ctl[kCtlFirst];
-    switch (Rp->P) {
-      case 8: bstep_warp<8>(Rp, w.y, slot, step, first); break;
-      case 16: bstep_warp<16>(Rp, w.y, slot, step, first); break;
-      case 32: bstep_warp<32>(Rp, w.y, slot, step, first); break;
-      case 64: bstep_warp<64>(Rp, w.y, slot, step, first); break;
-      default: break;
+    if (kSmall) {
+      switch (Rp->P) {
+        case 8: bstep_warp<8>(Rp, w.y, slot, step, first); break;
+        case 16: bstep_warp<16>(Rp, w.y, slot, step, first); break;
+        case 32: bstep_warp<32>(Rp, w.y, slot, step, first); break;
+        default: break;
+      }
+    } else if (Rp->P == 64) {
+      bstep_warp<64>(Rp, w.y, slot, step, first);
     }
   }
 }
@@ -1959,11 +1967,14 @@ struct pimd_batch {
   std::vector<int2> h_step, h_nbr, h_est;
   std::vector<int4> h_clu;
   // [0] step items, [1] force, [2] nbr, [3] est, [4] end of the warp items,
-  // [5] their claim counter, [6] rebuild-list length, [7] end of the
-  // 128-bead warp items, [8] their claim counter
+  // [5] claim counter of the 64-bead warp items, [6] rebuild-list length,
+  // [7] end of the 128-bead warp items, [8] their claim counter, [9] end of
+  // the 64-bead warp items, [10] claim counter of the smaller warp items
   int h_counts[16] = {0};
-  int wslot = 0;          // floats of shared memory per warp of the warp-item step kernel
+  int wslot = wslot_floats(64);   // floats of shared memory per warp of the 64-bead warp-item kernel
   int grid_w = 0;         // its blocks (persistent grid)
+  int grid_ws = 0;        // blocks of the 8-, 16-, 32-bead warp-item kernel
+  bool w64_items = false, wsmall_items = false;   // which warp-item kernels have items
   int grid_w128 = 0;      // blocks of the 128-bead warp-item kernel
   bool block_items = true;   // some replica has a bead count outside the warp-item classes
   bool w128_items = false;   // some replica has 128 beads
@@ -2039,15 +2050,14 @@ pimd_status upload(pimd_batch *b) {
   std::vector<RepDesc> descs(b->capacity);
   // warp items first, largest bead count first (the costliest items are
   // claimed first), then the block items of the other bead counts
-  int pmax_w = 0;
-  for (int P : {64, 32, 16, 8})
+  int n64 = 0;
+  for (int P : {64, 32, 16, 8}) {
     for (int s = 0; s < b->capacity && !b->ffma; ++s) {
       Replica &r = b->reps[s];
-      if (r.live && r.P == P) {
-        b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
-        pmax_w = std::max(pmax_w, P);
-      }
+      if (r.live && r.P == P) b->h_step.insert(b->h_step.end(), r.items_step.begin(), r.items_step.end());
     }
+    if (P == 64) n64 = (int)b->h_step.size();
+  }
   const int nw = (int)b->h_step.size();
   for (int s = 0; s < b->capacity && !b->ffma; ++s) {   // then the 128-bead warp items
     Replica &r = b->reps[s];
@@ -2086,26 +2096,15 @@ pimd_status upload(pimd_batch *b) {
   b->h_counts[6] = 0;
   b->h_counts[7] = nw128;
   b->h_counts[8] = 0;
-  const bool blk = b->h_counts[0] > nw128, w128 = nw128 > nw;
-  if (blk != b->block_items || w128 != b->w128_items) {
+  b->h_counts[9] = n64;
+  b->h_counts[10] = 0;
+  const bool blk = b->h_counts[0] > nw128, w128 = nw128 > nw, w64 = n64 > 0, wsm = nw > n64;
+  if (blk != b->block_items || w128 != b->w128_items || w64 != b->w64_items || wsm != b->wsmall_items) {
     b->block_items = blk;
     b->w128_items = w128;
-    if (b->graph) {   // the captured step launches k_bstep / k_bstep_w128 or not
-      cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
-    }
-  }
-  const int slot = pmax_w ? wslot_floats(pmax_w) : wslot_floats(8);
-  if (slot != b->wslot) {
-    b->wslot = slot;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k_bstep_w, kWWarps * 32,
-                                                      (size_t)kWWarps * slot * sizeof(float)) != cudaSuccess ||
-        nb < 1)
-      nb = 1;
-    b->wblocks_sm = b->wtuned > 0 ? std::min(b->wtuned, nb) : nb;
-    b->grid_w = b->nsm * b->wblocks_sm;
-    if (b->graph) {   // the captured launch has the old shared-memory size
+    b->w64_items = w64;
+    b->wsmall_items = wsm;
+    if (b->graph) {   // the captured step launches another set of step kernels
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
@@ -2127,8 +2126,12 @@ pimd_status upload(pimd_batch *b) {
 
 // The two step kernels: warp items, then block items.
 void launch_step_kernels(pimd_batch *b) {
-  k_bstep_w<<<b->grid_w, kWWarps * 32, (size_t)kWWarps * b->wslot * sizeof(float), b->stream>>>(
-      b->d_reps, b->d_step, b->d_counts, b->d_counts + 5, b->wslot);
+  if (b->w64_items)
+    k_bstep_w<false><<<b->grid_w, kWWarps * 32, (size_t)kWWarps * b->wslot * sizeof(float), b->stream>>>(
+        b->d_reps, b->d_step, b->d_counts, b->d_counts + 5, b->wslot);
+  if (b->wsmall_items)
+    k_bstep_w<true><<<b->grid_ws, kWWarps * 32, (size_t)kWWarps * wslot_floats(32) * sizeof(float), b->stream>>>(
+        b->d_reps, b->d_step, b->d_counts, b->d_counts + 10, wslot_floats(32));
   if (b->w128_items)
     k_bstep_w128<<<b->grid_w128, kWWarps * 32, (size_t)kWWarps * wslot_floats(128) * sizeof(float), b->stream>>>(
         b->d_reps, b->d_step, b->d_counts, b->d_counts + 8);
@@ -2144,7 +2147,9 @@ void launch_nbr_kernels(pimd_batch *b) {
 // Kernels launched per MD step: control, warp-item step, 128-bead warp-item
 // step and block-item step (each when some replica needs it), rebuild
 // decision, rebuilds, forces.
-int step_launches(const pimd_batch *b) { return 5 + (b->block_items ? 1 : 0) + (b->w128_items ? 1 : 0); }
+int step_launches(const pimd_batch *b) {
+  return 4 + (b->w64_items ? 1 : 0) + (b->wsmall_items ? 1 : 0) + (b->block_items ? 1 : 0) + (b->w128_items ? 1 : 0);
+}
 
 // One MD step of every active replica.
 cudaError_t launch_one_step(pimd_batch *b, cudaEvent_t e0, cudaEvent_t e1) {
@@ -2428,8 +2433,10 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
   }
   const int wsmem = (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float));
   const int wsmem128 = (int)(kWWarps * wslot_floats(128) * sizeof(float));
-  if (cudaFuncSetAttribute((const void *)k_bstep_w, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem) !=
+  if (cudaFuncSetAttribute((const void *)k_bstep_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem) !=
           cudaSuccess ||
+      cudaFuncSetAttribute((const void *)k_bstep_w<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kWWarps * wslot_floats(32) * sizeof(float))) != cudaSuccess ||
       cudaFuncSetAttribute((const void *)k_bstep_w128, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem128) !=
           cudaSuccess) {
     cudaGetLastError();
@@ -2445,6 +2452,17 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
   };
   b->grid_step = occ((const void *)k_bstep);
   b->grid_w128 = occ((const void *)k_bstep_w128, (size_t)kWWarps * wslot_floats(128) * sizeof(float));
+  b->grid_ws = occ((const void *)k_bstep_w<true>, (size_t)kWWarps * wslot_floats(32) * sizeof(float));
+  b->wblocks_sm = 0;
+  {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k_bstep_w<false>, kWWarps * 32,
+                                                      (size_t)kWWarps * b->wslot * sizeof(float)) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    b->wblocks_sm = nb;
+    b->grid_w = nsm * nb;
+  }
   b->grid_clu = occ((const void *)k_bforce);
   b->grid_nbr = occ((const void *)k_bnbr, kNbrSmem, kNbrThreads);
   b->grid_est = 8 * nsm;
@@ -2937,10 +2955,10 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
     return PIMD_OK;
   };
   pimd_status st = PIMD_OK;
-  if (!b->ffma && std::any_of(classes.begin(), classes.end(), [](int P) { return warp_class(P); })) {
+  if (!b->ffma && std::find(classes.begin(), classes.end(), 64) != classes.end()) {
     if (b->dirty && (st = upload(b)) != PIMD_OK) return st;
     int nbmax = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbmax, (const void *)k_bstep_w, kWWarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbmax, (const void *)k_bstep_w<false>, kWWarps * 32,
                                                       (size_t)kWWarps * b->wslot * sizeof(float)) != cudaSuccess ||
         nbmax < 1)
       nbmax = 1;

@@ -18,7 +18,9 @@ Workloads (the synthetic stand-ins for the paper's DP-water runs, Sec. V):
     T uniform in [100, 400] K, H or D masses with probability 1/2.
   * ``serving_trace``: Poisson arrivals, molecule count log-uniform in
     [32, 4096] (96 to 12288 atoms), P log-uniform over {4, ..., 128},
-    step count log-uniform in [1000, 50000].
+    step count log-uniform in [1000, 50000]; its boxes come from
+    ``water_lattice_box`` (oxygens on a randomly displaced subset of a cubic
+    lattice, O-O >= 2.5 A), which is linear in the molecule count.
 """
 from __future__ import annotations
 
@@ -63,26 +65,22 @@ def box_length(nmol: int, density_g_cm3: float = 1.0) -> float:
     return (vol_cm3 ** (1.0 / 3.0)) * 1e8
 
 
-def _random_rotation(g: np.random.Generator) -> np.ndarray:
-    q = g.normal(size=4)
-    q /= np.linalg.norm(q)
-    a, b, c, d = q
-    return np.array([
-        [a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
-        [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
-        [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d],
-    ])
-
-
 def water_box(nmol: int, L: float, P: int, seed: int, *, r_oo_min: float = 2.5,
               r0: float = 1.0, theta0_deg: float = 104.5, jitter: float = 0.0,
               deuterium: bool = False):
     """Return (x [P][3*nmol][3], mass [3*nmol]) for a random water-like box.
 
     Atoms are ordered O, H, H per molecule.  Coordinates are unwrapped (the O
-    lies in [0, L)^3; hydrogens may stick out by a bond length)."""
+    lies in [0, L)^3; hydrogens may stick out by a bond length).  Oxygens are
+    placed by random sequential addition: a uniform candidate is kept if no
+    placed oxygen lies within r_oo_min (minimum image); the test looks only at
+    the 27 periodic cells around the candidate (cells at least r_oo_min wide),
+    which is the same decision as a test against every placed oxygen."""
     g = rng(seed)
     O = np.zeros((nmol, 3))
+    nc = max(1, int(L // r_oo_min))          # cells per edge, each >= r_oo_min
+    cells = {}
+    r2min = r_oo_min * r_oo_min
     n = 0
     attempts = 0
     while n < nmol:
@@ -90,22 +88,77 @@ def water_box(nmol: int, L: float, P: int, seed: int, *, r_oo_min: float = 2.5,
         if attempts > 2000 * max(nmol, 1):
             raise RuntimeError("water_box: could not place %d molecules in L=%.3f" % (nmol, L))
         p = g.uniform(0.0, L, size=3)
-        if n:
-            d = O[:n] - p
+        c = [min(nc - 1, int(p[a] * nc / L)) for a in range(3)]
+        near = []
+        if nc < 3:
+            near = list(range(n))
+        else:
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        near.extend(cells.get(((c[0] + dx) % nc, (c[1] + dy) % nc, (c[2] + dz) % nc), ()))
+        if near:
+            d = O[near] - p
             d -= L * np.rint(d / L)
-            if np.min(np.einsum("ij,ij->i", d, d)) < r_oo_min * r_oo_min:
+            if np.min(np.einsum("ij,ij->i", d, d)) < r2min:
                 continue
         O[n] = p
+        cells.setdefault(tuple(c), []).append(n)
         n += 1
+    return _molecules(g, O, P, r0, theta0_deg, jitter, deuterium)
+
+
+def water_lattice_box(nmol: int, L: float, P: int, seed: int, *, r_oo_min: float = 2.5,
+                      r0: float = 1.0, theta0_deg: float = 104.5, jitter: float = 0.0,
+                      deuterium: bool = False):
+    """As water_box, but the oxygens start on a random subset of the sites of
+    a k x k x k cubic lattice (k^3 >= nmol), each displaced uniformly within
+    the cube that keeps every O-O distance >= r_oo_min: linear in nmol and
+    vectorised, for the serving trace's thousands of boxes of up to 4096
+    molecules (random sequential addition takes seconds per large box).  At
+    1 g/cm^3 the lattice is wide enough from 70 molecules on; smaller boxes
+    (and any box whose lattice would be too tight) fall back to water_box."""
+    k = 1
+    while k ** 3 < nmol:
+        k += 1
+    a = L / k
+    if a < r_oo_min:
+        return water_box(nmol, L, P, seed, r_oo_min=r_oo_min, r0=r0, theta0_deg=theta0_deg, jitter=jitter,
+                         deuterium=deuterium)
+    g = rng(seed)
+    sites = g.permutation(k ** 3)[:nmol]
+    ijk = np.stack([sites // (k * k), (sites // k) % k, sites % k], axis=1).astype(np.float64)
+    delta = 0.5 * (a - r_oo_min)
+    O = (ijk + 0.5) * a + g.uniform(-delta, delta, size=(nmol, 3))
+    return _molecules(g, O, P, r0, theta0_deg, jitter, deuterium)
+
+
+def _molecules(g, O, P, r0, theta0_deg, jitter, deuterium):
+    """Water-like molecules at oxygen positions O [nmol][3]: a uniformly
+    random orientation each, rigid geometry (r0, theta0), every bead a copy
+    plus N(0, jitter^2); atoms O, H, H per molecule."""
+    nmol = O.shape[0]
     half = math.radians(theta0_deg) / 2.0
     h1 = r0 * np.array([math.sin(half), math.cos(half), 0.0])
     h2 = r0 * np.array([-math.sin(half), math.cos(half), 0.0])
+    # one uniformly random orientation per molecule (unit quaternions)
+    q = g.normal(size=(nmol, 4))
+    q /= np.linalg.norm(q, axis=1)[:, None]
+    a, b, c, d = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    R = np.empty((nmol, 3, 3))
+    R[:, 0, 0] = a * a + b * b - c * c - d * d
+    R[:, 0, 1] = 2 * (b * c - a * d)
+    R[:, 0, 2] = 2 * (b * d + a * c)
+    R[:, 1, 0] = 2 * (b * c + a * d)
+    R[:, 1, 1] = a * a - b * b + c * c - d * d
+    R[:, 1, 2] = 2 * (c * d - a * b)
+    R[:, 2, 0] = 2 * (b * d - a * c)
+    R[:, 2, 1] = 2 * (c * d + a * b)
+    R[:, 2, 2] = a * a - b * b - c * c + d * d
     x1 = np.zeros((3 * nmol, 3))
-    for m in range(nmol):
-        R = _random_rotation(g)
-        x1[3 * m] = O[m]
-        x1[3 * m + 1] = O[m] + R @ h1
-        x1[3 * m + 2] = O[m] + R @ h2
+    x1[0::3] = O
+    x1[1::3] = O + R @ h1
+    x1[2::3] = O + R @ h2
     x = np.repeat(x1[None, :, :], P, axis=0)
     if jitter > 0.0:
         x = x + g.normal(0.0, jitter, size=x.shape)
