@@ -274,6 +274,36 @@ def sweep_bench(stream, fp64_peak, steps=4, warmup=2):
             "unit": METRIC, "points": out}
 
 
+def same_mix_handles(reps, precision, md_steps=100, warm=10):
+    """The replicas of the batched mix as independent single-system handles
+    (plain FP64 or split precision), each on its own CUDA stream, all
+    stepped together: bead-atom-steps/s of md_steps steps (host clock around
+    the launches and a device synchronise)."""
+    import torch
+    from paper_2602_13553_gb300 import binding, inputs
+    sims, streams = [], []
+    units = 0
+    for r in reps:
+        x0, mass = inputs.water_box(r.nmol, r.L, r.P, r.seed, jitter=0.02, deuterium=r.deuterium)
+        st = torch.cuda.Stream()
+        sims.append(binding.Simulation(x0, mass, T=r.T, dt=5e-4, potential=binding.POT_WATERLIKE,
+                                       ff=inputs.water_ff_for_box(r.L), box=(r.L,) * 3, seed=r.seed,
+                                       precision=precision, stream=st.cuda_stream))
+        streams.append(st)
+        units += 3 * r.nmol * r.P
+    for sim in sims:
+        sim.step(warm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for sim in sims:
+        sim.step(md_steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for sim in sims:
+        sim.close()
+    return units * md_steps / dt
+
+
 def batched_bench(stream, steps, warmup):
     """The batched workload: 256 independent water-like replicas (32-512
     molecules log-uniform at 1 g/cm^3, P in {8,16,32,64}, T in [100,400] K,
@@ -351,6 +381,11 @@ def batched_bench(stream, steps, warmup):
                      "avg_launch_ms": per_ms,
                      "traffic": traffic_for("k_bstep_w" if dom == "step" else "k_bforce"),
                      "kernel_time_share": {k: round(v / tot, 4) for k, v in kt.items()}},
+        "same_mix": {"plain_fp64_handles": same_mix_handles(reps, 0), "split_handles": same_mix_handles(reps, 1),
+                     "unit": METRIC,
+                     "basis": "the same 256 replicas as independent single-system handles, one CUDA stream "
+                              "each, 100 MD steps of all of them (host clock around launches and a device "
+                              "synchronise): plain FP64, and split precision without the batch engine"},
         "transform_ab": {"tensor_core_step_ms": kt["step"] / 10.0, "ffma_step_ms": kt_ffma["step"] / 10.0,
                          "basis": "per-MD-step device time of the step kernels over the mix: warp items with "
                                   "3xTF32 mma.sync transforms against block items with FP32 FMA transforms"},

@@ -875,13 +875,13 @@ __global__ void __launch_bounds__(kWWarps * 32, 1) k_bstep_w128(const RepDesc *_
 // turns the step's skin maxima (squared FP32 bit patterns in ctl) into the
 // one conservative (drift, spread) pair that the neighbour-list check reads,
 // and clears them for the next step (threadfence-and-count, no waiting).
-// kBig: the 128-bead instance (eight mode tiles, one block per SM's share of
-// registers), as k_bstep_w128 is for the batch.
-template <bool kBig>
-__global__ void __launch_bounds__(kWWarps * 32, kBig ? 1 : 3) k_sstep_w(const RepDesc *__restrict__ Rp,
-                                                                       const int64_t *__restrict__ stepp,
-                                                                       int step_off, int first, int slot_floats,
-                                                                       double *blkmax, unsigned *done) {
+// kClass: 0 the 8-, 16- and 32-bead instance (128 registers, four blocks per
+// SM), 1 the 64-bead one (three blocks), 2 the 128-bead one (eight mode
+// tiles, one block's share of registers), as for the batch.
+template <int kClass>
+__global__ void __launch_bounds__(kWWarps * 32, kClass == 0 ? 4 : (kClass == 1 ? 3 : 1))
+    k_sstep_w(const RepDesc *__restrict__ Rp, const int64_t *__restrict__ stepp, int step_off, int first,
+              int slot_floats, double *blkmax, unsigned *done) {
   extern __shared__ __align__(16) float wsm[];
   float *slot = wsm + (threadIdx.x >> 5) * slot_floats;
   const int lane = threadIdx.x & 31;
@@ -889,16 +889,17 @@ __global__ void __launch_bounds__(kWWarps * 32, kBig ? 1 : 3) k_sstep_w(const Re
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const uint64_t step = (uint64_t)(*stepp + step_off);
   for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += nw) {
-    if (kBig) {
+    if (kClass == 2) {
       if (Rp->P == 128) bstep_warp<128>(Rp, tile, slot, step, first);
-      continue;
-    }
-    switch (Rp->P) {
-      case 8: bstep_warp<8>(Rp, tile, slot, step, first); break;
-      case 16: bstep_warp<16>(Rp, tile, slot, step, first); break;
-      case 32: bstep_warp<32>(Rp, tile, slot, step, first); break;
-      case 64: bstep_warp<64>(Rp, tile, slot, step, first); break;
-      default: break;
+    } else if (kClass == 1) {
+      if (Rp->P == 64) bstep_warp<64>(Rp, tile, slot, step, first);
+    } else {
+      switch (Rp->P) {
+        case 8: bstep_warp<8>(Rp, tile, slot, step, first); break;
+        case 16: bstep_warp<16>(Rp, tile, slot, step, first); break;
+        case 32: bstep_warp<32>(Rp, tile, slot, step, first); break;
+        default: break;
+      }
     }
   }
   if (!blkmax) return;
@@ -1691,6 +1692,7 @@ __global__ void __launch_bounds__(128, 6) k_bforce(const RepDesc *__restrict__ r
 __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *items, const int *count) {
   __shared__ CSum sK[128], sS[128];
   __shared__ CSum sred[3][4];
+  __shared__ float sDv[3 * 128];   // the tile's deviation rows (A atoms x 3 x P <= 384)
   const int n = *count;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 w = items[it];
@@ -1702,6 +1704,12 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
     CSum kk{0.0, 0.0}, ss{0.0, 0.0}, rF{0.0, 0.0}, rcF{0.0, 0.0}, mv0{0.0, 0.0};
     for (int tile = w.y; tile < ntiles; tile += R.ne) {
       const int tile0 = tile * A;
+      // stage the tile's deviations (contiguous in [N][3][P]) once: every
+      // mode's transform reads the whole row
+      const int nrow = min(A, N - tile0) * 3 * P;
+      __syncthreads();
+      for (int t = threadIdx.x; t < nrow; t += blockDim.x) sDv[t] = R.d[(size_t)tile0 * 3 * P + t];
+      __syncthreads();
       for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
         const int k = task % P, al = task / P;
         const int i = tile0 + al;
@@ -1714,7 +1722,7 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
           const double v = k == 0 ? R.v0[(size_t)i * 3 + c] : (double)R.vk[row + k];
           v2 += v * v;
           float qa = 0.f, qb = 0.f, dma = 0.f, dmb = 0.f;
-          const float *__restrict__ dr = R.d + row;
+          const float *__restrict__ dr = sDv + (al * 3 + c) * P;
           const float *__restrict__ mc = R.Mtf + k;
           int j = 0;
           for (; j + 1 < P; j += 2) {
@@ -2275,10 +2283,13 @@ cudaError_t split_warp_prepare() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void *)k_sstep_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kWWarps * wslot_floats(kWMaxP) * sizeof(float)));
+    e = cudaFuncSetAttribute((const void *)k_sstep_w<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kWWarps * wslot_floats(32) * sizeof(float)));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void *)k_sstep_w<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute((const void *)k_sstep_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kWWarps * wslot_floats(64) * sizeof(float)));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void *)k_sstep_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kWWarps * wslot_floats(128) * sizeof(float)));
   if (e == cudaSuccess) g_sw_nsm = nsm > 0 ? nsm : 152;
   return e;
@@ -2373,18 +2384,20 @@ cudaError_t launch_step_split_warp(const void *desc, int N, int P, const int64_t
   const cudaError_t pe = split_warp_prepare();
   if (pe != cudaSuccess) return pe;
   const int nsm = g_sw_nsm;
-  const bool big = P == 128;
-  const int slot = big ? wslot_floats(128) : wslot_floats(kWMaxP);
+  const int cls = P == 128 ? 2 : (P == 64 ? 1 : 0);
+  const int slot = wslot_floats(cls == 2 ? 128 : (cls == 1 ? 64 : 32));
+  const int per_sm = cls == 2 ? 2 : (cls == 1 ? 3 : 4);   // resident blocks per SM (registers, shared memory)
   const int smem = (int)(kWWarps * slot * sizeof(float));
   const int ntiles = (N + kWAtoms - 1) / kWAtoms;
-  const int warps = std::min(ntiles, nsm * (big ? 2 : 3) * kWWarps);
+  const int warps = std::min(ntiles, nsm * per_sm * kWWarps);
   const int grid = std::max(1, (warps + kWWarps - 1) / kWWarps);
-  if (big)
-    k_sstep_w<true><<<grid, kWWarps * 32, smem, s>>>(reinterpret_cast<const RepDesc *>(desc), step, step_off, first,
-                                                     slot, blkmax, done);
+  const RepDesc *d = reinterpret_cast<const RepDesc *>(desc);
+  if (cls == 2)
+    k_sstep_w<2><<<grid, kWWarps * 32, smem, s>>>(d, step, step_off, first, slot, blkmax, done);
+  else if (cls == 1)
+    k_sstep_w<1><<<grid, kWWarps * 32, smem, s>>>(d, step, step_off, first, slot, blkmax, done);
   else
-    k_sstep_w<false><<<grid, kWWarps * 32, smem, s>>>(reinterpret_cast<const RepDesc *>(desc), step, step_off,
-                                                      first, slot, blkmax, done);
+    k_sstep_w<0><<<grid, kWWarps * 32, smem, s>>>(d, step, step_off, first, slot, blkmax, done);
   return cudaGetLastError();
 }
 
@@ -2962,21 +2975,24 @@ extern "C" pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_tria
                                                       (size_t)kWWarps * b->wslot * sizeof(float)) != cudaSuccess ||
         nbmax < 1)
       nbmax = 1;
-    int best = nbmax;
-    float best_ms = 1e30f;
+    // each candidate: one untimed step (caches and clocks settle), then the
+    // faster of two timed trials; a smaller grid than the occupancy limit must
+    // win by more than 3% (the timings are a few milliseconds and noisy)
+    std::vector<float> tms(nbmax + 1, 1e30f);
     for (int nb = nbmax; nb >= 1 && st == PIMD_OK; --nb) {
       b->wblocks_sm = nb;
       b->grid_w = b->nsm * nb;
-      // one untimed step first (caches and clocks settle), then the trial
       if (launch_one_step(b, nullptr, nullptr) != cudaSuccess) return fail(PIMD_ECUDA, "autotune step failed");
       b->launches += step_launches(b);
-      float ms = 0.f;
-      st = time_step(&ms);
-      if (st == PIMD_OK && ms < best_ms) {
-        best_ms = ms;
-        best = nb;
+      for (int rep = 0; rep < 2 && st == PIMD_OK; ++rep) {
+        float ms = 0.f;
+        st = time_step(&ms);
+        if (st == PIMD_OK) tms[nb] = std::min(tms[nb], ms);
       }
     }
+    int best = nbmax;
+    for (int nb = nbmax - 1; nb >= 1; --nb)
+      if (tms[nb] < 0.97f * tms[best]) best = nb;
     b->wblocks_sm = best;
     b->wtuned = best;
     b->grid_w = b->nsm * best;
