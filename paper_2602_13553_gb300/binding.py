@@ -7,6 +7,7 @@ the library's allocator hook, see ``use_torch_allocator``) and CUDA streams.
 """
 from __future__ import annotations
 
+import collections.abc
 import ctypes
 import os
 import threading
@@ -96,6 +97,31 @@ class Estimates(ctypes.Structure):
         out["S_mode"] = np.array(self.S_mode[:P])
         out["U_bead"] = np.array(self.U_bead[:P])
         return out
+
+
+class _EstimatesMap(collections.abc.Mapping):
+    """Read-only mapping slot -> estimator dict over one pimd_estimates array;
+    a slot's dict is built when it is first read (a batch holds hundreds of
+    replicas; building every dict costs milliseconds of host time)."""
+
+    def __init__(self, arr, slots):
+        self._arr = arr
+        self._slots = list(slots)
+        self._live = set(self._slots)
+        self._cache = {}
+
+    def __getitem__(self, slot):
+        if slot not in self._live:
+            raise KeyError(slot)
+        if slot not in self._cache:
+            self._cache[slot] = self._arr[slot].as_dict()
+        return self._cache[slot]
+
+    def __iter__(self):
+        return iter(self._slots)
+
+    def __len__(self):
+        return len(self._slots)
 
 
 # every symbol include/pimd.h declares (checked by the CPU tests)
@@ -460,9 +486,10 @@ class Batch:
         return np.array(st[:]), np.array(left[:])
 
     def estimators(self):
+        """slot -> estimator dict of every live replica (converted on first access)."""
         arr = (Estimates * self.capacity)()
         check(_batch_lib().pimd_batch_estimators(self._h, arr))
-        return {s: arr[s].as_dict() for s in range(self.capacity) if arr[s].step >= 0}
+        return _EstimatesMap(arr, [s for s in range(self.capacity) if arr[s].step >= 0])
 
     def get_state(self, slot: int):
         P, N = self.shapes[slot]

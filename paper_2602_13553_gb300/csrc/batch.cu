@@ -1701,7 +1701,9 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
     const int A = P >= 128 ? 1 : 128 / P;       // estimator tile: A P <= 128 tasks
     const int ntiles = (N + A - 1) / A;
     const int ntask = A * P;
-    CSum kk{0.0, 0.0}, ss{0.0, 0.0}, rF{0.0, 0.0}, rcF{0.0, 0.0}, mv0{0.0, 0.0};
+    // per thread a handful of tiles (plain FP64 sums: a few tens of terms);
+    // every combination across threads and blocks below is compensated
+    double kk = 0.0, ss = 0.0, rF = 0.0, rcF = 0.0, mv0 = 0.0;
     for (int tile = w.y; tile < ntiles; tile += R.ne) {
       const int tile0 = tile * A;
       // stage the tile's deviations (contiguous in [N][3][P]) once: every
@@ -1714,13 +1716,23 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
         const int k = task % P, al = task / P;
         const int i = tile0 + al;
         if (i >= N) continue;
+        // the FP64 pipe is the scarce unit: products of FP32 quantities stay
+        // in FP32 and are converted once per task; only terms with an FP64
+        // factor (the centroid x_c, the centroid-mode velocity, the masses)
+        // are formed in FP64.  x.F = x_c.F + d.F, (x - x_c).F = (d - <d>).F.
         const double mm = __ldg(R.mass_mm + i);
-        double v2 = 0.0, q2 = 0.0;
+        double v2 = 0.0, xcF = 0.0;
+        float v2f = 0.f, q2f = 0.f, dF = 0.f, dcF = 0.f;
         const float invP = 1.0f / (float)P;
         for (int c = 0; c < 3; ++c) {
           const size_t row = ((size_t)i * 3 + c) * P;
-          const double v = k == 0 ? R.v0[(size_t)i * 3 + c] : (double)R.vk[row + k];
-          v2 += v * v;
+          if (k == 0) {
+            const double v = R.v0[(size_t)i * 3 + c];
+            v2 = fma(v, v, v2);
+          } else {
+            const float v = R.vk[row + k];
+            v2f = fmaf(v, v, v2f);
+          }
           float qa = 0.f, qb = 0.f, dma = 0.f, dmb = 0.f;
           const float *__restrict__ dr = sDv + (al * 3 + c) * P;
           const float *__restrict__ mc = R.Mtf + k;
@@ -1736,24 +1748,27 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
             qa = fmaf(__ldg(mc + j * P), dr[j], qa);
             dma += dr[j];
           }
-          const double q = (double)(qa + qb);
-          if (k > 0) q2 += q * q;
+          const float q = qa + qb;
+          if (k > 0) q2f = fmaf(q, q, q2f);
           const float dk = dr[k];
-          const double xk = R.xc[(size_t)i * 3 + c] + (double)dk;
-          const double fk = (double)R.F[row + k];
-          rF.add(xk * fk);
-          rcF.add((double)(dk - (dma + dmb) * invP) * fk);
+          const float fk = R.F[row + k];
+          xcF = fma(R.xc[(size_t)i * 3 + c], (double)fk, xcF);
+          dF = fmaf(dk, fk, dF);
+          dcF = fmaf(dk - (dma + dmb) * invP, fk, dcF);
         }
-        kk.add(0.5 * mm * v2);
-        ss.add(0.5 * mm * R.wn2 * __ldg(R.lam + k) * q2);
-        if (k == 0) mv0.add(mm * v2);
+        v2 += (double)v2f;
+        rF += xcF + (double)dF;
+        rcF += (double)dcF;
+        kk = fma(0.5 * mm, v2, kk);
+        ss = fma(0.5 * mm * R.wn2 * __ldg(R.lam + k), (double)q2f, ss);
+        if (k == 0) mv0 = fma(mm, v2, mv0);
       }
     }
     // per-mode sums: tile tasks never exceed the 128 threads, so thread t
     // always held task t, i.e. mode t mod P; sum over atoms in order
     double *out = R.epart + (size_t)w.y * (2 * P + 4);
-    sK[threadIdx.x] = kk;
-    sS[threadIdx.x] = ss;
+    sK[threadIdx.x] = CSum{kk, 0.0};
+    sS[threadIdx.x] = CSum{ss, 0.0};
     __syncthreads();
     for (int k = threadIdx.x; k < P; k += blockDim.x) {
       CSum a{0.0, 0.0}, b2{0.0, 0.0};
@@ -1764,14 +1779,12 @@ __global__ void __launch_bounds__(128) k_best(const RepDesc *reps, const int2 *i
       out[k] = a.value();
       out[P + k] = b2.value();
     }
-    rF = warp_csum(rF);
-    rcF = warp_csum(rcF);
-    mv0 = warp_csum(mv0);
+    const CSum crF = warp_csum(CSum{rF, 0.0}), crcF = warp_csum(CSum{rcF, 0.0}), cmv0 = warp_csum(CSum{mv0, 0.0});
     __syncthreads();
     if ((threadIdx.x & 31) == 0) {
-      sred[0][threadIdx.x >> 5] = rF;
-      sred[1][threadIdx.x >> 5] = rcF;
-      sred[2][threadIdx.x >> 5] = mv0;
+      sred[0][threadIdx.x >> 5] = crF;
+      sred[1][threadIdx.x >> 5] = crcF;
+      sred[2][threadIdx.x >> 5] = cmv0;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
@@ -1819,6 +1832,7 @@ __device__ double neumaier_b(const double *p, int n, size_t stride) {
 __global__ void k_best_final(const RepDesc *reps, int nslots, double *eout) {
   __shared__ double tot[2 * kMaxBeads + 4];
   __shared__ double U[kMaxBeads], Wv[kMaxBeads];
+  __shared__ CSum cu[128], cw[128];
   const int r = blockIdx.x;
   if (r >= nslots) return;
   const RepDesc &R = reps[r];
@@ -1826,9 +1840,31 @@ __global__ void k_best_final(const RepDesc *reps, int nslots, double *eout) {
   const int P = R.P;
   const int W = 2 * P + 4;
   for (int s = threadIdx.x; s < W; s += blockDim.x) tot[s] = neumaier_b(R.epart + s, R.ne, W);
+  // the bead sums of U and Tr Xi over the molecules: thread t sums bead
+  // t mod P over the molecule rows of chunk t / P (compensated), then the
+  // chunks are added in order -- a fixed decomposition for a given P
+  const int nch = P >= 128 ? 1 : 128 / P;
+  const int per = (R.nmol + nch - 1) / nch;
+  if (threadIdx.x < nch * P) {
+    const int k = threadIdx.x % P, ch = threadIdx.x / P;
+    CSum su{0.0, 0.0}, sw{0.0, 0.0};
+    const int m1 = min(R.nmol, (ch + 1) * per);
+    for (int m = ch * per; m < m1; ++m) {
+      su.add(R.Upart[(size_t)m * P + k]);
+      sw.add(R.Wpart[(size_t)m * P + k]);
+    }
+    cu[threadIdx.x] = su;
+    cw[threadIdx.x] = sw;
+  }
+  __syncthreads();
   for (int k = threadIdx.x; k < P; k += blockDim.x) {
-    U[k] = neumaier_b(R.Upart + k, R.nmol, P);
-    Wv[k] = neumaier_b(R.Wpart + k, R.nmol, P);
+    CSum su{0.0, 0.0}, sw{0.0, 0.0};
+    for (int ch = 0; ch < nch; ++ch) {
+      su.add(cu[ch * P + k]);
+      sw.add(cw[ch * P + k]);
+    }
+    U[k] = su.value();
+    Wv[k] = sw.value();
   }
   double *o = eout + (size_t)r * kOutStride;
   for (int k = threadIdx.x; k < 3 * kMaxBeads; k += blockDim.x) o[k] = 0.0;
@@ -1945,6 +1981,10 @@ struct pimd_batch {
   int capacity = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // a second stream and two events: the step kernels of the bead classes run
+  // side by side (a fork and a join inside every step, captured into the graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   DevAllocator alloc;
   std::vector<Replica> reps;
   RepDesc *d_reps = nullptr;
@@ -2133,17 +2173,31 @@ pimd_status upload(pimd_batch *b) {
 }
 
 // The two step kernels: warp items, then block items.
+// The classes' step kernels touch disjoint replicas, so the 8-32-bead and
+// block-item kernels run on the side stream beside the 64- and 128-bead ones
+// (fork after the control kernel, join before the rebuild decision): one
+// kernel's tail fills with the other's work.
 void launch_step_kernels(pimd_batch *b) {
+  const bool fork = (b->w64_items || b->w128_items) && (b->wsmall_items || b->block_items);
+  cudaStream_t s2 = fork ? b->side : b->stream;
+  if (fork) {
+    cudaEventRecord(b->fork_ev, b->stream);
+    cudaStreamWaitEvent(b->side, b->fork_ev, 0);
+  }
   if (b->w64_items)
     k_bstep_w<false><<<b->grid_w, kWWarps * 32, (size_t)kWWarps * b->wslot * sizeof(float), b->stream>>>(
         b->d_reps, b->d_step, b->d_counts, b->d_counts + 5, b->wslot);
   if (b->wsmall_items)
-    k_bstep_w<true><<<b->grid_ws, kWWarps * 32, (size_t)kWWarps * wslot_floats(32) * sizeof(float), b->stream>>>(
+    k_bstep_w<true><<<b->grid_ws, kWWarps * 32, (size_t)kWWarps * wslot_floats(32) * sizeof(float), s2>>>(
         b->d_reps, b->d_step, b->d_counts, b->d_counts + 10, wslot_floats(32));
   if (b->w128_items)
     k_bstep_w128<<<b->grid_w128, kWWarps * 32, (size_t)kWWarps * wslot_floats(128) * sizeof(float), b->stream>>>(
         b->d_reps, b->d_step, b->d_counts, b->d_counts + 8);
-  if (b->block_items) k_bstep<<<b->grid_step, 128, 0, b->stream>>>(b->d_reps, b->d_step, b->d_counts);
+  if (b->block_items) k_bstep<<<b->grid_step, 128, 0, s2>>>(b->d_reps, b->d_step, b->d_counts);
+  if (fork) {
+    cudaEventRecord(b->join_ev, b->side);
+    cudaStreamWaitEvent(b->stream, b->join_ev, 0);
+  }
 }
 
 // The rebuild decision over all neighbour items, then the rebuilds listed.
@@ -2434,6 +2488,12 @@ extern "C" pimd_status pimd_batch_create(int32_t max_replicas, void *stream, pim
     }
     b->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    pimd_batch_destroy(b);
+    return fail(PIMD_ECUDA, "cannot create the batch's side stream");
+  }
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -2518,6 +2578,9 @@ extern "C" void pimd_batch_destroy(pimd_batch *b) {
   for (auto p : b->mtab) dev_free(b->alloc, p, b->stream);
   if (b->h_eout) cudaFreeHost(b->h_eout);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -2841,10 +2904,18 @@ extern "C" pimd_status pimd_batch_estimators(pimd_batch *b, pimd_estimates *out)
     b->launches += 2;
     BK(cudaGetLastError());
   }
-  if ((st = pimd_batch_status(b, nullptr, nullptr, nullptr)) != PIMD_OK) return st;
+  // the control words (steps, error bits) and the outputs, one synchronisation
+  k_bgather_ctl<<<(b->capacity + 127) / 128, 128, 0, b->stream>>>(b->d_reps, b->capacity, b->d_ctl);
+  b->launches += 1;
+  BK(cudaGetLastError());
+  BK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(long long) * kCtlWords * b->capacity, cudaMemcpyDeviceToHost,
+                     b->stream));
   BK(cudaMemcpyAsync(b->h_eout, b->d_eout, sizeof(double) * kOutStride * b->capacity, cudaMemcpyDeviceToHost,
                      b->stream));
   BK(cudaStreamSynchronize(b->stream));
+  for (int s = 0; s < b->capacity; ++s)
+    if (b->reps[s].live && (b->h_ctl[(size_t)s * kCtlWords + kCtlWords - 1] & kErrNbrOverflow))
+      return fail(PIMD_EOVERFLOW, "replica %d: neighbour list overflow", s);
   for (int s = 0; s < b->capacity; ++s) {
     pimd_estimates &e = out[s];
     std::memset(&e, 0, sizeof(e));

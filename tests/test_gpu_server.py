@@ -75,6 +75,31 @@ def test_served_job_agrees_with_oracle(orc, pimd):
     srv.close()
 
 
+def test_serving_trace_jobs_agree_with_oracle(orc, pimd):
+    """Jobs of the serving workload itself (the Poisson trace's boxes, drawn
+    on the perturbed lattice, its temperatures, seeds and bead counts),
+    served together at a reduced step count, against the oracle: the
+    trace's first jobs small enough for the oracle to follow in seconds."""
+    trace = inputs.serving_trace(2000, 50.0, seed=1)
+    picks = [j for j in trace if j.nmol <= 160 and j.P <= 32][:5]
+    assert len(picks) == 5
+    srv = pimd.Server(8 << 30, max_replicas=8, chunk_steps=10, keep_state=True)
+    jobs = {}
+    for j in picks:
+        L = inputs.box_length(j.nmol)
+        x0, mass = inputs.water_lattice_box(j.nmol, L, j.P, j.seed % (2 ** 31), jitter=0.02)
+        kw = dict(T=j.T, dt=5e-4, ff=inputs.water_ff_for_box(L), box=(L, L, L), seed=j.seed)
+        jobs[srv.submit(x0, mass, nsteps=25, **kw)] = (x0, mass, kw)
+    res = wait(srv, list(jobs))
+    for jid, (x0, mass, kw) in jobs.items():
+        x, v, st = srv.get_state(jid)
+        assert st == 25
+        c = orc.Sim(x0, mass, potential=1, **kw)
+        c.run(25)
+        assert_split_close(x, v, res[jid], c, c.estimators(), "trace job %d (P = %d)" % (jid, x0.shape[0]))
+    srv.close()
+
+
 def test_small_jobs_pass_a_head_job_that_does_not_fit(pimd):
     """A head job that must wait for memory does not idle the budget: a later
     job that fits is admitted while the head waits."""
