@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from tests._gpu import pimd  # noqa: F401
+from tests._kat import published_vectors
 
 pytestmark = pytest.mark.gpu
 
@@ -32,3 +33,12 @@ def test_noise_words_and_deviates(orc, pimd, seed, stream, step):
             r = np.sqrt(-2.0 * np.log(u[[0, 0, 2]]))
             tol = 8 * np.spacing(np.maximum(r, 1.0))
             assert np.all(np.abs(eta[k, i] - c) <= tol), (k, i, eta[k, i], c)
+
+
+def test_device_words_match_published_vector(pimd):
+    """The published all-zero Philox-4x32-10 vector (counter 0, key 0) is the
+    device's word for seed 0, atom 0, mode 0, stream 0, step 0."""
+    ctr, key, out = published_vectors()[0]
+    assert ctr == [0, 0, 0, 0] and key == [0, 0]
+    words, _ = pimd.noise_sample(0, 0, 0, 1, 1)
+    assert list(map(int, words[0, 0])) == out
