@@ -514,13 +514,14 @@ void pimd_server_destroy(pimd_server *s);
  * Limits: 1 <= P <= 128 and 1 <= N with 3 N P < 2^31; other sizes are
  * EINVAL, as are T <= 0, volume < 0, sp <= 0, fmass <= 0 and fmmode normal
  * with method pimd.  The call synchronises the stream and copies the result
- * into *out before it returns.  The array is shared by every call on a
+ * into *out before it returns, so it cannot be captured into a CUDA graph.
+ * The array is shared by every call on a
  * device and keeps the last call's contents; each call rewrites all it
  * reads, but calls whose kernels overlap on one GPU race and must be
  * serialised by the caller.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current),
  * which loads the library's device code there if nothing has yet; make that
- * first call before any stream capture begins on the device. */
+ * first call while no other stream of the device is capturing a graph. */
 pimd_status pimd_estimators_noalloc(int32_t N, int32_t P, double T, double volume, const double *x,
                                     const double *v_nm, const double *F, const double *mass,
                                     const double *U_bead, double vir_sum, const pimd_params *params,

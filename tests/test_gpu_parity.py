@@ -116,14 +116,54 @@ def test_water_64_molecules_P32(orc, pimd, integ):
     _compare_est(g.estimators(), c.estimators(), 1e-8)
 
 
+def _skin_crossed(c, nmol, L, steps, skin=1.5):
+    """Step the oracle one step at a time and report whether the list
+    criterion 2 (centroid drift + bead spread) > skin of the oxygens, counted
+    from the initial centroids, is crossed: then the device must have rebuilt
+    its lists at least once during the run."""
+    def centroids(x):
+        return x[:, 0:3 * nmol:3, :].mean(axis=0)
+    c0 = centroids(c.x)
+    crossed = False
+    for _ in range(steps):
+        c.run(1)
+        cc = centroids(c.x)
+        d = cc - c0
+        d -= L * np.rint(d / L)
+        drift = np.sqrt((d * d).sum(axis=1)).max()
+        spread = np.sqrt(((c.x[:, 0:3 * nmol:3, :] - cc[None]) ** 2).sum(axis=2)).max()
+        crossed |= 2.0 * (drift + spread) > skin
+    return crossed
+
+
 def test_water_large_box_neighbour_rebuilds(orc, pimd):
     """512 molecules (24.84 A box): the O-O list is a genuine subset, and a
-    hot start makes the skin criterion trigger rebuilds during the run."""
+    hot start (900 K) crosses the skin criterion near step 53 of the 80, so
+    the lists are rebuilt during the run (one bead chunk per molecule)."""
     x0, mass = _water(512, 24.84, 4, 2, jitter=0.05)
-    c, g = _pair(orc, pimd, x0, mass, T=600.0, dt=5e-4, potential=1, ff=inputs.WATER_FF,
+    c, g = _pair(orc, pimd, x0, mass, T=900.0, dt=5e-4, potential=1, ff=inputs.WATER_FF,
                  box=(24.84,) * 3, tau=0.05)
-    c.run(60)
-    g.step(60)
+    assert _skin_crossed(c, 512, 24.84, 80)
+    g.step(80)
+    xg, vg, _ = g.get_state()
+    assert coord_err(xg, c.x) < 1e-8
+    assert coord_err(vg, c.v) < 1e-8
+    _compare_est(g.estimators(), c.estimators(), 1e-8)
+
+
+@pytest.mark.parametrize("P", [40, 64])
+def test_water_two_bead_chunks_neighbour_rebuilds(orc, pimd, P):
+    """More than 32 beads: two bead chunks per molecule, each cluster of the
+    force kernel rebuilding the same list; a hot start (900 K, 0.05 A
+    jitter) crosses the skin near step 55 of the 80, so the lists are
+    rebuilt on the device."""
+    nmol = 96
+    L = inputs.box_length(nmol)
+    x0, mass = _water(nmol, L, P, 5, jitter=0.05)
+    c, g = _pair(orc, pimd, x0, mass, T=900.0, dt=5e-4, potential=1, ff=inputs.water_ff_for_box(L),
+                 box=(L,) * 3, tau=0.05)
+    assert _skin_crossed(c, nmol, L, 80)
+    g.step(80)
     xg, vg, _ = g.get_state()
     assert coord_err(xg, c.x) < 1e-8
     assert coord_err(vg, c.v) < 1e-8
