@@ -698,25 +698,26 @@ __device__ void bstep_warp(const RepDesc *__restrict__ Rp, int tile, float *__re
     const int a = lane / 3, c = lane - 3 * a;
     const int i = tile0 + a;
     const size_t ic = (size_t)tile0 * 3 + lane;
+    // the increments (kick, noise) are products of FP32 quantities, formed
+    // in FP32; the velocity and position accumulate them in FP64
     const double dr = Rp->dr0, c1_0 = Rp->c1_0;
-    const double kfac = (integ == 0 ? (first ? 0.5 : 1.0) : 0.5) * dt;
-    const double kb = kfac * __ldg(Rp->inv_mm + i);
-    const double c2s = Rp->c2_0 * __ldg(Rp->sigv + i);
-    const double f0 = (double)sf0[lane];
+    const float kbf = (integ == 0 ? kick : half) * __ldg(Rp->inv_mmf + i);
+    const float c2sf = __ldg(c2f) * __ldg(Rp->sigvf + i);
+    const float f0 = sf0[lane];
     const float e = se[lane], e2 = se2[lane];
     double x = xpre, v = vpre;
     if (integ == 0) {
-      v = fma(kb, f0, v);
+      v += (double)(kbf * f0);
       x = fma(dr, v, x);
-      if (thermo) v = fma(c1_0, v, c2s * (double)e);
+      if (thermo) v = fma(c1_0, v, (double)(c2sf * e));
       x = fma(dr, v, x);
     } else {
       if (!first) {
-        v = fma(kb, f0, v);
-        if (thermo) v = fma(c1_0, v, c2s * (double)e2);
+        v += (double)(kbf * f0);
+        if (thermo) v = fma(c1_0, v, (double)(c2sf * e2));
       }
-      if (thermo) v = fma(c1_0, v, c2s * (double)e);
-      v = fma(kb, f0, v);
+      if (thermo) v = fma(c1_0, v, (double)(c2sf * e));
+      v += (double)(kbf * f0);
       x = fma(dr, v, x);
     }
     Rp->xc[ic] = x;
