@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_force_harmonic_f64(ForceArgs a) {
   if (a.step_inc && blockIdx.x == 0 && threadIdx.x == 0) *a.step_inc += 1;
 }
 
-// Water-like model, FP64.  A cluster of kForceBlocks (2) blocks x 4 warps
+// Water-like model, FP64.  A cluster of kForceBlocks (4) blocks x 4 warps
 // serves one (molecule m, chunk of Bk = min(P, 32) beads).  Lane = (group u,
 // bead kl): beads of the chunk in adjacent lanes (coalesced gathers of a
 // neighbour's bead row), G = 32 / Bk groups when P < 32.  Warps s = 0 ..
