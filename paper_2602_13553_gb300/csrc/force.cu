@@ -116,7 +116,13 @@ __global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_fo
     // and block maxima
     double md = 0.0, me = 0.0;
     const double2 *bm = reinterpret_cast<const double2 *>(a.blkmax);
-    for (int b = threadIdx.x; b < a.nblk_check; b += blockDim.x) {
+    int b = threadIdx.x;
+    for (; b + (int)blockDim.x < a.nblk_check; b += 2 * blockDim.x) {   // two entries in flight
+      const double2 e = bm[b], f = bm[b + blockDim.x];
+      md = fmax(md, fmax(e.x, f.x));
+      me = fmax(me, fmax(e.y, f.y));
+    }
+    if (b < a.nblk_check) {
       const double2 e = bm[b];
       md = fmax(md, e.x);
       me = fmax(me, e.y);
@@ -263,19 +269,18 @@ __global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_fo
     const double e4 = 4.0 * a.eps, e24 = 24.0 * a.eps;
     double f0 = 0.0, f1 = 0.0, f2 = 0.0, ulj = 0.0, wlj = 0.0;
     double wx = 0.0, wy = 0.0, wz = 0.0;
-    for (int q = q0; q < q1; ++q) {
-      const int j = nl[q];
-      const size_t sj = (size_t)(3 * j) * 3 * P + k;
-      float d0f = __ldg(a.x32 + sj) - xf0, d1f = __ldg(a.x32 + sj + P) - xf1;
-      float d2f = __ldg(a.x32 + sj + 2 * P) - xf2;
+    // one candidate j from its FP32 and FP64 bead positions: the FP32
+    // prefilter, then the exact FP64 cutoff test and the pair terms
+    auto pair = [&](const float (&pf)[3], const double (&pd)[3]) {
+      float d0f = pf[0] - xf0, d1f = pf[1] - xf1, d2f = pf[2] - xf2;
       const float n0 = rintf(d0f * if0), n1 = rintf(d1f * if1), n2 = rintf(d2f * if2);
       d0f = fmaf(-n0, Lf0, d0f);
       d1f = fmaf(-n1, Lf1, d1f);
       d2f = fmaf(-n2, Lf2, d2f);
-      if (d0f * d0f + d1f * d1f + d2f * d2f >= rpre2) continue;
-      const double d0 = fma(-(double)n0, L0, a.x[sj] - xo0);
-      const double d1 = fma(-(double)n1, L1, a.x[sj + P] - xo1);
-      const double d2 = fma(-(double)n2, L2, a.x[sj + 2 * P] - xo2);
+      if (d0f * d0f + d1f * d1f + d2f * d2f >= rpre2) return;
+      const double d0 = fma(-(double)n0, L0, pd[0] - xo0);
+      const double d1 = fma(-(double)n1, L1, pd[1] - xo1);
+      const double d2 = fma(-(double)n2, L2, pd[2] - xo2);
       const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
       if (r2 < rc2) {
         // 1 / r2 by Newton's iteration x <- x (2 - r2 x) from the FP32
@@ -298,6 +303,39 @@ __global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_fo
           wz = fma(fr * d2, d2, wz);
         }
       }
+    };
+    // four candidates per round: their indices, then their bead rows (FP32
+    // and FP64), are requested before any arithmetic, so the gathers of a
+    // round overlap; the candidates are then summed in list order
+    int q = q0;
+    for (; q + 4 <= q1; q += 4) {
+      int jj[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) jj[v] = nl[q + v];
+      float pf[4][3];
+      double pd[4][3];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const size_t sj = (size_t)(3 * jj[v]) * 3 * P + k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          pf[v][c] = __ldg(a.x32 + sj + c * P);
+          pd[v][c] = a.x[sj + c * P];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) pair(pf[v], pd[v]);
+    }
+    for (; q < q1; ++q) {
+      const size_t sj = (size_t)(3 * nl[q]) * 3 * P + k;
+      float pf[3];
+      double pd[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pf[c] = __ldg(a.x32 + sj + c * P);
+        pd[c] = a.x[sj + c * P];
+      }
+      pair(pf, pd);
     }
     // each molecule takes half of every pair's energy and virial
     acc[0] = f0;
