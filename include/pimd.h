@@ -416,7 +416,7 @@ pimd_status pimd_batch_autotune(pimd_batch *b, int32_t steps_per_trial, int32_t 
 enum { PIMD_TRANSFORMS_TENSOR = 0, PIMD_TRANSFORMS_FFMA = 1 };
 pimd_status pimd_batch_set_transforms(pimd_batch *b, int32_t kind);
 
-/* Kernel accounting: kernels enqueued so far (graph nodes included), and/* Kernel accounting: kernels enqueued so far (graph nodes included), and
+/* Kernel accounting: kernels enqueued so far (graph nodes included), and
  * nsteps real steps launched one kernel at a time with CUDA events around
  * four groups of the step's kernels: ms[0..3] receive the summed device
  * milliseconds of the control kernel, the fused-step kernels (warp items and,
