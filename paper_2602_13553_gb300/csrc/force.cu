@@ -85,7 +85,7 @@ template <bool kDiag>
 __global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_force_water_f64(ForceArgs a) {
   constexpr int NC = kDiag ? 14 : 11;   // F (9), U, Tr Xi, then Xi_xx, Xi_yy, Xi_zz
   __shared__ double sacc[NC][128];
-  __shared__ double red[NC][32];
+  __shared__ double gath[kForceBlocks][NC][32];   // rank 0: every block's partial sums
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int P = a.P;
@@ -353,12 +353,15 @@ __global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_fo
 #pragma unroll
   for (int c = 0; c < NC; ++c) sacc[c][threadIdx.x] = acc[c];
   __syncthreads();
+  // each block's partial sums go straight into rank 0's shared memory
+  // (distributed shared memory stores), so after one cluster barrier rank 0
+  // sums them locally in rank order and the other blocks may exit
   for (int t = threadIdx.x; t < NC * Bk; t += blockDim.x) {
     const int comp = t / Bk, kk = t % Bk;
     double sum = 0.0;
     for (int w = 0; w < 4; ++w)
       for (int g = 0; g < G; ++g) sum += sacc[comp][w * 32 + g * Bk + kk];
-    red[comp][kk] = sum;
+    *cluster.map_shared_rank(&gath[rank][comp][kk], 0) = sum;
   }
   cluster.sync();
   if (rank == 0 && m < a.nmol) {
@@ -367,7 +370,7 @@ __global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_fo
       const int k2 = chunk * Bk + kk;
       if (k2 >= P) continue;
       double sum = 0.0;
-      for (int r = 0; r < kForceBlocks; ++r) sum += cluster.map_shared_rank(&red[0][0], r)[comp * 32 + kk];
+      for (int r = 0; r < kForceBlocks; ++r) sum += gath[r][comp][kk];
       if (comp < 9)
         a.F[(size_t)(3 * m + comp / 3) * 3 * P + (comp % 3) * P + k2] = sum;
       else if (comp == 9)
@@ -379,8 +382,6 @@ __global__ void __cluster_dims__(kForceBlocks, 1, 1) __launch_bounds__(128) k_fo
     }
     if (a.step_inc && blockIdx.x == 0 && threadIdx.x == 0) *a.step_inc += 1;
   }
-  // keep every block's shared memory alive until rank 0 has read it
-  cluster.sync();
 }
 
 // --- O-O neighbour list on ring-polymer centroids ---------------------------
