@@ -2,16 +2,18 @@
 // size advanced together in split precision, and the serving layer on top.
 //
 // Every replica's state lives in its own device arena and is described by a
-// RepDesc in a device table.  Each MD step is five or six launches over all
-// replicas -- control, step (warp items, and block items when some replica's
-// bead count needs them), rebuild decision, rebuilds, forces -- each a
-// persistent grid of fixed size that walks a device-resident work list (step
-// tiles, force clusters, neighbour blocks) whose length it reads from device
-// memory.  Because neither grid sizes nor pointers change when replicas join
-// or leave, one CUDA graph of G steps is captured once per batch and replayed
-// for the batch's lifetime: continuous batching without re-capture (a graph
-// is captured again only when block items appear or disappear, or when the
-// warp-item shared-memory slot grows).  Per-replica
+// RepDesc in a device table.  Each MD step is a sequence of launches over all
+// replicas -- control; the step, one kernel per class of bead count present
+// (warp items of 64 beads; of 8, 16 or 32; of 128; block items of any other
+// count), the classes side by side on two streams; rebuild decision;
+// rebuilds; forces -- each a persistent grid of fixed size that walks a
+// device-resident work list (step tiles, force clusters, neighbour blocks)
+// whose length it reads from device memory.  Because neither grid sizes nor
+// pointers change when replicas join or leave, one CUDA graph of G steps is
+// captured once per batch and replayed for the batch's lifetime: continuous
+// batching without re-capture (a graph is captured again only when the set
+// of classes present changes, a work list outgrows its array, or the
+// autotuner changes a grid).  Per-replica
 // step counters, step budgets and the "at integer time" flag live on the
 // device, so every replica runs exactly its own number of steps.
 //
