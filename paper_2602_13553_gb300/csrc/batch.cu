@@ -2655,7 +2655,16 @@ extern "C" pimd_status pimd_batch_add(pimd_batch *b, const pimd_system *sys, int
   d.eps = sys->ff[4];
   d.sig = sys->ff[5];
   d.rc = sys->ff[6];
-  d.skin = 1.5;
+  // Verlet skin of the replica's O-O list (A): a thinner skin than the
+  // single-system 1.5 A trades more frequent rebuilds for fewer list
+  // candidates in the force kernel (the 256-replica mix: 1.5 A 0.289, 1.0 A
+  // 0.276, 0.85 A 0.273, 0.7 A 0.270 ms per MD step; rebuilds on 1.6, 2.7,
+  // 3.4, 4.7% of replica-steps).  0.85 A keeps every replica of 100-400 K
+  // well clear of rebuilding every step (the oxygens' bead spread alone
+  // uses up to ~0.5 A of the budget at 100 K).  Rebuild timing changes no
+  // force: the list is complete whenever it is used and its sums are
+  // ordered by neighbour index.
+  d.skin = 0.85;
   d.rlist = d.rc + d.skin;
   for (int c = 0; c < 3; ++c) {
     d.boxf[c] = (float)d.box[c];
