@@ -41,8 +41,8 @@ WATER_FF = (45.0, 1.0, 3.3, math.radians(104.5), 6.7e-3, 3.166, 6.0)
 
 def water_ff_for_box(L: float):
     """The water-like force field for a cubic box of edge L: the 6 A O-O cutoff,
-    capped at 0.48 L in boxes too small for minimum-image interactions at 6 A
-    (the 32-molecule boxes of the mixes are 9.86 A)."""
+    capped at 0.48 L (boxes under 12.5 A, such as the 9.86 A 32-molecule boxes
+    of the mixes), which keeps the minimum image valid with a margin."""
     ff = list(WATER_FF)
     ff[6] = min(ff[6], 0.48 * L)
     return tuple(ff)
